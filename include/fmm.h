@@ -1,0 +1,199 @@
+/*
+ * fmm.h -- C ABI of a single-GPU fast multipole method for the 3-D Laplace
+ * (1/r) kernel on NVIDIA GB300 (sm_103a).
+ *
+ * The method is the FMM of Yokota & Barba, "A Tuned and Scalable Fast
+ * Multipole Method as a Preeminent Algorithm for Exascale Systems"
+ * (arXiv:1106.2176): a Morton-indexed octree (Sec. 2.2, Sec. 5), multipole and
+ * local expansions truncated after p terms (Sec. 2.1), the operators P2M,
+ * M2M, M2L, L2L, L2P and the direct near-field P2P (Sec. 2.1, Fig.
+ * flow_chart; Sec. 3.1 names P2P and M2L as the dominant kernels).
+ *
+ * Given N particles x_i with charges q_i the library computes
+ *     phi_i  = sum_{j != i, r_ij > 0} q_j / |x_i - x_j|
+ *     grad_i = d phi_i / d x_i = - sum_{j != i, r_ij > 0} q_j (x_i - x_j) / |x_i - x_j|^3
+ * to the accuracy set by p and theta (no 1/(4 pi) factor, no softening;
+ * coincident pairs contribute nothing).
+ *
+ * Conventions shared by every entry point:
+ *   - Return value: FMM_OK (0) on success, a negative FMM_E* code on error.
+ *     No C++ exception crosses this boundary. fmm_last_error() gives a
+ *     message for the calling thread.
+ *   - Pointers to particle data are device pointers unless FMM_HOST_MEM is
+ *     OR-ed into the dtype argument of fmm_build; then x, q and the outputs
+ *     of fmm_evaluate are host pointers and the library copies them.
+ *   - The caller owns x, q, phi and grad. The handle owns every workspace;
+ *     fmm_destroy frees them. fmm_build copies what it needs, so x and q may
+ *     be reused once the handle's stream has passed the build.
+ *   - All device work is asynchronous on the handle's stream (the legacy
+ *     default stream unless fmm_set_stream was called). fmm_build makes a
+ *     few host synchronisations to size the tree and the lists; fmm_evaluate
+ *     with device pointers makes none.
+ *   - A handle is not thread safe; use one handle per thread.
+ */
+#ifndef FMM_H
+#define FMM_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define FMM_API __attribute__((visibility("default")))
+#else
+#define FMM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fmm_ctx *fmm_handle;
+
+/* status codes */
+enum {
+    FMM_OK = 0,
+    FMM_EINVAL = -1,     /* bad argument (null pointer, size or range) */
+    FMM_ENOMEM = -2,     /* device or host allocation failed */
+    FMM_ESTATE = -3,     /* call out of order, e.g. evaluate before build */
+    FMM_ECUDA = -4,      /* a CUDA runtime call or kernel launch failed */
+    FMM_ENONFINITE = -5, /* a position is NaN or infinite */
+    FMM_ENODEV = -6      /* no usable sm_103 device */
+};
+
+/* element types of x, q, phi, grad; FMM_HOST_MEM may be OR-ed in */
+enum { FMM_F32 = 0, FMM_F64 = 1, FMM_HOST_MEM = 0x100 };
+
+/* arithmetic of the evaluation */
+enum {
+    FMM_FP64 = 0,  /* every stage in FP64 (the on-device reference path) */
+    FMM_MIXED = 1  /* FP32 P2P and expansions, M2L on the tensor cores in
+                      split TF32 with FP32 accumulation, FP64 tree, FP64
+                      offsets and final sums */
+};
+
+/* M2L engine (FMM_MIXED only) */
+enum { FMM_M2L_AUTO = 0, FMM_M2L_TENSOR = 1, FMM_M2L_CUDACORE = 2 };
+
+typedef struct {
+    int64_t n;              /* particles of the last build */
+    int64_t ncells;         /* cells of the tree */
+    int64_t nleaves;
+    int32_t depth;          /* deepest level */
+    int32_t precision;      /* FMM_FP64 or FMM_MIXED */
+    int64_t n_p2p_pairs;    /* leaf pairs in the P2P lists, (A, A) included */
+    int64_t n_m2l_pairs;    /* accepted cell pairs, same-level and other */
+    int64_t n_m2l_irregular;/* accepted pairs whose cells sit on different levels */
+    int64_t n_interactions; /* sum over P2P pairs of n_A * n_B, minus n */
+    int64_t n_stencil;      /* same-level M2L translation vectors (all octants) */
+    int32_t m2l_engine;     /* engine used by the last evaluate */
+    int32_t reserved0;
+    /* milliseconds of the last build / evaluate, measured with CUDA events */
+    double ms_build, ms_evaluate;
+    double ms_p2m, ms_m2m, ms_m2l, ms_l2l, ms_l2p, ms_p2p, ms_combine;
+    int64_t kernel_launches; /* kernels this handle launched since creation */
+} fmm_stats;
+
+/* Sizes of the arrays fmm_export_tree writes. */
+typedef struct {
+    int64_t n, ncells, n_p2p, n_m2l;
+    int32_t depth, p;
+} fmm_tree_sizes;
+
+/*
+ * Create a handle for up to N particles with expansions of p terms (degrees
+ * 0..p-1, Sec. 2.1), multipole acceptance parameter theta and leaf size
+ * ncrit. Limits: N >= 1, 1 <= p <= 20, 0 < theta < 1, ncrit >= 1. The cell
+ * accepted for M2L against cell B when r_A + r_B < theta |c_A - c_B|, r the
+ * half diagonal of the box. Precomputes the level-independent translation
+ * operators. Returns FMM_EINVAL, FMM_ENODEV, FMM_ENOMEM or FMM_ECUDA on error;
+ * *out is set to NULL then.
+ */
+FMM_API int fmm_create(int64_t N, int p, double theta, int ncrit, fmm_handle *out);
+
+/* Select FMM_FP64 (default) or FMM_MIXED. Takes effect at the next build. */
+FMM_API int fmm_set_precision(fmm_handle h, int mode);
+
+/* Select the M2L engine for FMM_MIXED (FMM_M2L_AUTO uses the tensor cores). */
+FMM_API int fmm_set_m2l_engine(fmm_handle h, int engine);
+
+/* Use the given cudaStream_t (NULL = legacy default stream) for all work. */
+FMM_API int fmm_set_stream(fmm_handle h, void *stream);
+
+/*
+ * Build the octree and the interaction lists (Sec. 2.1 hierarchical
+ * subdivision into near and far; Sec. 2.2 Morton-indexed boxes; Sec. 5
+ * sorted indices with start/offset ranges).
+ *   x: n*3 positions, row-major (x0 y0 z0 x1 ...); q: n charges;
+ *   dtype: FMM_F32 or FMM_F64, optionally | FMM_HOST_MEM;
+ *   1 <= n <= N of fmm_create.
+ * Errors: FMM_EINVAL (null pointer, n out of range, bad dtype),
+ * FMM_ENONFINITE (a coordinate is NaN or infinite), FMM_ENOMEM, FMM_ECUDA.
+ */
+FMM_API int fmm_build(fmm_handle h, const void *x, const void *q, int64_t n, int dtype);
+
+/*
+ * Evaluate the potential and its gradient at every particle of the last
+ * build, in the caller's particle order (Sec. 2.1, Fig. flow_chart: P2M,
+ * M2M, M2L, L2L, L2P and P2P).
+ *   phi: n values; grad: n*3 values row-major, or NULL to skip the gradient
+ *   (it is computed anyway). Element type and memory kind are the build's.
+ * Errors: FMM_ESTATE (no successful build), FMM_EINVAL, FMM_ECUDA.
+ */
+FMM_API int fmm_evaluate(fmm_handle h, void *phi, void *grad);
+
+/* Counters and phase timings of the last build and evaluate; synchronises
+ * the handle's stream. */
+FMM_API int fmm_get_stats(fmm_handle h, fmm_stats *out);
+
+/* Sizes of the arrays written by fmm_export_tree (after a build). */
+FMM_API int fmm_get_tree_sizes(fmm_handle h, fmm_tree_sizes *out);
+
+/*
+ * Copy the tree and the lists of the last build to HOST buffers (any may be
+ * NULL). Sizes from fmm_get_tree_sizes. Used to check the GPU tree bit for
+ * bit against an independent implementation.
+ *   keys[n]       sorted 63-bit Morton keys
+ *   perm[n]       perm[k] = input index of the k-th sorted particle
+ *   level[ncells], anchor[ncells] (Morton key of the cell's lowest corner),
+ *   begin[ncells], end[ncells] (sorted particle range), child[ncells]
+ *   (first child or -1), nchild[ncells], parent[ncells] (-1 for the root);
+ *   cells in breadth-first order, key order within a level
+ *   p2p_ptr[ncells+1], p2p_idx[n_p2p]: CSR by target cell, sources ascending
+ *   m2l_ptr[ncells+1], m2l_idx[n_m2l]: CSR by target cell, sources ascending
+ *   box[4]: origin x, y, z of the root cube and its half width R0
+ * Synchronises the handle's stream.
+ */
+FMM_API int fmm_export_tree(fmm_handle h, uint64_t *keys, int32_t *perm, int32_t *level, uint64_t *anchor,
+                    int32_t *begin, int32_t *end, int32_t *child, int32_t *nchild, int32_t *parent,
+                    int64_t *p2p_ptr, int32_t *p2p_idx, int64_t *m2l_ptr, int32_t *m2l_idx,
+                    double *box);
+
+/*
+ * Copy the multipole and local expansions of the last evaluate to HOST
+ * buffers M and L (ncells * p * p doubles each, either may be NULL). Entry
+ * [c][k] is the k-th real coefficient of cell c in the packed real layout:
+ * for degree n at offset n*n, Re(n,0), then Re(n,m), Im(n,m) for m = 1..n.
+ * Coefficients are scaled by the cell width w: M_n^m / w^n and L_n^m w^(n+1).
+ * Synchronises the handle's stream.
+ */
+FMM_API int fmm_export_expansions(fmm_handle h, double *M, double *L);
+
+/*
+ * FP64 direct sum on the device (the quantity the FMM approximates), for the
+ * targets tidx[0..nt) (device int64 indices) or all n particles when tidx is
+ * NULL. x, q: device FP64 (n*3, n); phi[nt], grad[nt*3]: device FP64. Sums
+ * run over j in index order. Runs on the handle's stream; the handle only
+ * supplies the stream and the launch counter.
+ */
+FMM_API int fmm_direct(fmm_handle h, const double *x, const double *q, int64_t n, const int64_t *tidx,
+               int64_t nt, double *phi, double *grad);
+
+FMM_API int fmm_destroy(fmm_handle h);
+
+/* Message of the last error on the calling thread ("" if none). */
+FMM_API const char *fmm_last_error(fmm_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FMM_H */

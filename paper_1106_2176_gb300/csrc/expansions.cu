@@ -1,0 +1,803 @@
+// Multipole and local expansions: P2M, M2M, M2L, L2L and L2P (Sec. 2.1 and
+// Fig. flow_chart of Yokota & Barba, arXiv:1106.2176), over solid harmonics of
+// p terms (degrees 0..p-1).
+//
+// Basis: R_n^m(x) = r^n P_n^m(cos t) e^{imf} / (n+m)!  and
+//        I_n^m(x) = (n-m)! P_n^m(cos t) e^{imf} / r^(n+1),
+// P_n^m without the Condon-Shortley phase, X_n^{-m} = (-1)^m conj(X_n^m). They
+// are generated here from Cartesian three-term recurrences (no trigonometry):
+//   R_m^m = R_{m-1}^{m-1} (x + iy) / (2m),   R_{m+1}^m = z R_m^m,
+//   (n+m)(n-m) R_n^m = (2n-1) z R_{n-1}^m - r^2 R_{n-2}^m;
+//   I_0^0 = 1/r,  I_m^m = (2m-1) (x + iy) / r^2 I_{m-1}^{m-1},
+//   I_{m+1}^m = (2m+1) z / r^2 I_m^m,
+//   r^2 I_n^m = (2n-1) z I_{n-1}^m - (n+m-1)(n-m-1) I_{n-2}^m.
+//
+// Every expansion is stored scaled by the width w of its cell, M_n^m / w^n and
+// L_n^m w^(n+1); then the same-level M2L operator depends only on the integer
+// lattice offset of the two cells and M2M / L2L only on the child octant:
+//   M2M  M~p(n,m) = sum_{k,l} conj(R_k^l(t)) M~c(n-k, m-l) 2^-(n-k),  t = (c_c - c_p)/w_p
+//   M2L  L~A(n,m) += (-1)^n sum_{j,k} M~B(j,k) I_{j+n}^{k+m}(u),      u = (c_A - c_B)/w
+//   L2L  L~c(k,l) += 2^-(k+1) sum_{n,m} L~p(n,m) conj(R_{n-k}^{m-l}(t))
+//   P2M  M~(n,m)  = sum_j q_j conj(R_n^m((x_j - c)/w))
+//   L2P  phi = Re sum L~ conj(R(x^)) / w, grad from d_z R_n^m = R_{n-1}^m and
+//        (d_x + i d_y) R_n^m = -R_{n-1}^{m+1}, divided by w^2.
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <tuple>
+
+#include "fmm_internal.cuh"
+
+namespace fmm {
+
+static inline unsigned nblk(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+__host__ __device__ inline int tri(int n, int m) { return n * (n + 1) / 2 + m; }
+__host__ __device__ inline int full(int n, int m) { return n * n + n + m; }
+
+// R_n^m, 0 <= m <= n < P, triangular storage, element k at re[k * st]
+template <class T>
+__host__ __device__ void regular_tri(int P, T x, T y, T z, T *re, T *im, int st)
+{
+    const T r2 = x * x + y * y + z * z;
+    T mre = T(1), mim = T(0);
+    for (int m = 0; m < P; m++) {
+        if (m > 0) {
+            const T f = T(1) / T(2 * m);
+            const T a = (mre * x - mim * y) * f;
+            const T b = (mre * y + mim * x) * f;
+            mre = a;
+            mim = b;
+        }
+        re[tri(m, m) * st] = mre;
+        im[tri(m, m) * st] = mim;
+        if (m + 1 >= P) continue;
+        T p2re = mre, p2im = mim, p1re = z * mre, p1im = z * mim;
+        re[tri(m + 1, m) * st] = p1re;
+        im[tri(m + 1, m) * st] = p1im;
+        for (int n = m + 2; n < P; n++) {
+            const T a = T(2 * n - 1), b = T(1) / T((n + m) * (n - m));
+            const T cre = (a * z * p1re - r2 * p2re) * b;
+            const T cim = (a * z * p1im - r2 * p2im) * b;
+            re[tri(n, m) * st] = cre;
+            im[tri(n, m) * st] = cim;
+            p2re = p1re; p2im = p1im; p1re = cre; p1im = cim;
+        }
+    }
+}
+
+// I_n^m, 0 <= m <= n < Q, triangular storage; x != 0
+template <class T>
+__host__ __device__ void irregular_tri(int Q, T x, T y, T z, T *re, T *im)
+{
+    const T r2 = x * x + y * y + z * z;
+    const T ir2 = T(1) / r2;
+    T mre = sqrt(ir2), mim = T(0);
+    for (int m = 0; m < Q; m++) {
+        if (m > 0) {
+            const T f = T(2 * m - 1) * ir2;
+            const T a = (mre * x - mim * y) * f;
+            const T b = (mre * y + mim * x) * f;
+            mre = a;
+            mim = b;
+        }
+        re[tri(m, m)] = mre;
+        im[tri(m, m)] = mim;
+        if (m + 1 >= Q) continue;
+        const T f1 = T(2 * m + 1) * z * ir2;
+        T p2re = mre, p2im = mim, p1re = mre * f1, p1im = mim * f1;
+        re[tri(m + 1, m)] = p1re;
+        im[tri(m + 1, m)] = p1im;
+        for (int n = m + 2; n < Q; n++) {
+            const T a = T(2 * n - 1) * z, b = T((n + m - 1) * (n - m - 1));
+            const T cre = (a * p1re - b * p2re) * ir2;
+            const T cim = (a * p1im - b * p2im) * ir2;
+            re[tri(n, m)] = cre;
+            im[tri(n, m)] = cim;
+            p2re = p1re; p2im = p1im; p1re = cre; p1im = cim;
+        }
+    }
+}
+
+// complex coefficient (n, m), any -n <= m <= n, of a packed real expansion
+template <class T>
+__device__ __forceinline__ void cget(const T *__restrict__ X, int n, int m, T &re, T &im)
+{
+    const int a = m < 0 ? -m : m;
+    re = X[re_idx(n, a)];
+    im = a ? X[im_idx(n, a)] : T(0);
+    if (m < 0) {
+        im = -im;
+        if (a & 1) {
+            re = -re;
+            im = -im;
+        }
+    }
+}
+
+__device__ __forceinline__ void tri_inv(int k, int &n, int &m)
+{
+    n = (int)((sqrtf(8.0f * k + 1.0f) - 1.0f) * 0.5f);
+    while (tri(n + 1, 0) <= k) n++;
+    while (tri(n, 0) > k) n--;
+    m = k - tri(n, 0);
+}
+
+// geometric centre and width of a cell: origin + (anchor + 2^(20-l)) h, w = h 2^(21-l)
+__device__ __forceinline__ void cell_geom(const Box *__restrict__ b, int4 a, double c[3], double &w)
+{
+    const double h = b->h;
+    const double half = ldexp(1.0, FMM_MAXLEVEL - 1 - a.w);
+    c[0] = __dadd_rn(b->origin[0], __dmul_rn((double)a.x + half, h));
+    c[1] = __dadd_rn(b->origin[1], __dmul_rn((double)a.y + half, h));
+    c[2] = __dadd_rn(b->origin[2], __dmul_rn((double)a.z + half, h));
+    w = ldexp(h, FMM_MAXLEVEL - a.w);
+}
+
+__device__ __forceinline__ int child_octant(int4 a)
+{
+    const int bit = FMM_MAXLEVEL - a.w;
+    return ((a.x >> bit) & 1) | (((a.y >> bit) & 1) << 1) | (((a.z >> bit) & 1) << 2);
+}
+
+__device__ __forceinline__ double4_32a load_pt(const double4_32a *p, int j) { return p[j]; }
+__device__ __forceinline__ double4_32a load_pt(const float4 *p, int j)
+{
+    float4 v = p[j];
+    return make_double4_32a(v.x, v.y, v.z, v.w);
+}
+
+// ---------------------------------------------------------------------------
+// P2M: one block per leaf, a chunk of particles at a time
+// ---------------------------------------------------------------------------
+template <class T, class P4>
+__global__ void __launch_bounds__(64) p2m_k(int p, const int *__restrict__ leaves, const int *__restrict__ begin,
+                                            const int *__restrict__ end, const int4 *__restrict__ xyz,
+                                            const Box *__restrict__ box, const P4 *__restrict__ xs, T *__restrict__ M,
+                                            int chunk)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int ntri = p * (p + 1) / 2, PP = p * p;
+    T *sre = reinterpret_cast<T *>(smem_raw);
+    T *sim = sre + chunk * ntri;
+    const int c = leaves[blockIdx.x];
+    double cen[3], w;
+    cell_geom(box, xyz[c], cen, w);
+    const double iw = 1.0 / w;
+    const int b = begin[c], e = end[c];
+    T are[4] = {0, 0, 0, 0}, aim[4] = {0, 0, 0, 0};
+    for (int j0 = b; j0 < e; j0 += chunk) {
+        const int t = threadIdx.x;
+        if (t < chunk) {
+            const int j = j0 + t;
+            if (j < e) {
+                const double4_32a pt = load_pt(xs, j);
+                const T dx = (T)((pt.x - cen[0]) * iw), dy = (T)((pt.y - cen[1]) * iw), dz = (T)((pt.z - cen[2]) * iw);
+                regular_tri<T>(p, dx, dy, dz, sre + t, sim + t, chunk);
+                const T q = (T)pt.w;
+                for (int k = 0; k < ntri; k++) {
+                    sre[k * chunk + t] *= q;
+                    sim[k * chunk + t] *= -q;
+                }
+            } else {
+                for (int k = 0; k < ntri; k++) {
+                    sre[k * chunk + t] = T(0);
+                    sim[k * chunk + t] = T(0);
+                }
+            }
+        }
+        __syncthreads();
+        for (int r = 0; r < 4; r++) {
+            const int k = threadIdx.x + r * blockDim.x;
+            if (k >= ntri) break;
+            T sr = 0, si = 0;
+            for (int tt = 0; tt < chunk; tt++) {
+                sr += sre[k * chunk + tt];
+                si += sim[k * chunk + tt];
+            }
+            are[r] += sr;
+            aim[r] += si;
+        }
+        __syncthreads();
+    }
+    T *Mc = M + (size_t)c * PP;
+    for (int r = 0; r < 4; r++) {
+        const int k = threadIdx.x + r * blockDim.x;
+        if (k >= ntri) break;
+        int n, m;
+        tri_inv(k, n, m);
+        Mc[re_idx(n, m)] = are[r];
+        if (m) Mc[im_idx(n, m)] = aim[r];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// M2M: one thread per (parent cell, output coefficient)
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void m2m_k(int p, int ls, int le, const int *__restrict__ child, const int *__restrict__ nchild,
+                      const int4 *__restrict__ xyz, const T *__restrict__ rtab, T *__restrict__ M)
+{
+    const int ntri = p * (p + 1) / 2, PP = p * p;
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = ls + (int)(gid / ntri);
+    const int ci = (int)(gid % ntri);
+    if (c >= le) return;
+    const int nc = nchild[c];
+    if (nc == 0) return;
+    int n, m;
+    tri_inv(ci, n, m);
+    T sr = 0, si = 0;
+    const int c0 = child[c];
+    for (int ch = c0; ch < c0 + nc; ch++) {
+        const T *R = rtab + (size_t)child_octant(xyz[ch]) * PP * 2;
+        const T *Mc = M + (size_t)ch * PP;
+        for (int k = 0; k <= n; k++) {
+            const int j = n - k;
+            const T sc = (T)ldexp(1.0, -j);
+            for (int l = -k; l <= k; l++) {
+                const int mu = m - l;
+                if (mu > j || mu < -j) continue;
+                const T rr = R[2 * full(k, l)], ri = -R[2 * full(k, l) + 1];  // conj(R)
+                T mr, mi;
+                cget(Mc, j, mu, mr, mi);
+                sr += sc * (rr * mr - ri * mi);
+                si += sc * (rr * mi + ri * mr);
+            }
+        }
+    }
+    T *Mp = M + (size_t)c * PP;
+    Mp[re_idx(n, m)] = sr;
+    if (m) Mp[im_idx(n, m)] = si;
+}
+
+// ---------------------------------------------------------------------------
+// L2L: one thread per (child cell, output coefficient), parent level done
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void l2l_k(int p, int ls, int le, const int *__restrict__ parent, const int4 *__restrict__ xyz,
+                      const T *__restrict__ rtab, T *__restrict__ L)
+{
+    const int ntri = p * (p + 1) / 2, PP = p * p;
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = ls + (int)(gid / ntri);
+    const int ci = (int)(gid % ntri);
+    if (c >= le) return;
+    int k, l;
+    tri_inv(ci, k, l);
+    const T *R = rtab + (size_t)child_octant(xyz[c]) * PP * 2;
+    const T *Lp = L + (size_t)parent[c] * PP;
+    T sr = 0, si = 0;
+    for (int n = k; n < p; n++) {
+        const int d = n - k;
+        for (int m = -n; m <= n; m++) {
+            const int mu = m - l;
+            if (mu > d || mu < -d) continue;
+            T lr, li;
+            cget(Lp, n, m, lr, li);
+            const T rr = R[2 * full(d, mu)], ri = -R[2 * full(d, mu) + 1];
+            sr += lr * rr - li * ri;
+            si += lr * ri + li * rr;
+        }
+    }
+    const T sc = (T)ldexp(1.0, -(k + 1));
+    T *Lc = L + (size_t)c * PP;
+    Lc[re_idx(k, l)] += sc * sr;
+    if (l) Lc[im_idx(k, l)] += sc * si;
+}
+
+// ---------------------------------------------------------------------------
+// M2L on the CUDA cores, same-level pairs from the octant stencil.
+// One block per tile of targets (one level, one octant); the loop runs over
+// the stencil vectors v, gathering for each target the source at lattice
+// offset v (absent cells contribute nothing).
+// ---------------------------------------------------------------------------
+constexpr int M2L_CC_T = 128, M2L_CC_ACC = 12, M2L_CC_FLUSH = 16;
+
+template <class T>
+struct Acc { using type = double; };
+
+template <class T>
+__global__ void __launch_bounds__(M2L_CC_T) m2l_cc_k(int p, const M2LTile *__restrict__ tiles, const int *__restrict__ ntiles,
+                                                     const int *__restrict__ tgt, const int4 *__restrict__ xyz,
+                                                     const uint64_t *__restrict__ anchor, const LevelDesc *__restrict__ ld,
+                                                     const int *__restrict__ map_pool, const int4 *__restrict__ st,
+                                                     const int *__restrict__ st_off, const T *__restrict__ itab,
+                                                     const T *__restrict__ M, T *__restrict__ L, int tile_max)
+{
+    if ((int)blockIdx.x >= *ntiles) return;
+    const M2LTile td = tiles[blockIdx.x];
+    const int PP = p * p, Q = 2 * p - 1, QQ = Q * Q, ntri = p * (p + 1) / 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sI = reinterpret_cast<T *>(smem_raw);                 // QQ complex
+    T *sM = sI + 2 * QQ;                                     // tile_max * PP complex
+    int *ssrc = reinterpret_cast<int *>(sM + 2 * (size_t)tile_max * PP);
+    int *spos = ssrc + tile_max;                             // 3 per target
+
+    const int l = td.level, sh = FMM_MAXLEVEL - l;
+    if ((int)threadIdx.x < td.count) {
+        const int4 a = xyz[tgt[td.start + threadIdx.x]];
+        spos[3 * threadIdx.x + 0] = a.x >> sh;
+        spos[3 * threadIdx.x + 1] = a.y >> sh;
+        spos[3 * threadIdx.x + 2] = a.z >> sh;
+    }
+    const LevelDesc LD = ld[l];
+    const int nout = td.count * ntri;
+    using A = typename Acc<T>::type;
+    T blk[2 * M2L_CC_ACC];
+    A tot[2 * M2L_CC_ACC];
+#pragma unroll
+    for (int r = 0; r < 2 * M2L_CC_ACC; r++) {
+        blk[r] = T(0);
+        tot[r] = A(0);
+    }
+    const int e0 = st_off[td.octant], e1 = st_off[td.octant + 1];
+    int since = 0;
+    for (int e = e0; e < e1; e++) {
+        const int4 v = st[e];
+        __syncthreads();
+        if ((int)threadIdx.x < td.count)
+            ssrc[threadIdx.x] = level_lookup(LD, map_pool, anchor, l, spos[3 * threadIdx.x] + v.x,
+                                             spos[3 * threadIdx.x + 1] + v.y, spos[3 * threadIdx.x + 2] + v.z);
+        const T *Iv = itab + (size_t)v.w * 2 * QQ;
+        for (int i = threadIdx.x; i < 2 * QQ; i += blockDim.x) sI[i] = Iv[i];
+        __syncthreads();
+        for (int i = threadIdx.x; i < td.count * PP; i += blockDim.x) {
+            const int t = i / PP, f = i - t * PP;
+            const int src = ssrc[t];
+            int j = (int)sqrtf((float)f);
+            while (j * j > f) j--;
+            while ((j + 1) * (j + 1) <= f) j++;
+            const int k = f - j * j - j;
+            T re = 0, im = 0;
+            if (src >= 0) cget(M + (size_t)src * PP, j, k, re, im);
+            sM[2 * ((size_t)t * PP + f)] = re;
+            sM[2 * ((size_t)t * PP + f) + 1] = im;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < M2L_CC_ACC; r++) {
+            const int o = threadIdx.x + r * M2L_CC_T;
+            if (o >= nout) break;
+            const int t = o / ntri;
+            if (ssrc[t] < 0) continue;
+            int n, m;
+            tri_inv(o - t * ntri, n, m);
+            const T *Mt = sM + 2 * (size_t)t * PP;
+            T sr = 0, si = 0;
+            for (int j = 0; j < p; j++)
+                for (int k = -j; k <= j; k++) {
+                    const T mr = Mt[2 * full(j, k)], mi = Mt[2 * full(j, k) + 1];
+                    const int fi = full(j + n, k + m);
+                    const T ir = sI[2 * fi], ii = sI[2 * fi + 1];
+                    sr += mr * ir - mi * ii;
+                    si += mr * ii + mi * ir;
+                }
+            if (n & 1) {
+                sr = -sr;
+                si = -si;
+            }
+            blk[2 * r] += sr;
+            blk[2 * r + 1] += si;
+        }
+        if (++since == M2L_CC_FLUSH || e + 1 == e1) {
+            since = 0;
+#pragma unroll
+            for (int r = 0; r < 2 * M2L_CC_ACC; r++) {
+                tot[r] += (A)blk[r];
+                blk[r] = T(0);
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < M2L_CC_ACC; r++) {
+        const int o = threadIdx.x + r * M2L_CC_T;
+        if (o >= nout) break;
+        const int t = o / ntri;
+        int n, m;
+        tri_inv(o - t * ntri, n, m);
+        T *Lc = L + (size_t)tgt[td.start + t] * PP;
+        Lc[re_idx(n, m)] += (T)tot[2 * r];
+        if (m) Lc[im_idx(n, m)] += (T)tot[2 * r + 1];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// M2L between cells of different levels (explicit list, one block per target)
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(64) m2lx_k(int p, int nc, const int *__restrict__ ptr, const int *__restrict__ src,
+                                             const int4 *__restrict__ xyz, const T *__restrict__ M, T *__restrict__ L)
+{
+    const int c = blockIdx.x;
+    if (c >= nc) return;
+    const int k0 = ptr[c], k1 = ptr[c + 1];
+    if (k0 == k1) return;
+    const int PP = p * p, Q = 2 * p - 1, ntri = p * (p + 1) / 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double *tre = reinterpret_cast<double *>(smem_raw);      // Q(Q+1)/2
+    double *tim = tre + Q * (Q + 1) / 2;
+    T *sI = reinterpret_cast<T *>(tim + Q * (Q + 1) / 2);   // Q*Q complex
+    T *sM = sI + 2 * Q * Q;                                  // PP complex
+    const int4 a = xyz[c];
+    const long long WA = 1LL << (FMM_MAXLEVEL - a.w);
+    double accr[4] = {0, 0, 0, 0}, acci[4] = {0, 0, 0, 0};
+    for (int k = k0; k < k1; k++) {
+        const int B = src[k];
+        const int4 b = xyz[B];
+        const long long WB = 1LL << (FMM_MAXLEVEL - b.w);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            // u = (c_A - c_B) / w_A in half-grid units; exact in FP64
+            const double sc = 1.0 / (double)(2 * WA);
+            const double ux = (double)(2LL * (a.x - b.x) + (WA - WB)) * sc;
+            const double uy = (double)(2LL * (a.y - b.y) + (WA - WB)) * sc;
+            const double uz = (double)(2LL * (a.z - b.z) + (WA - WB)) * sc;
+            irregular_tri<double>(Q, ux, uy, uz, tre, tim);
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < Q * Q; i += blockDim.x) {
+            int n = (int)sqrtf((float)i);
+            while (n * n > i) n--;
+            while ((n + 1) * (n + 1) <= i) n++;
+            const int m = i - n * n - n, am = m < 0 ? -m : m;
+            double re = tre[tri(n, am)], im = tim[tri(n, am)];
+            if (m < 0) {
+                im = -im;
+                if (am & 1) {
+                    re = -re;
+                    im = -im;
+                }
+            }
+            sI[2 * i] = (T)re;
+            sI[2 * i + 1] = (T)im;
+        }
+        const double rho = (double)WB / (double)WA;
+        for (int i = threadIdx.x; i < PP; i += blockDim.x) {
+            int j = (int)sqrtf((float)i);
+            while (j * j > i) j--;
+            while ((j + 1) * (j + 1) <= i) j++;
+            const int kk = i - j * j - j;
+            T re, im;
+            cget(M + (size_t)B * PP, j, kk, re, im);
+            const T s = (T)pow(rho, (double)j);
+            sM[2 * i] = re * s;
+            sM[2 * i + 1] = im * s;
+        }
+        __syncthreads();
+        for (int r = 0; r < 4; r++) {
+            const int o = threadIdx.x + r * blockDim.x;
+            if (o >= ntri) break;
+            int n, m;
+            tri_inv(o, n, m);
+            T sr = 0, si = 0;
+            for (int j = 0; j < p; j++)
+                for (int kk = -j; kk <= j; kk++) {
+                    const T mr = sM[2 * full(j, kk)], mi = sM[2 * full(j, kk) + 1];
+                    const int fi = full(j + n, kk + m);
+                    sr += mr * sI[2 * fi] - mi * sI[2 * fi + 1];
+                    si += mr * sI[2 * fi + 1] + mi * sI[2 * fi];
+                }
+            if (n & 1) {
+                sr = -sr;
+                si = -si;
+            }
+            accr[r] += (double)sr;
+            acci[r] += (double)si;
+        }
+    }
+    T *Lc = L + (size_t)c * PP;
+    for (int r = 0; r < 4; r++) {
+        const int o = threadIdx.x + r * blockDim.x;
+        if (o >= ntri) break;
+        int n, m;
+        tri_inv(o, n, m);
+        Lc[re_idx(n, m)] += (T)accr[r];
+        if (m) Lc[im_idx(n, m)] += (T)acci[r];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// L2P: one block per leaf; phi and grad of the far field into far[] (sorted)
+// ---------------------------------------------------------------------------
+template <class T, class P4>
+__global__ void __launch_bounds__(64) l2p_k(int p, const int *__restrict__ leaves, const int *__restrict__ begin,
+                                            const int *__restrict__ end, const int4 *__restrict__ xyz,
+                                            const Box *__restrict__ box, const P4 *__restrict__ xs,
+                                            const T *__restrict__ L, double4_32a *__restrict__ far)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sL = reinterpret_cast<T *>(smem_raw);
+    const int PP = p * p;
+    const int c = leaves[blockIdx.x];
+    for (int i = threadIdx.x; i < PP; i += blockDim.x) sL[i] = L[(size_t)c * PP + i];
+    __syncthreads();
+    double cen[3], w;
+    cell_geom(box, xyz[c], cen, w);
+    const double iw = 1.0 / w;
+    for (int j = begin[c] + threadIdx.x; j < end[c]; j += blockDim.x) {
+        const double4_32a pt = load_pt(xs, j);
+        const T x = (T)((pt.x - cen[0]) * iw), y = (T)((pt.y - cen[1]) * iw), z = (T)((pt.z - cen[2]) * iw);
+        const T r2 = x * x + y * y + z * z;
+        T F = 0, Fz = 0, Gr = 0, Gi = 0;
+        T mre = 1, mim = 0;
+        for (int m = 0; m < p; m++) {
+            if (m > 0) {
+                const T f = T(1) / T(2 * m);
+                const T a = (mre * x - mim * y) * f, b = (mre * y + mim * x) * f;
+                mre = a;
+                mim = b;
+            }
+            const T wm = m ? T(2) : T(1);
+            T p2re = 0, p2im = 0, p1re = 0, p1im = 0;
+            for (int n = m; n < p; n++) {
+                T rre, rim;
+                if (n == m) {
+                    rre = mre;
+                    rim = mim;
+                } else if (n == m + 1) {
+                    rre = z * mre;
+                    rim = z * mim;
+                } else {
+                    const T a = T(2 * n - 1), b = T(1) / T((n + m) * (n - m));
+                    rre = (a * z * p1re - r2 * p2re) * b;
+                    rim = (a * z * p1im - r2 * p2im) * b;
+                }
+                p2re = p1re; p2im = p1im; p1re = rre; p1im = rim;
+                // phi: Re(L_n^m conj(R_n^m)), doubled for m > 0
+                const T lr = sL[re_idx(n, m)], li = m ? sL[im_idx(n, m)] : T(0);
+                F += wm * (lr * rre + li * rim);
+                if (n + 1 < p) {
+                    // d/dz: Re(L_{n+1}^m conj(R_n^m)), doubled for m > 0
+                    const T zr = sL[re_idx(n + 1, m)], zi = m ? sL[im_idx(n + 1, m)] : T(0);
+                    Fz += wm * (zr * rre + zi * rim);
+                    // G = (d_x - i d_y) phi: -L_{n+1}^{m-1} conj(R) ...
+                    T ar, ai;
+                    if (m == 0) {
+                        ar = -sL[re_idx(n + 1, 1)];
+                        ai = sL[im_idx(n + 1, 1)];
+                    } else {
+                        ar = sL[re_idx(n + 1, m - 1)];
+                        ai = (m - 1) ? sL[im_idx(n + 1, m - 1)] : T(0);
+                    }
+                    Gr -= ar * rre + ai * rim;
+                    Gi -= ai * rre - ar * rim;
+                    // ... + conj(L_{n+1}^{m+1} conj(R)) for m >= 1
+                    if (m >= 1) {
+                        const T br = sL[re_idx(n + 1, m + 1)], bi = sL[im_idx(n + 1, m + 1)];
+                        Gr += br * rre + bi * rim;
+                        Gi -= bi * rre - br * rim;
+                    }
+                }
+            }
+        }
+        const double iw2 = iw * iw;
+        far[j] = make_double4_32a((double)F * iw, (double)Gr * iw2, -(double)Gi * iw2, (double)Fz * iw2);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host: tables and orchestration
+// ---------------------------------------------------------------------------
+static int floordiv2(int a) { return a >= 0 ? a / 2 : -((-a + 1) / 2); }
+
+int m2l_tile_size(fmm_ctx *h)
+{
+    if (h->precision == FMM_MIXED && h->engine_req != FMM_M2L_CUDACORE && tensor_m2l_supported(h)) return 128;
+    const int ntri = h->p * (h->p + 1) / 2;
+    int t = std::min(32, (M2L_CC_T * M2L_CC_ACC) / ntri);
+    return std::max(t, 1);
+}
+
+void operators_init(fmm_ctx *h)
+{
+    const int p = h->p, PP = p * p, Q = 2 * p - 1, QQ = Q * Q;
+    const double c = h->cmac;
+    // same-level stencils: v accepted by the MAC, its parent offset rejected
+    const int R = 2 * (int)std::ceil(std::sqrt(3.0 / c)) + 3;
+    std::map<std::tuple<int, int, int>, int> vid;
+    std::vector<std::tuple<int, int, int>> vecs;
+    h->st_off.assign(9, 0);
+    h->st_host.clear();
+    for (int o = 0; o < 8; o++) {
+        const int ox = o & 1, oy = (o >> 1) & 1, oz = (o >> 2) & 1;
+        for (int vx = -R; vx <= R; vx++)
+            for (int vy = -R; vy <= R; vy++)
+                for (int vz = -R; vz <= R; vz++) {
+                    const double d2 = (double)(vx * vx + vy * vy + vz * vz);
+                    if (!(3.0 < c * d2)) continue;
+                    const int ux = floordiv2(ox + vx), uy = floordiv2(oy + vy), uz = floordiv2(oz + vz);
+                    const double u2 = (double)(ux * ux + uy * uy + uz * uz);
+                    if (3.0 < c * u2) continue;
+                    auto key = std::make_tuple(vx, vy, vz);
+                    auto it = vid.find(key);
+                    int id;
+                    if (it == vid.end()) {
+                        id = (int)vecs.size();
+                        vid[key] = id;
+                        vecs.push_back(key);
+                    } else id = it->second;
+                    h->st_host.insert(h->st_host.end(), {vx, vy, vz, id});
+                }
+        h->st_off[o + 1] = (int)(h->st_host.size() / 4);
+    }
+    h->nV = (int)vecs.size();
+    int near = 0;
+    for (int vx = -R; vx <= R; vx++)
+        for (int vy = -R; vy <= R; vy++)
+            for (int vz = -R; vz <= R; vz++)
+                if (!(3.0 < c * (double)(vx * vx + vy * vy + vz * vz))) near++;
+    h->p2p_cap_hint = near;
+
+    // device stencil: int4 entries followed by the 9 octant offsets
+    const int ne = h->st_off[8];
+    std::vector<int> buf(4 * ne + 9);
+    std::copy(h->st_host.begin(), h->st_host.end(), buf.begin());
+    for (int o = 0; o < 9; o++) buf[4 * ne + o] = h->st_off[o];
+    h->st_dev.ensure(sizeof(int) * buf.size());
+    FMM_CUDA_TRY(cudaMemcpy(h->st_dev.p, buf.data(), sizeof(int) * buf.size(), cudaMemcpyHostToDevice));
+
+    // I_n^m(u), u = -v, full storage of degree < Q, per vector
+    {
+        std::vector<double> tre(Q * (Q + 1) / 2), tim(Q * (Q + 1) / 2);
+        std::vector<double> t64((size_t)std::max(h->nV, 1) * 2 * QQ);
+        for (int id = 0; id < h->nV; id++) {
+            auto [vx, vy, vz] = vecs[id];
+            irregular_tri<double>(Q, -(double)vx, -(double)vy, -(double)vz, tre.data(), tim.data());
+            double *dst = t64.data() + (size_t)id * 2 * QQ;
+            for (int n = 0; n < Q; n++)
+                for (int m = -n; m <= n; m++) {
+                    const int am = m < 0 ? -m : m;
+                    double re = tre[tri(n, am)], im = tim[tri(n, am)];
+                    if (m < 0) {
+                        im = -im;
+                        if (am & 1) {
+                            re = -re;
+                            im = -im;
+                        }
+                    }
+                    dst[2 * full(n, m)] = re;
+                    dst[2 * full(n, m) + 1] = im;
+                }
+        }
+        std::vector<float> t32(t64.size());
+        for (size_t i = 0; i < t64.size(); i++) t32[i] = (float)t64[i];
+        h->itab64.ensure(sizeof(double) * t64.size());
+        h->itab32.ensure(sizeof(float) * t32.size());
+        FMM_CUDA_TRY(cudaMemcpy(h->itab64.p, t64.data(), sizeof(double) * t64.size(), cudaMemcpyHostToDevice));
+        FMM_CUDA_TRY(cudaMemcpy(h->itab32.p, t32.data(), sizeof(float) * t32.size(), cudaMemcpyHostToDevice));
+    }
+    // R_n^m(t_o), t_o = (c_child - c_parent) / w_parent = (+-1/4, +-1/4, +-1/4)
+    {
+        std::vector<double> tre(p * (p + 1) / 2), tim(p * (p + 1) / 2);
+        std::vector<double> r64((size_t)8 * 2 * PP);
+        for (int o = 0; o < 8; o++) {
+            const double tx = (o & 1) ? 0.25 : -0.25, ty = (o & 2) ? 0.25 : -0.25, tz = (o & 4) ? 0.25 : -0.25;
+            regular_tri<double>(p, tx, ty, tz, tre.data(), tim.data(), 1);
+            double *dst = r64.data() + (size_t)o * 2 * PP;
+            for (int n = 0; n < p; n++)
+                for (int m = -n; m <= n; m++) {
+                    const int am = m < 0 ? -m : m;
+                    double re = tre[tri(n, am)], im = tim[tri(n, am)];
+                    if (m < 0) {
+                        im = -im;
+                        if (am & 1) {
+                            re = -re;
+                            im = -im;
+                        }
+                    }
+                    dst[2 * full(n, m)] = re;
+                    dst[2 * full(n, m) + 1] = im;
+                }
+        }
+        std::vector<float> r32(r64.size());
+        for (size_t i = 0; i < r64.size(); i++) r32[i] = (float)r64[i];
+        h->rtab64.ensure(sizeof(double) * r64.size());
+        h->rtab32.ensure(sizeof(float) * r32.size());
+        FMM_CUDA_TRY(cudaMemcpy(h->rtab64.p, r64.data(), sizeof(double) * r64.size(), cudaMemcpyHostToDevice));
+        FMM_CUDA_TRY(cudaMemcpy(h->rtab32.p, r32.data(), sizeof(float) * r32.size(), cudaMemcpyHostToDevice));
+    }
+}
+
+template <class T, class P4>
+static void far_field_t(fmm_ctx *h, const P4 *xs, const T *rtab, const T *itab)
+{
+    cudaStream_t s = h->stream;
+    const int p = h->p, PP = p * p, ntri = p * (p + 1) / 2, Q = 2 * p - 1;
+    const int nc = h->ncells;
+    h->Mexp.ensure(sizeof(T) * (size_t)nc * PP);
+    h->Lexp.ensure(sizeof(T) * (size_t)nc * PP);
+    T *M = h->Mexp.as<T>(), *L = h->Lexp.as<T>();
+    const Box *box = h->box.as<Box>();
+    cudaEvent_t *ev = h->tm.ev;
+
+    // P2M
+    FMM_CUDA_TRY(cudaEventRecord(ev[2], s));
+    {
+        int chunk = std::min(64, (int)((48 * 1024) / (sizeof(T) * 2 * ntri)));
+        chunk = std::max(chunk, 1);
+        size_t smem = sizeof(T) * 2 * (size_t)ntri * chunk;
+        p2m_k<T, P4><<<h->nleaves, 64, smem, s>>>(p, h->leaves.as<int>(), h->c_begin.as<int>(), h->c_end.as<int>(),
+                                                  h->c_xyz.as<int4>(), box, xs, M, chunk);
+        count_launch(h);
+        check_launch("p2m");
+    }
+    // M2M, deepest level first
+    FMM_CUDA_TRY(cudaEventRecord(ev[3], s));
+    for (int l = h->depth - 1; l >= 0; l--) {
+        const int ls = h->lvl_start[l], le = h->lvl_start[l + 1];
+        const int64_t nt = (int64_t)(le - ls) * ntri;
+        if (nt == 0) continue;
+        m2m_k<T><<<nblk(nt, 128), 128, 0, s>>>(p, ls, le, h->c_child.as<int>(), h->c_nchild.as<int>(), h->c_xyz.as<int4>(),
+                                               rtab, M);
+        count_launch(h);
+    }
+    check_launch("m2m");
+    // M2L
+    FMM_CUDA_TRY(cudaEventRecord(ev[4], s));
+    FMM_CUDA_TRY(cudaMemsetAsync(L, 0, sizeof(T) * (size_t)nc * PP, s));
+    const int *st_off = reinterpret_cast<const int *>(h->st_dev.as<char>() + sizeof(int4) * h->st_off[8]);
+    if (h->depth >= 2) {
+        if (std::is_same<T, float>::value && h->engine_used == FMM_M2L_TENSOR) {
+            m2l_tensor(h, reinterpret_cast<float *>(L), reinterpret_cast<const float *>(M));
+        } else {
+            const int tile = m2l_tile_size(h);
+            size_t smem = sizeof(T) * 2 * ((size_t)Q * Q + (size_t)tile * PP) + sizeof(int) * 4 * tile;
+            static size_t set_smem[2] = {0, 0};
+            size_t &ss = set_smem[sizeof(T) == 8];
+            if (smem > ss) {
+                FMM_CUDA_TRY(cudaFuncSetAttribute(m2l_cc_k<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                ss = smem;
+            }
+            m2l_cc_k<T><<<h->ntiles_max, M2L_CC_T, smem, s>>>(
+                p, h->m2l_tiles.as<M2LTile>(), reinterpret_cast<const int *>(h->m2l_misc.as<unsigned>() + 24 * (FMM_MAXLEVEL + 1)),
+                h->m2l_tgt.as<int>(), h->c_xyz.as<int4>(), h->c_anchor.as<uint64_t>(), h->lvl_desc.as<LevelDesc>(),
+                h->map_pool.as<int>(), h->st_dev.as<int4>(), st_off, itab, M, L, tile);
+            count_launch(h);
+            check_launch("m2l");
+        }
+    }
+    if (h->n_m2lx > 0) {
+        size_t smem = sizeof(double) * (size_t)Q * (Q + 1) + sizeof(T) * 2 * ((size_t)Q * Q + PP);
+        static size_t set_x[2] = {0, 0};
+        size_t &ss = set_x[sizeof(T) == 8];
+        if (smem > ss) {
+            FMM_CUDA_TRY(cudaFuncSetAttribute(m2lx_k<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            ss = smem;
+        }
+        m2lx_k<T><<<nc, 64, smem, s>>>(p, nc, h->m2lx_ptr.as<int>(), h->m2lx_src.as<int>(), h->c_xyz.as<int4>(), M, L);
+        count_launch(h);
+        check_launch("m2l irregular");
+    }
+    // L2L, top down
+    FMM_CUDA_TRY(cudaEventRecord(ev[5], s));
+    for (int l = 0; l < h->depth; l++) {
+        const int ls = h->lvl_start[l + 1], le = h->lvl_start[l + 2];
+        const int64_t nt = (int64_t)(le - ls) * ntri;
+        if (nt == 0) continue;
+        l2l_k<T><<<nblk(nt, 128), 128, 0, s>>>(p, ls, le, h->c_parent.as<int>(), h->c_xyz.as<int4>(), rtab, L);
+        count_launch(h);
+    }
+    check_launch("l2l");
+    // L2P
+    FMM_CUDA_TRY(cudaEventRecord(ev[6], s));
+    h->far.ensure(sizeof(double4_32a) * (size_t)h->n);
+    l2p_k<T, P4><<<h->nleaves, 64, sizeof(T) * PP, s>>>(p, h->leaves.as<int>(), h->c_begin.as<int>(), h->c_end.as<int>(),
+                                                        h->c_xyz.as<int4>(), box, xs, L, h->far.as<double4_32a>());
+    count_launch(h);
+    check_launch("l2p");
+    FMM_CUDA_TRY(cudaEventRecord(ev[7], s));
+}
+
+void far_field(fmm_ctx *h)
+{
+    if (h->precision == FMM_FP64) {
+        far_field_t<double, double4_32a>(h, h->xs64.as<double4_32a>(), h->rtab64.as<double>(), h->itab64.as<double>());
+    } else if (h->dtype == FMM_F64) {
+        far_field_t<float, double4_32a>(h, h->xs64.as<double4_32a>(), h->rtab32.as<float>(), h->itab32.as<float>());
+    } else {
+        far_field_t<float, float4>(h, h->xs32.as<float4>(), h->rtab32.as<float>(), h->itab32.as<float>());
+    }
+}
+
+}  // namespace fmm

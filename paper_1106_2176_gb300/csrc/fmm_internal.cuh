@@ -1,0 +1,251 @@
+// Internal declarations of the GB300 FMM library (not part of the C ABI).
+//
+// Data layout in HBM (one handle, n particles, C cells, p terms, PP = p*p):
+//   sorted particles   xs64[n] double4_32a (x, y, z, q)      FP64 path, FP64 input
+//                      xs32[n] float4  (x, y, z, q)      mixed path (P2P)
+//   cells (SoA, breadth first, key order within a level)
+//                      level, begin, end, child, nchild, parent: int32[C]
+//                      anchor: uint64[C] (Morton key of the lowest corner)
+//                      xyz: int4[C] (lowest corner in grid units, level)
+//   expansions         Mexp, Lexp: real[C][PP], packed real layout (degree n at
+//                      offset n*n: Re(n,0), Re(n,1), Im(n,1), ..., Re(n,n), Im(n,n)),
+//                      scaled by the cell width w: M_n^m / w^n, L_n^m w^(n+1)
+//   lists              P2P: CSR by target cell, int32 sources ascending
+//                      M2L between cells of different levels: CSR, int32
+//                      M2L between cells of one level: implicit, the stencil
+//                      of the target's octant applied through a per-level map
+//   results            far[n], near[n]: double4_32a (phi, dphi/dx, dphi/dy, dphi/dz)
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/fmm.h"
+
+#define FMM_MAXP 20
+#define FMM_MAXLEVEL 21
+#define FMM_DENSE_MAP_MAXLEVEL 8  // levels with 8^l <= 2^24 get a dense lattice map
+
+namespace fmm {
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+struct Error {
+    int code;
+    std::string msg;
+};
+
+void set_error(const std::string &msg);
+const std::string &get_error();
+
+#define FMM_CUDA_TRY(expr)                                                                 \
+    do {                                                                                   \
+        cudaError_t e_ = (expr);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            throw ::fmm::Error{FMM_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)}; \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// device memory owned by a handle; grows on demand, never shrinks
+// ---------------------------------------------------------------------------
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    void ensure(size_t bytes);  // may reallocate (contents are not kept)
+    void ensure_keep(size_t bytes, size_t used, cudaStream_t s);  // keeps the first `used` bytes
+    void release();
+    template <class T>
+    T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+struct PinnedBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    void ensure(size_t bytes);
+    void release();
+    template <class T>
+    T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+// root cube, computed on the device
+struct Box {
+    unsigned long long enc_lo[3], enc_hi[3];  // order-preserving encodings of min / max
+    double origin[3];
+    double R0;     // half width of the root cube
+    double s;      // 2^21 / (2 R0)
+    double h;      // 2 R0 / 2^21 (grid spacing)
+    int nonfinite; // set when a coordinate is NaN or infinite
+    int pad;
+};
+
+// per-level lookup from lattice position to cell index (M2L stencil)
+struct LevelDesc {
+    int start, end;      // cell index range of the level
+    long long map_off;   // offset of a dense map (8^l int32) in the map pool, or -1
+};
+
+// M2L tile: up to TILE target cells of one level and one octant
+struct M2LTile {
+    int start;   // first entry in the target list
+    int count;
+    int level;
+    int octant;
+};
+
+// counters written by the traversal and read back by the host
+struct TravCounters {
+    unsigned long long n_p2p, n_m2lx, n_next, n_m2l_implicit;
+};
+
+struct Timers {
+    cudaEvent_t ev[16];
+    bool ok = false;
+};
+
+}  // namespace fmm
+
+struct fmm_ctx {
+    // parameters
+    int64_t Nmax = 0;
+    int p = 0;
+    double theta = 0, cmac = 0;  // cmac = fl(theta * theta)
+    int ncrit = 0;
+    int precision_req = FMM_FP64;
+    int engine_req = FMM_M2L_AUTO;
+    // device
+    int dev = 0, nsm = 0, cc_major = 0, cc_minor = 0;
+    cudaStream_t stream = nullptr;  // caller's stream (or legacy default)
+    cudaStream_t s2 = nullptr;      // private stream for P2P concurrency
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    fmm::Timers tm;
+    int64_t launches = 0;
+
+    // state of the last build
+    bool built = false, evaluated = false;
+    int64_t n = 0;
+    int dtype = FMM_F64;
+    bool host_mem = false;
+    int precision = FMM_FP64;
+    int engine_used = 0;
+    int ncells = 0, depth = 0, nleaves = 0;
+    std::vector<int> lvl_start;  // cells of level l are [lvl_start[l], lvl_start[l+1])
+    int64_t n_p2p = 0, n_m2lx = 0, n_m2l_implicit = 0, n_interactions = 0;
+    int ntiles_max = 0;
+    int p2p_cap_hint = 0;       // near-field stencil size (P2P sources of a leaf in a uniform tree)
+    double ms_build = 0;
+
+    // stencil of same-level M2L (host copy and device copy)
+    int nV = 0;                 // distinct translation vectors over all octants
+    std::vector<int> st_off;    // st_off[o] .. st_off[o+1]: entries of octant o
+    std::vector<int> st_host;   // 4 ints per entry: vx, vy, vz (source - target), vector id
+    fmm::DevBuf st_dev;         // int4 per entry
+    fmm::DevBuf itab64, itab32; // I_n^m(u), u = -v, full complex storage of degree < 2p-1, per vector
+    fmm::DevBuf rtab64, rtab32; // R_n^m(t_o), 8 child offsets, full complex storage of degree < p
+    fmm::DevBuf ttab;           // tensor-core M2L operators (split TF32 images), per vector
+    size_t ttab_stride = 0;     // bytes per vector in ttab
+
+    // workspaces
+    fmm::DevBuf box;
+    fmm::DevBuf x_in, q_in;             // staging of host inputs
+    fmm::DevBuf keys, keys2, idx, idx2; // Morton keys and permutation (radix sort ping-pong)
+    fmm::DevBuf hist, scan_tmp;
+    fmm::DevBuf xs64, xs32;
+    fmm::DevBuf c_level, c_anchor, c_begin, c_end, c_child, c_nchild, c_parent, c_xyz;
+    fmm::DevBuf split_cnt, split_off, split_bnd;
+    fmm::DevBuf leaves;
+    fmm::DevBuf frontA, frontB;
+    fmm::DevBuf p2p_pairs, m2lx_pairs;
+    fmm::DevBuf pair_keys, pair_keys2, pair_vals, pair_vals2;
+    fmm::DevBuf p2p_ptr, p2p_src, m2lx_ptr, m2lx_src, row_cnt;
+    fmm::DevBuf counters;
+    fmm::DevBuf lvl_desc, map_pool;
+    fmm::DevBuf m2l_tgt, m2l_tiles, m2l_misc;
+    fmm::DevBuf Mexp, Lexp;
+    fmm::DevBuf far, near;
+    fmm::DevBuf out_phi, out_grad;      // staging of host outputs
+    fmm::DevBuf direct_part;
+    fmm::PinnedBuf hpin;
+
+    ~fmm_ctx();
+};
+
+namespace fmm {
+
+// launch bookkeeping: every kernel launch of the library goes through this
+inline void count_launch(fmm_ctx *h) { h->launches++; }
+void check_launch(const char *what);
+
+// tree.cu
+void tree_build(fmm_ctx *h, const void *x, const void *q, int64_t n, int dtype_base);
+void tree_export(fmm_ctx *h, uint64_t *keys, int32_t *perm, int32_t *level, uint64_t *anchor,
+                 int32_t *begin, int32_t *end, int32_t *child, int32_t *nchild, int32_t *parent,
+                 int64_t *p2p_ptr, int32_t *p2p_idx, int64_t *m2l_ptr, int32_t *m2l_idx, double *box);
+int64_t tree_m2l_total(fmm_ctx *h);
+int m2l_tile_size(fmm_ctx *h);
+void scan_exclusive_u32(fmm_ctx *h, const unsigned *in, unsigned *out, int64_t count, unsigned *total_dev,
+                        cudaStream_t s);
+
+// expansions.cu
+void operators_init(fmm_ctx *h);  // stencil, I tables, R tables
+void far_field(fmm_ctx *h);       // P2M, M2M, M2L, L2L, L2P into h->far
+
+// m2l_tc.cu
+void tensor_tables_init(fmm_ctx *h);
+bool tensor_m2l_supported(fmm_ctx *h);
+void m2l_tensor(fmm_ctx *h, float *L, const float *M);
+
+// p2p.cu
+void near_field(fmm_ctx *h, cudaStream_t s);  // P2P into h->near
+void combine_unsort(fmm_ctx *h, void *phi, void *grad);
+void direct_sum(fmm_ctx *h, const double *x, const double *q, int64_t n, const int64_t *tidx, int64_t nt,
+                double *phi, double *grad);
+
+// packed real layout of an order-p expansion
+__host__ __device__ inline int re_idx(int n, int m) { return n * n + (m == 0 ? 0 : 2 * m - 1); }
+__host__ __device__ inline int im_idx(int n, int m) { return n * n + 2 * m; }
+
+}  // namespace fmm
+
+namespace fmm {
+
+// 21-bit integer -> every third bit of a 63-bit word (bit b -> bit 3b)
+__host__ __device__ inline uint64_t spread3(uint32_t v)
+{
+    uint64_t x = v & 0x1fffffu;
+    x = (x | (x << 32)) & 0x001f00000000ffffull;
+    x = (x | (x << 16)) & 0x001f0000ff0000ffull;
+    x = (x | (x << 8)) & 0x100f00f00f00f00full;
+    x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+    x = (x | (x << 2)) & 0x1249249249249249ull;
+    return x;
+}
+
+__host__ __device__ inline uint64_t morton3(uint32_t x, uint32_t y, uint32_t z)
+{
+    return spread3(x) | (spread3(y) << 1) | (spread3(z) << 2);
+}
+
+// Cell at lattice position (x, y, z) of level l, or -1.
+__device__ inline int level_lookup(const LevelDesc &L, const int *__restrict__ map_pool,
+                                   const uint64_t *__restrict__ anchor, int l, int x, int y, int z)
+{
+    const int side = 1 << l;
+    if (x < 0 || y < 0 || z < 0 || x >= side || y >= side || z >= side) return -1;
+    const uint64_t k = morton3((uint32_t)x, (uint32_t)y, (uint32_t)z);
+    if (L.map_off >= 0) return map_pool[L.map_off + (long long)k];
+    const uint64_t a = k << (3 * (FMM_MAXLEVEL - l));
+    int lo = L.start, hi = L.end;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (anchor[mid] < a) lo = mid + 1;
+        else hi = mid;
+    }
+    return (lo < L.end && anchor[lo] == a) ? lo : -1;
+}
+
+}  // namespace fmm

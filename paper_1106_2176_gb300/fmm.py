@@ -1,0 +1,263 @@
+"""Python binding of the C ABI in include/fmm.h (ctypes; argument marshalling only).
+
+Every step of the FMM runs in the CUDA kernels of libfmm.so; this module only
+passes pointers, sizes and the current CUDA stream. There is no CPU path: if the
+library is missing or no sm_103 GPU is present, the calls raise.
+
+    from paper_1106_2176_gb300 import FMM
+    f = FMM(N, p=8, theta=0.5, ncrit=64, precision="mixed")
+    f.build(x, q)            # torch CUDA tensors (n,3) and (n,), float32 or float64
+    phi, grad = f.evaluate() # torch CUDA tensors in the input order
+
+Host numpy arrays are accepted too (the library copies them; FMM_HOST_MEM).
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIBPATH = os.path.join(_HERE, "libfmm.so")
+_HEADER = os.path.join(_HERE, "..", "include", "fmm.h")
+
+FMM_OK, FMM_EINVAL, FMM_ENOMEM, FMM_ESTATE, FMM_ECUDA, FMM_ENONFINITE, FMM_ENODEV = 0, -1, -2, -3, -4, -5, -6
+FMM_F32, FMM_F64, FMM_HOST_MEM = 0, 1, 0x100
+FMM_FP64, FMM_MIXED = 0, 1
+FMM_M2L_AUTO, FMM_M2L_TENSOR, FMM_M2L_CUDACORE = 0, 1, 2
+
+_ERRNAMES = {FMM_EINVAL: "FMM_EINVAL", FMM_ENOMEM: "FMM_ENOMEM", FMM_ESTATE: "FMM_ESTATE",
+             FMM_ECUDA: "FMM_ECUDA", FMM_ENONFINITE: "FMM_ENONFINITE", FMM_ENODEV: "FMM_ENODEV"}
+
+
+class FMMError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (_ERRNAMES.get(code, "FMM_E?"), code, msg))
+        self.code = code
+
+
+class fmm_stats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("ncells", ctypes.c_int64), ("nleaves", ctypes.c_int64),
+                ("depth", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("n_p2p_pairs", ctypes.c_int64), ("n_m2l_pairs", ctypes.c_int64),
+                ("n_m2l_irregular", ctypes.c_int64), ("n_interactions", ctypes.c_int64),
+                ("n_stencil", ctypes.c_int64), ("m2l_engine", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("ms_build", ctypes.c_double), ("ms_evaluate", ctypes.c_double),
+                ("ms_p2m", ctypes.c_double), ("ms_m2m", ctypes.c_double), ("ms_m2l", ctypes.c_double),
+                ("ms_l2l", ctypes.c_double), ("ms_l2p", ctypes.c_double), ("ms_p2p", ctypes.c_double),
+                ("ms_combine", ctypes.c_double), ("kernel_launches", ctypes.c_int64)]
+
+
+class fmm_tree_sizes(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("ncells", ctypes.c_int64), ("n_p2p", ctypes.c_int64),
+                ("n_m2l", ctypes.c_int64), ("depth", ctypes.c_int32), ("p", ctypes.c_int32)]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+
+
+def declared_symbols():
+    """Names of the functions include/fmm.h declares."""
+    src = open(_HEADER).read()
+    return sorted(set(re.findall(r"^\s*FMM_API\s+(?:int|const char \*)\s*(fmm_\w+)\s*\(", src, re.M)))
+
+
+def lib():
+    """Load libfmm.so (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIBPATH):
+        raise RuntimeError("libfmm.so is not built; run paper_1106_2176_gb300._build.build()")
+    L = ctypes.CDLL(_LIBPATH)
+    i64, i32, d = ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    L.fmm_create.argtypes = [i64, i32, d, i32, ctypes.POINTER(_vp)]
+    L.fmm_set_precision.argtypes = [_vp, i32]
+    L.fmm_set_m2l_engine.argtypes = [_vp, i32]
+    L.fmm_set_stream.argtypes = [_vp, _vp]
+    L.fmm_build.argtypes = [_vp, _vp, _vp, i64, i32]
+    L.fmm_evaluate.argtypes = [_vp, _vp, _vp]
+    L.fmm_get_stats.argtypes = [_vp, ctypes.POINTER(fmm_stats)]
+    L.fmm_get_tree_sizes.argtypes = [_vp, ctypes.POINTER(fmm_tree_sizes)]
+    L.fmm_export_tree.argtypes = [_vp] + [_vp] * 14
+    L.fmm_export_expansions.argtypes = [_vp, _vp, _vp]
+    L.fmm_direct.argtypes = [_vp, _vp, _vp, i64, _vp, i64, _vp, _vp]
+    L.fmm_destroy.argtypes = [_vp]
+    L.fmm_last_error.argtypes = [_vp]
+    L.fmm_last_error.restype = ctypes.c_char_p
+    for name in declared_symbols():
+        getattr(L, name).restype = getattr(L, name).restype if name == "fmm_last_error" else ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(rc, h=None):
+    if rc != FMM_OK:
+        msg = lib().fmm_last_error(h).decode(errors="replace")
+        raise FMMError(rc, msg)
+
+
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+def _stream_ptr():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class FMM:
+    """Handle of one FMM configuration (N, p, theta, ncrit) on the current GPU."""
+
+    def __init__(self, N, p=8, theta=0.5, ncrit=64, precision="fp64", m2l_engine="auto"):
+        self._h = _vp()
+        _check(lib().fmm_create(int(N), int(p), float(theta), int(ncrit), ctypes.byref(self._h)))
+        self.N, self.p, self.theta, self.ncrit = int(N), int(p), float(theta), int(ncrit)
+        self.set_precision(precision)
+        self.set_m2l_engine(m2l_engine)
+        self._n = 0
+        self._dtype = None
+        self._host = False
+
+    # -- configuration -------------------------------------------------------
+    def set_precision(self, precision):
+        mode = {"fp64": FMM_FP64, "mixed": FMM_MIXED}[precision]
+        _check(lib().fmm_set_precision(self._h, mode), self._h)
+        self.precision = precision
+
+    def set_m2l_engine(self, engine):
+        e = {"auto": FMM_M2L_AUTO, "tensor": FMM_M2L_TENSOR, "cudacore": FMM_M2L_CUDACORE}[engine]
+        _check(lib().fmm_set_m2l_engine(self._h, e), self._h)
+
+    # -- the two calls of the method ------------------------------------------
+    def build(self, x, q):
+        """x: (n, 3), q: (n,); torch CUDA tensors or host numpy arrays, float32 or float64."""
+        if _is_torch(x):
+            import torch
+            if x.dtype not in (torch.float32, torch.float64) or q.dtype != x.dtype:
+                raise TypeError("x and q must both be float32 or both float64")
+            if not (x.is_cuda and q.is_cuda):
+                raise TypeError("torch tensors must be on the GPU; pass numpy arrays for host memory")
+            x = x.contiguous()
+            q = q.contiguous()
+            dt = FMM_F64 if x.dtype == torch.float64 else FMM_F32
+            self._keep = (x, q)
+            _check(lib().fmm_set_stream(self._h, _stream_ptr()), self._h)
+            _check(lib().fmm_build(self._h, _vp(x.data_ptr()), _vp(q.data_ptr()), x.shape[0], dt), self._h)
+            self._host = False
+            self._torch_dtype = x.dtype
+            self._device = x.device
+        else:
+            x = np.ascontiguousarray(x)
+            if x.dtype not in (np.float32, np.float64):
+                x = x.astype(np.float64)
+            q = np.ascontiguousarray(q, dtype=x.dtype)
+            dt = FMM_F64 if x.dtype == np.float64 else FMM_F32
+            self._keep = (x, q)
+            _check(lib().fmm_set_stream(self._h, None), self._h)
+            _check(lib().fmm_build(self._h, _vp(x.ctypes.data), _vp(q.ctypes.data), x.shape[0], dt | FMM_HOST_MEM),
+                   self._h)
+            self._host = True
+            self._np_dtype = x.dtype
+        self._n = x.shape[0]
+        self._dtype = dt
+        return self
+
+    def evaluate(self, phi=None, grad=None):
+        """Potential and gradient at every particle of the last build, input order."""
+        n = self._n
+        if self._host:
+            phi = np.empty(n, dtype=self._np_dtype) if phi is None else phi
+            grad = np.empty((n, 3), dtype=self._np_dtype) if grad is None else grad
+            _check(lib().fmm_evaluate(self._h, _vp(phi.ctypes.data), _vp(grad.ctypes.data)), self._h)
+            return phi, grad
+        import torch
+        if phi is None:
+            phi = torch.empty(n, dtype=self._torch_dtype, device=self._device)
+        if grad is None:
+            grad = torch.empty((n, 3), dtype=self._torch_dtype, device=self._device)
+        _check(lib().fmm_set_stream(self._h, _stream_ptr()), self._h)
+        _check(lib().fmm_evaluate(self._h, _vp(phi.data_ptr()), _vp(grad.data_ptr())), self._h)
+        return phi, grad
+
+    # -- introspection ---------------------------------------------------------
+    def stats(self):
+        s = fmm_stats()
+        _check(lib().fmm_get_stats(self._h, ctypes.byref(s)), self._h)
+        return {k: getattr(s, k) for k, _ in fmm_stats._fields_}
+
+    def tree_sizes(self):
+        s = fmm_tree_sizes()
+        _check(lib().fmm_get_tree_sizes(self._h, ctypes.byref(s)), self._h)
+        return {k: getattr(s, k) for k, _ in fmm_tree_sizes._fields_}
+
+    def export_tree(self):
+        sz = self.tree_sizes()
+        n, c = sz["n"], sz["ncells"]
+        out = dict(keys=np.zeros(n, np.uint64), perm=np.zeros(n, np.int32), level=np.zeros(c, np.int32),
+                   anchor=np.zeros(c, np.uint64), begin=np.zeros(c, np.int32), end=np.zeros(c, np.int32),
+                   child=np.zeros(c, np.int32), nchild=np.zeros(c, np.int32), parent=np.zeros(c, np.int32),
+                   p2p_ptr=np.zeros(c + 1, np.int64), p2p_idx=np.zeros(max(sz["n_p2p"], 1), np.int32),
+                   m2l_ptr=np.zeros(c + 1, np.int64), m2l_idx=np.zeros(max(sz["n_m2l"], 1), np.int32),
+                   box=np.zeros(4))
+        order = ["keys", "perm", "level", "anchor", "begin", "end", "child", "nchild", "parent", "p2p_ptr",
+                 "p2p_idx", "m2l_ptr", "m2l_idx", "box"]
+        _check(lib().fmm_export_tree(self._h, *[_vp(out[k].ctypes.data) for k in order]), self._h)
+        out["p2p_idx"] = out["p2p_idx"][: sz["n_p2p"]]
+        out["m2l_idx"] = out["m2l_idx"][: sz["n_m2l"]]
+        return out
+
+    def export_expansions(self):
+        sz = self.tree_sizes()
+        M = np.zeros((sz["ncells"], self.p * self.p))
+        L = np.zeros((sz["ncells"], self.p * self.p))
+        _check(lib().fmm_export_expansions(self._h, _vp(M.ctypes.data), _vp(L.ctypes.data)), self._h)
+        return M, L
+
+    def direct(self, x, q, targets=None):
+        """FP64 direct sum on the GPU (torch CUDA float64 tensors); targets: int64 indices or None."""
+        import torch
+        x = x.to(torch.float64).contiguous()
+        q = q.to(torch.float64).contiguous()
+        n = x.shape[0]
+        if targets is None:
+            nt, tp = n, None
+        else:
+            targets = targets.to(device=x.device, dtype=torch.int64).contiguous()
+            nt, tp = targets.shape[0], _vp(targets.data_ptr())
+        phi = torch.empty(nt, dtype=torch.float64, device=x.device)
+        grad = torch.empty((nt, 3), dtype=torch.float64, device=x.device)
+        _check(lib().fmm_set_stream(self._h, _stream_ptr()), self._h)
+        _check(lib().fmm_direct(self._h, _vp(x.data_ptr()), _vp(q.data_ptr()), n, tp, nt, _vp(phi.data_ptr()),
+                                _vp(grad.data_ptr())), self._h)
+        return phi, grad
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().fmm_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def unscale(M, L, level, R0, p):
+    """Turn exported scaled real expansions into complex full-storage ones
+    (entry n*n + n + m), multiplying back by the cell widths w = 2 R0 / 2^level."""
+    C = M.shape[0]
+    w = 2.0 * R0 / (2.0 ** np.asarray(level, dtype=np.float64))
+    outM = np.zeros((C, p * p), complex)
+    outL = np.zeros((C, p * p), complex)
+    for n in range(p):
+        for m in range(0, n + 1):
+            re = n * n + (0 if m == 0 else 2 * m - 1)
+            for X, out, sc in ((M, outM, w ** n), (L, outL, w ** (-(n + 1)))):
+                v = X[:, re] + (1j * X[:, n * n + 2 * m] if m else 0.0)
+                v = v * sc
+                out[:, n * n + n + m] = v
+                out[:, n * n + n - m] = (-1) ** m * np.conj(v)
+    return outM, outL

@@ -1,0 +1,43 @@
+"""Helpers shared by the GPU tests: build the library once, move inputs to the
+device, compare against the oracle."""
+import numpy as np
+import pytest
+
+from paper_1106_2176_gb300 import _build
+
+
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+_built = False
+
+
+def ensure_built():
+    global _built
+    if not _built:
+        _build.build()
+        _built = True
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def run_fmm(x, q, p, theta, ncrit, precision="fp64", dtype=np.float64, engine="auto"):
+    """FMM through the C ABI on device tensors; returns (phi, grad, handle)."""
+    torch = torch_cuda()
+    ensure_built()
+    from paper_1106_2176_gb300 import FMM
+    xt = torch.tensor(np.asarray(x, dtype=dtype), device="cuda")
+    qt = torch.tensor(np.asarray(q, dtype=dtype), device="cuda")
+    f = FMM(len(q), p=p, theta=theta, ncrit=ncrit, precision=precision, m2l_engine=engine)
+    f.build(xt, qt)
+    phi, grad = f.evaluate()
+    torch.cuda.synchronize()
+    return phi.cpu().numpy().astype(np.float64), grad.cpu().numpy().astype(np.float64), f

@@ -1,0 +1,56 @@
+"""The C-ABI library builds, loads and exports every entry point include/fmm.h
+declares; argument checks that need no GPU."""
+import ctypes
+import os
+
+import pytest
+
+from paper_1106_2176_gb300 import _build, fmm
+
+from conftest import gpu_available
+
+
+@pytest.fixture(scope="module")
+def L():
+    _build.build()
+    return fmm.lib()
+
+
+def test_header_declares_the_boundary():
+    names = fmm.declared_symbols()
+    for required in ("fmm_create", "fmm_build", "fmm_evaluate", "fmm_destroy", "fmm_set_precision",
+                     "fmm_set_stream", "fmm_get_stats", "fmm_export_tree", "fmm_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(L):
+    for name in fmm.declared_symbols():
+        assert hasattr(L, name), name
+
+
+def test_library_is_sm103a_only():
+    # the build passes one -gencode: compute_103a -> sm_103a
+    assert _build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+@pytest.mark.parametrize("args", [(0, 8, 0.5, 64), (100, 0, 0.5, 64), (100, 21, 0.5, 64),
+                                  (100, 8, 0.0, 64), (100, 8, 1.0, 64), (100, 8, float("nan"), 64),
+                                  (100, 8, 0.5, 0)])
+def test_create_rejects_bad_arguments(L, args):
+    h = ctypes.c_void_p()
+    rc = L.fmm_create(*args, ctypes.byref(h))
+    assert rc == fmm.FMM_EINVAL and not h.value
+    assert L.fmm_last_error(None)
+
+
+def test_null_handle_is_rejected(L):
+    assert L.fmm_build(None, None, None, 1, 0) == fmm.FMM_EINVAL
+    assert L.fmm_evaluate(None, None, None) == fmm.FMM_EINVAL
+    assert L.fmm_destroy(None) == fmm.FMM_EINVAL
+
+
+@pytest.mark.skipif(gpu_available(), reason="checks the no-device path")
+def test_create_without_device_fails_cleanly(L):
+    h = ctypes.c_void_p()
+    rc = L.fmm_create(1000, 8, 0.5, 64, ctypes.byref(h))
+    assert rc in (fmm.FMM_ENODEV, fmm.FMM_ECUDA) and not h.value

@@ -1,0 +1,158 @@
+"""GPU FMM against the oracle: FP64 parity <= 1e-12 relative L2 at the same
+p, theta, ncrit (Sec. 2.1 operators, Fig. flow_chart order); mixed precision
+within the FP64 FMM's own truncation error plus 2e-6 of the FP64 direct sum."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1106_2176_gb300 import inputs, unscale
+
+from gpu_common import ensure_built, rel, run_fmm, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+MIXED_SLACK = 2e-6
+
+
+@pytest.fixture(scope="module")
+def cube16k():
+    x, q = inputs.uniform_cube(16384, 1)
+    return x, q, oracle.fmm(x, q, 6, 0.5, 64), oracle.direct(x, q)
+
+
+def test_fp64_matches_oracle_small_config(cube16k):
+    # N = 16384, p = 6, theta = 0.5, ncrit = 64, FP64 throughout
+    x, q, (po, go), _ = cube16k
+    phi, grad, _ = run_fmm(x, q, 6, 0.5, 64)
+    assert rel(phi, po) <= FP64_TOL and rel(grad, go) <= FP64_TOL
+
+
+def test_fp64_expansions_match_oracle():
+    x, q = inputs.uniform_cube(6000, 2)
+    P = 5
+    phi, grad, f = run_fmm(x, q, P, 0.5, 16)
+    T = oracle.Tree(x, 16, 0.5)
+    _, _, Mo, Lo = T.evaluate(q, P, expansions=True)
+    Ms, Ls = f.export_expansions()
+    t = f.export_tree()
+    Mg, Lg = unscale(Ms, Ls, t["level"], t["box"][3], P)
+    assert np.max(np.abs(Mg - Mo)) <= 1e-12 * np.max(np.abs(Mo))
+    # local expansions per cell, relative to each cell's scale
+    sc = np.max(np.abs(Lo), axis=1, keepdims=True) + 1e-300
+    assert np.max(np.abs(Lg - Lo) / sc) <= 1e-11
+
+
+@pytest.mark.parametrize("P,theta,ncrit,gen", [(1, 0.5, 32, "uniform"), (2, 0.5, 8, "uniform"), (10, 0.4, 64, "uniform"),
+                                               (8, 0.7, 16, "plummer"), (4, 0.3, 4, "plummer"), (14, 0.5, 64, "uniform")])
+def test_fp64_matches_oracle_variants(P, theta, ncrit, gen):
+    x, q = getattr(inputs, "uniform_cube" if gen == "uniform" else "plummer")(8000, 11)
+    po, go = oracle.fmm(x, q, P, theta, ncrit)
+    phi, grad, _ = run_fmm(x, q, P, theta, ncrit)
+    assert rel(phi, po) <= FP64_TOL and rel(grad, go) <= FP64_TOL
+
+
+def test_fp64_float32_input():
+    x, q = inputs.uniform_cube(10000, 12, dtype=np.float32)
+    po, go = oracle.fmm(x.astype(np.float64), q.astype(np.float64), 6, 0.5, 32)
+    phi, grad, _ = run_fmm(x, q, 6, 0.5, 32, precision="fp64", dtype=np.float32)
+    # outputs are rounded to float32
+    assert rel(phi, po) <= 1e-7 and rel(grad, go) <= 1e-7
+
+
+def test_small_theta_is_direct_sum():
+    x, q = inputs.uniform_cube(3000, 13)
+    pd, gd = oracle.direct(x, q)
+    phi, grad, f = run_fmm(x, q, 3, 0.001, 32)
+    assert f.stats()["n_m2l_pairs"] == 0
+    assert rel(phi, pd) <= 1e-13 and rel(grad, gd) <= 1e-13
+
+
+def test_single_and_coincident_particles():
+    for x in (np.array([[0.1, 0.2, 0.3]]), np.tile([[0.5, 0.5, 0.5]], (40, 1))):
+        q = np.linspace(1, 2, len(x))
+        phi, grad, _ = run_fmm(x, q, 4, 0.5, 8)
+        assert np.all(phi == 0) and np.all(grad == 0)
+
+
+def test_mixed_within_truncation_error(cube16k):
+    x, q, (po, go), (pd, gd) = cube16k
+    e64 = rel(po, pd), rel(go, gd)
+    phi, grad, _ = run_fmm(x, q, 6, 0.5, 64, precision="mixed", dtype=np.float64)
+    assert rel(phi, pd) <= e64[0] + MIXED_SLACK
+    assert rel(grad, gd) <= e64[1] + MIXED_SLACK
+
+
+def test_mixed_float32_inputs_precision_config():
+    # N = 10^5 uniform, p = 10, theta = 0.4 (a reduced version of the 10^6 case)
+    x, q = inputs.uniform_cube(100000, 1, dtype=np.float32)
+    x64, q64 = x.astype(np.float64), q.astype(np.float64)
+    t = inputs.sample_targets(100000, 1024, seed=2)
+    pd, gd = oracle.direct(x64, q64, targets=t)
+    p64, g64, _ = run_fmm(x, q, 10, 0.4, 64, precision="fp64", dtype=np.float64)
+    pm, gm, _ = run_fmm(x, q, 10, 0.4, 64, precision="mixed", dtype=np.float32)
+    assert rel(pm[t], pd) <= rel(p64[t], pd) + MIXED_SLACK
+    assert rel(gm[t], gd) <= rel(g64[t], gd) + MIXED_SLACK
+
+
+def test_direct_sum_kernel_matches_oracle():
+    torch = torch_cuda()
+    ensure_built()
+    from paper_1106_2176_gb300 import FMM
+    x, q = inputs.uniform_cube(20000, 14)
+    t = inputs.sample_targets(20000, 700, seed=3)
+    f = FMM(10, p=2)
+    pg, gg = f.direct(torch.tensor(x, device="cuda"), torch.tensor(q, device="cuda"), torch.tensor(t, device="cuda"))
+    pd, gd = oracle.direct(x, q, targets=t)
+    assert rel(pg.cpu().numpy(), pd) <= 1e-14 and rel(gg.cpu().numpy(), gd) <= 1e-14
+
+
+def test_host_memory_path_matches_device_path():
+    ensure_built()
+    from paper_1106_2176_gb300 import FMM
+    x, q = inputs.uniform_cube(5000, 15)
+    phi_d, grad_d, _ = run_fmm(x, q, 6, 0.5, 32)
+    f = FMM(5000, p=6, theta=0.5, ncrit=32)
+    f.build(x, q)
+    phi_h, grad_h = f.evaluate()
+    assert np.array_equal(phi_h, phi_d) and np.array_equal(grad_h, grad_d)
+
+
+def test_errors_are_status_codes():
+    torch = torch_cuda()
+    ensure_built()
+    from paper_1106_2176_gb300 import FMM, FMMError, fmm
+    f = FMM(100, p=4)
+    with pytest.raises(FMMError) as e:
+        f.evaluate()
+    assert e.value.code == fmm.FMM_ESTATE
+    x = torch.zeros((200, 3), dtype=torch.float64, device="cuda")
+    q = torch.ones(200, dtype=torch.float64, device="cuda")
+    with pytest.raises(FMMError) as e:
+        f.build(x, q)
+    assert e.value.code == fmm.FMM_EINVAL
+    x = torch.rand((50, 3), dtype=torch.float64, device="cuda")
+    x[7, 1] = float("nan")
+    with pytest.raises(FMMError) as e:
+        f.build(x, q[:50])
+    assert e.value.code == fmm.FMM_ENONFINITE
+    # the handle stays usable after errors
+    x = torch.rand((50, 3), dtype=torch.float64, device="cuda")
+    f.build(x, q[:50])
+    phi, grad = f.evaluate()
+    assert torch.isfinite(phi).all()
+
+
+def test_rebuild_same_handle_is_deterministic():
+    x, q = inputs.uniform_cube(20000, 16)
+    torch = torch_cuda()
+    ensure_built()
+    from paper_1106_2176_gb300 import FMM
+    f = FMM(20000, p=6, precision="mixed")
+    xt, qt = torch.tensor(x, device="cuda"), torch.tensor(q, device="cuda")
+    outs = []
+    for _ in range(3):
+        f.build(xt, qt)
+        outs.append([t.cpu().numpy() for t in f.evaluate()])
+    for o in outs[1:]:
+        assert np.array_equal(o[0], outs[0][0]) and np.array_equal(o[1], outs[0][1])

@@ -1,0 +1,84 @@
+"""GPU octree and interaction lists, bit for bit against the oracle (Sec. 2.1
+near/far split, Sec. 2.2 Morton-indexed boxes, Sec. 5 sorted indices)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1106_2176_gb300 import inputs
+
+from gpu_common import ensure_built, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu_tree(x, q, ncrit, theta, dtype=np.float64, precision="fp64"):
+    torch = torch_cuda()
+    ensure_built()
+    from paper_1106_2176_gb300 import FMM
+    f = FMM(len(q), p=4, theta=theta, ncrit=ncrit, precision=precision)
+    f.build(torch.tensor(np.asarray(x, dtype), device="cuda"), torch.tensor(np.asarray(q, dtype), device="cuda"))
+    return f.export_tree(), f
+
+
+def compare(x, q, ncrit, theta, dtype=np.float64):
+    g, f = gpu_tree(x, q, ncrit, theta, dtype)
+    # the oracle sees exactly the values the GPU saw
+    xo = np.asarray(x, dtype).astype(np.float64)
+    T = oracle.Tree(xo, ncrit, theta)
+    ic, key, perm = T.particles()
+    org, R0 = T.box()
+    assert np.array_equal(g["box"][:3], org) and g["box"][3] == R0
+    assert np.array_equal(g["keys"], key)
+    assert np.array_equal(g["perm"].astype(np.int64), perm)
+    c = T.cells()
+    assert len(g["level"]) == T.ncells
+    for k in ("level", "anchor", "begin", "end", "child", "nchild", "parent"):
+        assert np.array_equal(g[k].astype(np.int64), c[k].astype(np.int64)), k
+    (pp, pi), (mp, mi) = T.lists()
+    assert np.array_equal(g["p2p_ptr"], pp) and np.array_equal(g["p2p_idx"].astype(np.int64), pi)
+    assert np.array_equal(g["m2l_ptr"], mp) and np.array_equal(g["m2l_idx"].astype(np.int64), mi)
+    s = f.stats()
+    assert s["n_p2p_pairs"] == T.n_p2p and s["n_m2l_pairs"] == T.n_m2l
+    assert s["n_interactions"] == T.interactions and s["depth"] == T.depth
+    return T
+
+
+@pytest.mark.parametrize("n,ncrit,theta,seed", [(1, 8, 0.5, 1), (2, 1, 0.5, 2), (7, 2, 0.5, 3), (1000, 16, 0.5, 4),
+                                                (16384, 64, 0.5, 1), (50000, 32, 0.4, 5), (20000, 8, 0.7, 6)])
+def test_uniform_tree_bit_exact(n, ncrit, theta, seed):
+    x, q = inputs.uniform_cube(n, seed)
+    compare(x, q, ncrit, theta)
+
+
+@pytest.mark.parametrize("n,ncrit", [(20000, 16), (3000, 1)])
+def test_plummer_tree_bit_exact(n, ncrit):
+    x, q = inputs.plummer(n, 9)
+    compare(x, q, ncrit, 0.5)
+
+
+def test_float32_input_bit_exact():
+    x, q = inputs.uniform_cube(30000, 10, dtype=np.float32)
+    compare(x, q, 64, 0.5, dtype=np.float32)
+
+
+def test_ragged_sizes_span_several_sort_tiles():
+    # 4096 keys per radix tile: sizes around tile edges
+    for n in (4095, 4096, 4097, 12289):
+        x, q = inputs.uniform_cube(n, n)
+        compare(x, q, 16, 0.5)
+
+
+def test_coincident_particles_reach_level_21():
+    x = np.tile([[0.25, -0.5, 0.125]], (300, 1))
+    x[:10] += np.linspace(0, 1, 10)[:, None]
+    q = np.ones(300)
+    T = compare(x, q, 8, 0.5)
+    assert T.depth == 21
+
+
+def test_duplicate_keys_sorted_stably():
+    rng = np.random.default_rng(3)
+    base = rng.uniform(-1, 1, (50, 3))
+    x = base[rng.integers(0, 50, 5000)]
+    q = rng.uniform(-1, 1, 5000)
+    compare(x, q, 4, 0.5)
