@@ -1,0 +1,348 @@
+#!/usr/bin/env python3
+"""FMM throughput on GB300: particles/s for the 3-D Laplace FMM.
+
+Workload (the paper's OpenMP / strong-scaling size, Sec. 3.1 and Sec. 4):
+N = 10^7 particles uniform in [-1, 1]^3, charges uniform in [-1, 1], FP32
+positions and charges, p = 8 terms, theta = 0.5, ncrit picked by the
+autotuner, mixed precision. One step = fmm_build + fmm_evaluate (tree, lists,
+P2M, M2M, M2L, L2L, L2P, P2P, unsort) with the inputs resident in HBM.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Prints one JSON line. With torchrun each rank runs an independent replica on
+its own GPU (the single-GPU method has no exchange step); value is the sum of
+the particles of all ranks divided by the slowest rank's time.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FMM particles/s at N=1e7 at ≤1e-4 rel-L2 err, mixed vs FP64; P2P % FP32 peak"
+FLOP_PER_INTERACTION = 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=10_000_000)
+    ap.add_argument("--p", type=int, default=8)
+    ap.add_argument("--theta", type=float, default=0.5)
+    ap.add_argument("--ncrit", type=int, default=0, help="0 = autotune")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--targets", type=int, default=4096, help="sampled targets for the error check")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=100_000)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "200"], stdout=open(self.path, "w"),
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [c.strip() for c in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm_, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm_)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 CPU oracle on a bounded sample of the workload
+# ---------------------------------------------------------------------------
+def cpu_oracle_rate(n_sample, p, theta, ncrit, seed=3):
+    import numpy as np
+    import oracle
+    from paper_1106_2176_gb300 import inputs
+    x, q = inputs.uniform_cube(n_sample, seed, dtype=np.float32)
+    x, q = x.astype(np.float64), q.astype(np.float64)
+    t0 = time.perf_counter()
+    oracle.fmm(x, q, p, theta, ncrit)
+    dt = time.perf_counter() - t0
+    return n_sample / dt, dt
+
+
+def run_reference(a, rank):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    ncrit = a.ncrit or 64
+    ns = a.cpu_sample
+    cores = os.cpu_count()
+    for _ in range(a.warmup):
+        cpu_oracle_rate(ns, a.p, a.theta, ncrit)
+    times = []
+    for _ in range(a.steps):
+        _, dt = cpu_oracle_rate(ns, a.p, a.theta, ncrit)
+        times.append(dt)
+    ms = 1000.0 * sum(times) / len(times)
+    value = ns / (ms / 1000.0)
+    sample = ("oracle FMM (FP64, OpenMP over target cells) on N=%d of the same uniform-cube workload, p=%d, "
+              "theta=%g, ncrit=%d; the FMM's cost is linear in N, so particles/s of the sample stands for "
+              "the full size" % (ns, a.p, a.theta, ncrit))
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": a.gpus,
+           "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "uniform cube N=%d (sampled: %d), p=%d, theta=%g, FP32 positions/charges"
+                      % (a.n, ns, a.p, a.theta)},
+           "cpu_baseline": {"value": value, "unit": "particles/s", "cores": cores, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def p2p_traffic(interactions, n):
+    """DRAM bytes per P2P launch from the committed ncu summary, scaled to this
+    workload by particle count; None when the kernel source changed since."""
+    path = os.path.join(ROOT, "profiles", "p2p_traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path))
+        src = open(os.path.join(ROOT, "paper_1106_2176_gb300", "csrc", "p2p.cu"), "rb").read()
+        if d.get("source_sha256") != hashlib.sha256(src).hexdigest():
+            return None
+        return d["dram_bytes"] * (n / d["n"])
+    except Exception:
+        return None
+
+
+def main():
+    a = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        if a.impl == "ours":
+            torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if a.impl == "ours" else "gloo")
+    if a.impl == "reference":
+        run_reference(a, rank)
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    import numpy as np
+    from paper_1106_2176_gb300 import FMM, _build, inputs, tune
+
+    _build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    N = a.n
+    x, q = inputs.uniform_cube(N, 3 + rank, dtype=np.float32)
+    xt = torch.tensor(x, device=dev)
+    qt = torch.tensor(q, device=dev)
+
+    ncrit = a.ncrit
+    tune_ms = None
+    if ncrit == 0:
+        ncrit, tune_ms = tune.tune_ncrit(xt, qt, a.p, a.theta, precision=a.precision)
+    f = FMM(N, p=a.p, theta=a.theta, ncrit=ncrit, precision=a.precision)
+    phi = torch.empty(N, dtype=torch.float32, device=dev)
+    grad = torch.empty((N, 3), dtype=torch.float32, device=dev)
+    for _ in range(max(a.warmup, 3)):
+        f.build(xt, qt)
+        f.evaluate(phi, grad)
+    torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream()
+    st0 = f.stats()
+    clocks = Clocks(local if os.environ.get("CUDA_VISIBLE_DEVICES") is None else local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p2p_ms, phase = [], {k: 0.0 for k in ("ms_build", "ms_p2m", "ms_m2m", "ms_m2l", "ms_l2l", "ms_l2p", "ms_p2p",
+                                          "ms_combine", "ms_evaluate")}
+    e0.record(stream)
+    for _ in range(a.steps):
+        f.build(xt, qt)
+        f.evaluate(phi, grad)
+        s = f.stats()  # phase times of this step (CUDA events on the launching streams)
+        p2p_ms.append(s["ms_p2p"])
+        for k in phase:
+            phase[k] += s[k] / a.steps
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1) / a.steps
+    st1 = f.stats()
+    launches = (st1["kernel_launches"] - st0["kernel_launches"]) // a.steps
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = N * world / (ms / 1000.0)
+
+    # accuracy: sampled targets against the FP64 direct sum on the GPU
+    tg = inputs.sample_targets(N, a.targets, seed=3)
+    tgt = torch.tensor(tg, device=dev)
+    x64, q64 = xt.double(), qt.double()
+    pd, gd = f.direct(x64, q64, tgt)
+    rel = lambda u, v: float(torch.linalg.norm(u - v) / torch.linalg.norm(v))
+    err_phi = rel(phi[tgt].double(), pd)
+    err_grad = rel(grad[tgt].double(), gd)
+
+    # FP64 path on the same GPU (one step, for the mixed-vs-FP64 comparison)
+    fp64 = None
+    if not a.no_fp64 and rank == 0:
+        f64 = FMM(N, p=a.p, theta=a.theta, ncrit=ncrit, precision="fp64")
+        p64 = torch.empty(N, dtype=torch.float64, device=dev)
+        g64 = torch.empty((N, 3), dtype=torch.float64, device=dev)
+        f64.build(x64, q64)
+        f64.evaluate(p64, g64)
+        torch.cuda.synchronize()
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        f64.build(x64, q64)
+        f64.evaluate(p64, g64)
+        b1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = b0.elapsed_time(b1)
+        fp64 = {"value": N / (ms64 / 1000.0), "unit": "particles/s", "ms_per_step": ms64,
+                "rel_l2_phi": rel(p64[tgt], pd), "rel_l2_grad": rel(g64[tgt], gd),
+                "mixed_speedup": ms64 / ms}
+        f64.close()
+        del p64, g64
+
+    # end to end through the C ABI with pinned host buffers
+    xh = torch.from_numpy(x).pin_memory()
+    qh = torch.from_numpy(q).pin_memory()
+    ph = torch.empty(N, dtype=torch.float32).pin_memory()
+    gh = torch.empty((N, 3), dtype=torch.float32).pin_memory()
+    fh = FMM(N, p=a.p, theta=a.theta, ncrit=ncrit, precision=a.precision)
+    for _ in range(2):
+        fh.build(xh.numpy(), qh.numpy())
+        fh.evaluate(ph.numpy(), gh.numpy())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        fh.build(xh.numpy(), qh.numpy())
+        fh.evaluate(ph.numpy(), gh.numpy())
+    torch.cuda.synchronize()
+    e2e_ms = 1000.0 * (time.perf_counter() - t0) / a.steps
+    if dist:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    fh.close()
+    e2e = {"value": N * world / (e2e_ms / 1000.0), "unit": "particles/s", "ms_per_step": e2e_ms,
+           "h2d_bytes_per_step": int(x.nbytes + q.nbytes), "d2h_bytes_per_step": int(ph.numpy().nbytes + gh.numpy().nbytes)}
+
+    # roofline of the dominant kernel (P2P, FP32 FMA pipe)
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tflops = nsm * 128 * 2 * sm_max * 1e6 / 1e12
+    inter = st1["n_interactions"]
+    p2p_avg = sum(p2p_ms) / len(p2p_ms)
+    achieved = FLOP_PER_INTERACTION * inter / (p2p_avg / 1000.0) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops, "traffic": p2p_traffic(inter, N), "kernel": "p2p_k<float>",
+                "peak_note": "FP32 FMA: %d SMs x 128 lanes x 2 flop x %.0f MHz (max SM clock); 20 flop per interaction"
+                             % (nsm, sm_max),
+                "interactions": inter, "p2p_ms": p2p_avg}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        ns = a.cpu_sample
+        rate, dt = cpu_oracle_rate(ns, a.p, a.theta, ncrit)
+        cpu = {"value": rate, "unit": "particles/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": "FP64 oracle FMM on N=%d of the same uniform-cube workload (p=%d, theta=%g, ncrit=%d), "
+                         "%.1f s on all host cores" % (ns, a.p, a.theta, ncrit, dt)}
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": world, "steps": a.steps,
+               "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f32" if a.precision == "mixed" else "f64", "data": "synthetic",
+               "config": {"workload": "uniform cube N=%d, charges U[-1,1], FP32 positions and charges, p=%d, theta=%g, "
+                                      "%s precision" % (N, a.p, a.theta, a.precision),
+                          "N": N, "p": a.p, "theta": a.theta, "ncrit": ncrit, "ncrit_tuning_ms": tune_ms,
+                          "precision": a.precision, "parallelism": "replicas" if world > 1 else "single",
+                          "l2": "inputs (x, q: %d MB) and the step's working set exceed the 129 MB L2"
+                                % ((x.nbytes + q.nbytes) // 2 ** 20)},
+               "rel_l2_phi": err_phi, "rel_l2_grad": err_grad, "error_targets": len(tg),
+               "fp64": fp64, "phases_ms": phase, "tree": {k: st1[k] for k in ("ncells", "nleaves", "depth",
+                                                                             "n_p2p_pairs", "n_m2l_pairs",
+                                                                             "n_m2l_irregular", "n_interactions",
+                                                                             "m2l_engine")},
+               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": ck}
+        print(json.dumps(out), flush=True)
+    f.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -286,6 +286,45 @@ __global__ void l2l_k(int p, int ls, int le, const int *__restrict__ parent, con
     if (l) Lc[im_idx(k, l)] += sc * si;
 }
 
+// Column m (orders +m and -m) of I_n^m(u), n = m .. Q-1, written to full
+// complex storage sI[2 * (n*n + n +- m)]; computed in FP64 by one thread:
+// I_m^m = (2m-1)!! (x + iy)^m / r^(2m+1), then the three-term recurrence in n.
+template <class T>
+__device__ void irregular_column(int Q, int m, double x, double y, double z, T *sI)
+{
+    const double r2 = x * x + y * y + z * z, ir2 = 1.0 / r2;
+    const double sg = (m & 1) ? -1.0 : 1.0;
+    auto put = [&](int n, double cr, double ci) {
+        sI[2 * (n * n + n + m)] = (T)cr;
+        sI[2 * (n * n + n + m) + 1] = (T)ci;
+        if (m) {
+            sI[2 * (n * n + n - m)] = (T)(sg * cr);
+            sI[2 * (n * n + n - m) + 1] = (T)(-sg * ci);
+        }
+    };
+    double pr = sqrt(ir2), pi = 0.0;  // I_0^0 = 1/r
+    for (int k = 1; k <= m; k++) {
+        const double f = (double)(2 * k - 1) * ir2;
+        const double a = (pr * x - pi * y) * f, b = (pr * y + pi * x) * f;
+        pr = a;
+        pi = b;
+    }
+    put(m, pr, pi);
+    if (m + 1 >= Q) return;
+    const double f1 = (double)(2 * m + 1) * z * ir2;
+    double p2r = pr, p2i = pi, p1r = pr * f1, p1i = pi * f1;
+    put(m + 1, p1r, p1i);
+    for (int n = m + 2; n < Q; n++) {
+        const double a = (double)(2 * n - 1) * z, b = (double)((n + m - 1) * (n - m - 1));
+        const double cr = (a * p1r - b * p2r) * ir2, ci = (a * p1i - b * p2i) * ir2;
+        put(n, cr, ci);
+        p2r = p1r;
+        p2i = p1i;
+        p1r = cr;
+        p1i = ci;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // M2L on the CUDA cores, same-level pairs from the octant stencil.
 // One block per tile of targets (one level, one octant); the loop runs over
@@ -302,8 +341,8 @@ __global__ void __launch_bounds__(M2L_CC_T) m2l_cc_k(int p, const M2LTile *__res
                                                      const int *__restrict__ tgt, const int4 *__restrict__ xyz,
                                                      const uint64_t *__restrict__ anchor, const LevelDesc *__restrict__ ld,
                                                      const int *__restrict__ map_pool, const int4 *__restrict__ st,
-                                                     const int *__restrict__ st_off, const T *__restrict__ itab,
-                                                     const T *__restrict__ M, T *__restrict__ L, int tile_max)
+                                                     const int *__restrict__ st_off, const T *__restrict__ M,
+                                                     T *__restrict__ L, int tile_max)
 {
     if ((int)blockIdx.x >= *ntiles) return;
     const M2LTile td = tiles[blockIdx.x];
@@ -339,8 +378,7 @@ __global__ void __launch_bounds__(M2L_CC_T) m2l_cc_k(int p, const M2LTile *__res
         if ((int)threadIdx.x < td.count)
             ssrc[threadIdx.x] = level_lookup(LD, map_pool, anchor, l, spos[3 * threadIdx.x] + v.x,
                                              spos[3 * threadIdx.x + 1] + v.y, spos[3 * threadIdx.x + 2] + v.z);
-        const T *Iv = itab + (size_t)v.w * 2 * QQ;
-        for (int i = threadIdx.x; i < 2 * QQ; i += blockDim.x) sI[i] = Iv[i];
+        if ((int)threadIdx.x < Q) irregular_column(Q, (int)threadIdx.x, -(double)v.x, -(double)v.y, -(double)v.z, sI);
         __syncthreads();
         for (int i = threadIdx.x; i < td.count * PP; i += blockDim.x) {
             const int t = i / PP, f = i - t * PP;
@@ -589,14 +627,20 @@ int m2l_tile_size(fmm_ctx *h)
     return std::max(t, 1);
 }
 
-void operators_init(fmm_ctx *h)
+// Same-level M2L stencils (Sec. 2.1 near/far split under the theta MAC): for
+// a target in octant o of its parent, the lattice offsets v with
+// 3 < fl(theta^2 |v|^2) (the MAC accepts the pair) whose parent offset
+// u = floor((o + v) / 2) has 3 >= fl(theta^2 |u|^2) (the parents were
+// rejected). Offsets are bounded by the lattice of the deepest level, so a tiny
+// theta on a shallow tree stays small. Rebuilt only when the bound grows.
+void stencil_update(fmm_ctx *h)
 {
-    const int p = h->p, PP = p * p, Q = 2 * p - 1, QQ = Q * Q;
     const double c = h->cmac;
-    // same-level stencils: v accepted by the MAC, its parent offset rejected
-    const int R = 2 * (int)std::ceil(std::sqrt(3.0 / c)) + 3;
+    const int Rfull = 2 * (int)std::ceil(std::sqrt(3.0 / c)) + 3;
+    const int R = std::min(Rfull, h->depth >= 20 ? Rfull : (1 << h->depth));
+    if (R <= h->st_R && h->st_dev.p) return;
     std::map<std::tuple<int, int, int>, int> vid;
-    std::vector<std::tuple<int, int, int>> vecs;
+    int nv = 0;
     h->st_off.assign(9, 0);
     h->st_host.clear();
     for (int o = 0; o < 8; o++) {
@@ -604,103 +648,71 @@ void operators_init(fmm_ctx *h)
         for (int vx = -R; vx <= R; vx++)
             for (int vy = -R; vy <= R; vy++)
                 for (int vz = -R; vz <= R; vz++) {
-                    const double d2 = (double)(vx * vx + vy * vy + vz * vz);
+                    const double d2 = (double)vx * vx + (double)vy * vy + (double)vz * vz;
                     if (!(3.0 < c * d2)) continue;
                     const int ux = floordiv2(ox + vx), uy = floordiv2(oy + vy), uz = floordiv2(oz + vz);
-                    const double u2 = (double)(ux * ux + uy * uy + uz * uz);
+                    const double u2 = (double)ux * ux + (double)uy * uy + (double)uz * uz;
                     if (3.0 < c * u2) continue;
                     auto key = std::make_tuple(vx, vy, vz);
                     auto it = vid.find(key);
-                    int id;
-                    if (it == vid.end()) {
-                        id = (int)vecs.size();
-                        vid[key] = id;
-                        vecs.push_back(key);
-                    } else id = it->second;
+                    int id = it == vid.end() ? (vid[key] = nv++) : it->second;
                     h->st_host.insert(h->st_host.end(), {vx, vy, vz, id});
                 }
         h->st_off[o + 1] = (int)(h->st_host.size() / 4);
     }
-    h->nV = (int)vecs.size();
+    h->nV = nv;
+    const int ne = h->st_off[8];
+    std::vector<int> buf(4 * (size_t)ne + 9);
+    std::copy(h->st_host.begin(), h->st_host.end(), buf.begin());
+    for (int o = 0; o < 9; o++) buf[4 * (size_t)ne + o] = h->st_off[o];
+    h->st_dev.ensure(sizeof(int) * buf.size());
+    FMM_CUDA_TRY(cudaMemcpy(h->st_dev.p, buf.data(), sizeof(int) * buf.size(), cudaMemcpyHostToDevice));
+    h->st_R = R;
+    // P2P sources of a leaf in a uniform tree: the offsets the MAC rejects
     int near = 0;
     for (int vx = -R; vx <= R; vx++)
         for (int vy = -R; vy <= R; vy++)
             for (int vz = -R; vz <= R; vz++)
-                if (!(3.0 < c * (double)(vx * vx + vy * vy + vz * vz))) near++;
+                if (!(3.0 < c * ((double)vx * vx + (double)vy * vy + (double)vz * vz))) near++;
     h->p2p_cap_hint = near;
+}
 
-    // device stencil: int4 entries followed by the 9 octant offsets
-    const int ne = h->st_off[8];
-    std::vector<int> buf(4 * ne + 9);
-    std::copy(h->st_host.begin(), h->st_host.end(), buf.begin());
-    for (int o = 0; o < 9; o++) buf[4 * ne + o] = h->st_off[o];
-    h->st_dev.ensure(sizeof(int) * buf.size());
-    FMM_CUDA_TRY(cudaMemcpy(h->st_dev.p, buf.data(), sizeof(int) * buf.size(), cudaMemcpyHostToDevice));
-
-    // I_n^m(u), u = -v, full storage of degree < Q, per vector
-    {
-        std::vector<double> tre(Q * (Q + 1) / 2), tim(Q * (Q + 1) / 2);
-        std::vector<double> t64((size_t)std::max(h->nV, 1) * 2 * QQ);
-        for (int id = 0; id < h->nV; id++) {
-            auto [vx, vy, vz] = vecs[id];
-            irregular_tri<double>(Q, -(double)vx, -(double)vy, -(double)vz, tre.data(), tim.data());
-            double *dst = t64.data() + (size_t)id * 2 * QQ;
-            for (int n = 0; n < Q; n++)
-                for (int m = -n; m <= n; m++) {
-                    const int am = m < 0 ? -m : m;
-                    double re = tre[tri(n, am)], im = tim[tri(n, am)];
-                    if (m < 0) {
+// R_n^m(t_o) for the 8 child offsets t_o = (c_child - c_parent) / w_parent
+// = (+-1/4, +-1/4, +-1/4), full complex storage, FP64 and FP32 copies.
+void operators_init(fmm_ctx *h)
+{
+    const int p = h->p, PP = p * p;
+    std::vector<double> tre(p * (p + 1) / 2), tim(p * (p + 1) / 2);
+    std::vector<double> r64((size_t)8 * 2 * PP);
+    for (int o = 0; o < 8; o++) {
+        const double tx = (o & 1) ? 0.25 : -0.25, ty = (o & 2) ? 0.25 : -0.25, tz = (o & 4) ? 0.25 : -0.25;
+        regular_tri<double>(p, tx, ty, tz, tre.data(), tim.data(), 1);
+        double *dst = r64.data() + (size_t)o * 2 * PP;
+        for (int n = 0; n < p; n++)
+            for (int m = -n; m <= n; m++) {
+                const int am = m < 0 ? -m : m;
+                double re = tre[tri(n, am)], im = tim[tri(n, am)];
+                if (m < 0) {
+                    im = -im;
+                    if (am & 1) {
+                        re = -re;
                         im = -im;
-                        if (am & 1) {
-                            re = -re;
-                            im = -im;
-                        }
                     }
-                    dst[2 * full(n, m)] = re;
-                    dst[2 * full(n, m) + 1] = im;
                 }
-        }
-        std::vector<float> t32(t64.size());
-        for (size_t i = 0; i < t64.size(); i++) t32[i] = (float)t64[i];
-        h->itab64.ensure(sizeof(double) * t64.size());
-        h->itab32.ensure(sizeof(float) * t32.size());
-        FMM_CUDA_TRY(cudaMemcpy(h->itab64.p, t64.data(), sizeof(double) * t64.size(), cudaMemcpyHostToDevice));
-        FMM_CUDA_TRY(cudaMemcpy(h->itab32.p, t32.data(), sizeof(float) * t32.size(), cudaMemcpyHostToDevice));
+                dst[2 * full(n, m)] = re;
+                dst[2 * full(n, m) + 1] = im;
+            }
     }
-    // R_n^m(t_o), t_o = (c_child - c_parent) / w_parent = (+-1/4, +-1/4, +-1/4)
-    {
-        std::vector<double> tre(p * (p + 1) / 2), tim(p * (p + 1) / 2);
-        std::vector<double> r64((size_t)8 * 2 * PP);
-        for (int o = 0; o < 8; o++) {
-            const double tx = (o & 1) ? 0.25 : -0.25, ty = (o & 2) ? 0.25 : -0.25, tz = (o & 4) ? 0.25 : -0.25;
-            regular_tri<double>(p, tx, ty, tz, tre.data(), tim.data(), 1);
-            double *dst = r64.data() + (size_t)o * 2 * PP;
-            for (int n = 0; n < p; n++)
-                for (int m = -n; m <= n; m++) {
-                    const int am = m < 0 ? -m : m;
-                    double re = tre[tri(n, am)], im = tim[tri(n, am)];
-                    if (m < 0) {
-                        im = -im;
-                        if (am & 1) {
-                            re = -re;
-                            im = -im;
-                        }
-                    }
-                    dst[2 * full(n, m)] = re;
-                    dst[2 * full(n, m) + 1] = im;
-                }
-        }
-        std::vector<float> r32(r64.size());
-        for (size_t i = 0; i < r64.size(); i++) r32[i] = (float)r64[i];
-        h->rtab64.ensure(sizeof(double) * r64.size());
-        h->rtab32.ensure(sizeof(float) * r32.size());
-        FMM_CUDA_TRY(cudaMemcpy(h->rtab64.p, r64.data(), sizeof(double) * r64.size(), cudaMemcpyHostToDevice));
-        FMM_CUDA_TRY(cudaMemcpy(h->rtab32.p, r32.data(), sizeof(float) * r32.size(), cudaMemcpyHostToDevice));
-    }
+    std::vector<float> r32(r64.size());
+    for (size_t i = 0; i < r64.size(); i++) r32[i] = (float)r64[i];
+    h->rtab64.ensure(sizeof(double) * r64.size());
+    h->rtab32.ensure(sizeof(float) * r32.size());
+    FMM_CUDA_TRY(cudaMemcpy(h->rtab64.p, r64.data(), sizeof(double) * r64.size(), cudaMemcpyHostToDevice));
+    FMM_CUDA_TRY(cudaMemcpy(h->rtab32.p, r32.data(), sizeof(float) * r32.size(), cudaMemcpyHostToDevice));
 }
 
 template <class T, class P4>
-static void far_field_t(fmm_ctx *h, const P4 *xs, const T *rtab, const T *itab)
+static void far_field_t(fmm_ctx *h, const P4 *xs, const T *rtab)
 {
     cudaStream_t s = h->stream;
     const int p = h->p, PP = p * p, ntri = p * (p + 1) / 2, Q = 2 * p - 1;
@@ -752,7 +764,7 @@ static void far_field_t(fmm_ctx *h, const P4 *xs, const T *rtab, const T *itab)
             m2l_cc_k<T><<<h->ntiles_max, M2L_CC_T, smem, s>>>(
                 p, h->m2l_tiles.as<M2LTile>(), reinterpret_cast<const int *>(h->m2l_misc.as<unsigned>() + 24 * (FMM_MAXLEVEL + 1)),
                 h->m2l_tgt.as<int>(), h->c_xyz.as<int4>(), h->c_anchor.as<uint64_t>(), h->lvl_desc.as<LevelDesc>(),
-                h->map_pool.as<int>(), h->st_dev.as<int4>(), st_off, itab, M, L, tile);
+                h->map_pool.as<int>(), h->st_dev.as<int4>(), st_off, M, L, tile);
             count_launch(h);
             check_launch("m2l");
         }
@@ -792,11 +804,11 @@ static void far_field_t(fmm_ctx *h, const P4 *xs, const T *rtab, const T *itab)
 void far_field(fmm_ctx *h)
 {
     if (h->precision == FMM_FP64) {
-        far_field_t<double, double4_32a>(h, h->xs64.as<double4_32a>(), h->rtab64.as<double>(), h->itab64.as<double>());
+        far_field_t<double, double4_32a>(h, h->xs64.as<double4_32a>(), h->rtab64.as<double>());
     } else if (h->dtype == FMM_F64) {
-        far_field_t<float, double4_32a>(h, h->xs64.as<double4_32a>(), h->rtab32.as<float>(), h->itab32.as<float>());
+        far_field_t<float, double4_32a>(h, h->xs64.as<double4_32a>(), h->rtab32.as<float>());
     } else {
-        far_field_t<float, float4>(h, h->xs32.as<float4>(), h->rtab32.as<float>(), h->itab32.as<float>());
+        far_field_t<float, float4>(h, h->xs32.as<float4>(), h->rtab32.as<float>());
     }
 }
 

@@ -144,7 +144,7 @@ struct fmm_ctx {
     std::vector<int> st_off;    // st_off[o] .. st_off[o+1]: entries of octant o
     std::vector<int> st_host;   // 4 ints per entry: vx, vy, vz (source - target), vector id
     fmm::DevBuf st_dev;         // int4 per entry
-    fmm::DevBuf itab64, itab32; // I_n^m(u), u = -v, full complex storage of degree < 2p-1, per vector
+    int st_R = 0;               // offsets |v_k| <= st_R are in the stencil
     fmm::DevBuf rtab64, rtab32; // R_n^m(t_o), 8 child offsets, full complex storage of degree < p
     fmm::DevBuf ttab;           // tensor-core M2L operators (split TF32 images), per vector
     size_t ttab_stride = 0;     // bytes per vector in ttab
@@ -191,7 +191,8 @@ void scan_exclusive_u32(fmm_ctx *h, const unsigned *in, unsigned *out, int64_t c
                         cudaStream_t s);
 
 // expansions.cu
-void operators_init(fmm_ctx *h);  // stencil, I tables, R tables
+void operators_init(fmm_ctx *h);  // R tables of M2M / L2L
+void stencil_update(fmm_ctx *h);  // same-level M2L stencil for the current tree depth
 void far_field(fmm_ctx *h);       // P2M, M2M, M2L, L2L, L2P into h->far
 
 // m2l_tc.cu

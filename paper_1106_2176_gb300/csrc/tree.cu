@@ -812,11 +812,13 @@ void tree_build(fmm_ctx *h, const void *x, const void *q, int64_t n, int dt)
     }
 
     // 5. dual traversal
+    stencil_update(h);
     {
         // the near-field stencil size bounds the P2P list of a leaf in a uniform tree
-        size_t cap_p2p = std::max<size_t>(1024, (size_t)h->nleaves * (size_t)(h->p2p_cap_hint + 8));
+        const size_t per = (size_t)h->p2p_cap_hint + 8;
+        size_t cap_p2p = std::max<size_t>(1024, std::min((size_t)h->nleaves * per, (size_t)h->nleaves * h->nleaves));
         size_t cap_m2lx = std::max<size_t>(1024, (size_t)ncells * 4);
-        size_t cap_next = std::max<size_t>(1024, (size_t)ncells * (size_t)(h->p2p_cap_hint + 8));
+        size_t cap_next = std::max<size_t>(1024, std::min((size_t)ncells * per, (size_t)ncells * ncells));
         h->p2p_pairs.ensure(sizeof(int2) * cap_p2p);
         h->m2lx_pairs.ensure(sizeof(int2) * cap_m2lx);
         h->frontA.ensure(sizeof(int2) * cap_next);
