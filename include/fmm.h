@@ -85,7 +85,7 @@ typedef struct {
     int64_t n_interactions; /* sum over P2P pairs of n_A * n_B, minus n */
     int64_t n_stencil;      /* same-level M2L translation vectors (all octants) */
     int32_t m2l_engine;     /* engine used by the last evaluate */
-    int32_t reserved0;
+    int32_t async_error;    /* nonzero if a device-side wait of the last evaluate timed out */
     /* milliseconds of the last build / evaluate, measured with CUDA events */
     double ms_build, ms_evaluate;
     double ms_p2m, ms_m2m, ms_m2l, ms_l2l, ms_l2p, ms_p2p, ms_combine;

@@ -83,7 +83,7 @@ fmm_ctx::~fmm_ctx()
                            &c_nchild, &c_parent, &c_xyz, &split_cnt, &split_off, &split_bnd, &leaves, &frontA,
                            &frontB, &p2p_pairs, &m2lx_pairs, &pair_keys, &pair_keys2, &pair_vals, &pair_vals2,
                            &p2p_ptr, &p2p_src, &m2lx_ptr, &m2lx_src, &row_cnt, &counters, &lvl_desc, &map_pool,
-                           &m2l_tgt, &m2l_tiles, &m2l_misc, &Mexp, &Lexp, &far, &near, &out_phi, &out_grad,
+                           &m2l_tgt, &m2l_tiles, &m2l_misc, &msplit, &Mexp, &Lexp, &far, &near, &out_phi, &out_grad,
                            &direct_part};
     for (auto *b : bufs) b->release();
     hpin.release();
@@ -316,6 +316,12 @@ int fmm_get_stats(fmm_handle h, fmm_stats *out)
     out->n_interactions = h->n_interactions;
     out->n_stencil = h->st_off.empty() ? 0 : h->st_off[8];
     out->m2l_engine = h->engine_used;
+    if (h->m2l_misc.p) {
+        int e = 0;
+        FMM_CUDA_TRY(cudaMemcpy(&e, h->m2l_misc.as<unsigned>() + 24 * (FMM_MAXLEVEL + 1) + 4, sizeof(int),
+                                cudaMemcpyDeviceToHost));
+        out->async_error = e;
+    }
     out->kernel_launches = h->launches;
     cudaEvent_t *ev = h->tm.ev;
     if (h->built) out->ms_build = ev_ms(ev[0], ev[1]);

@@ -140,10 +140,16 @@ __device__ __forceinline__ int child_octant(int4 a)
     return ((a.x >> bit) & 1) | (((a.y >> bit) & 1) << 1) | (((a.z >> bit) & 1) << 2);
 }
 
-__device__ __forceinline__ double4_32a load_pt(const double4_32a *p, int j) { return p[j]; }
-__device__ __forceinline__ double4_32a load_pt(const float4 *p, int j)
+// particle j relative to the cell centre c: absolute FP64 positions minus c,
+// or FP32 coordinates that are already relative to the leaf centre
+__device__ __forceinline__ double4_32a rel_pt(const double4_32a *p, int j, const double c[3])
 {
-    float4 v = p[j];
+    const double4_32a v = p[j];
+    return make_double4_32a(v.x - c[0], v.y - c[1], v.z - c[2], v.w);
+}
+__device__ __forceinline__ double4_32a rel_pt(const float4 *p, int j, const double *)
+{
+    const float4 v = p[j];
     return make_double4_32a(v.x, v.y, v.z, v.w);
 }
 
@@ -171,8 +177,8 @@ __global__ void __launch_bounds__(64) p2m_k(int p, const int *__restrict__ leave
         if (t < chunk) {
             const int j = j0 + t;
             if (j < e) {
-                const double4_32a pt = load_pt(xs, j);
-                const T dx = (T)((pt.x - cen[0]) * iw), dy = (T)((pt.y - cen[1]) * iw), dz = (T)((pt.z - cen[2]) * iw);
+                const double4_32a pt = rel_pt(xs, j, cen);
+                const T dx = (T)(pt.x * iw), dy = (T)(pt.y * iw), dz = (T)(pt.z * iw);
                 regular_tri<T>(p, dx, dy, dz, sre + t, sim + t, chunk);
                 const T q = (T)pt.w;
                 for (int k = 0; k < ntri; k++) {
@@ -554,8 +560,8 @@ __global__ void __launch_bounds__(64) l2p_k(int p, const int *__restrict__ leave
     cell_geom(box, xyz[c], cen, w);
     const double iw = 1.0 / w;
     for (int j = begin[c] + threadIdx.x; j < end[c]; j += blockDim.x) {
-        const double4_32a pt = load_pt(xs, j);
-        const T x = (T)((pt.x - cen[0]) * iw), y = (T)((pt.y - cen[1]) * iw), z = (T)((pt.z - cen[2]) * iw);
+        const double4_32a pt = rel_pt(xs, j, cen);
+        const T x = (T)(pt.x * iw), y = (T)(pt.y * iw), z = (T)(pt.z * iw);
         const T r2 = x * x + y * y + z * z;
         T F = 0, Fz = 0, Gr = 0, Gi = 0;
         T mre = 1, mim = 0;
@@ -621,7 +627,7 @@ static int floordiv2(int a) { return a >= 0 ? a / 2 : -((-a + 1) / 2); }
 
 int m2l_tile_size(fmm_ctx *h)
 {
-    if (h->precision == FMM_MIXED && h->engine_req != FMM_M2L_CUDACORE && tensor_m2l_supported(h)) return 128;
+    if (h->precision == FMM_MIXED && h->engine_used == FMM_M2L_TENSOR) return 128;
     const int ntri = h->p * (h->p + 1) / 2;
     int t = std::min(32, (M2L_CC_T * M2L_CC_ACC) / ntri);
     return std::max(t, 1);

@@ -148,6 +148,8 @@ struct fmm_ctx {
     fmm::DevBuf rtab64, rtab32; // R_n^m(t_o), 8 child offsets, full complex storage of degree < p
     fmm::DevBuf ttab;           // tensor-core M2L operators (split TF32 images), per vector
     size_t ttab_stride = 0;     // bytes per vector in ttab
+    int ttab_nv = -1;           // stencil vectors the operator images were made for
+    fmm::DevBuf msplit;         // M~ split into TF32 (hi, lo) rows for the tensor-core M2L
 
     // workspaces
     fmm::DevBuf box;

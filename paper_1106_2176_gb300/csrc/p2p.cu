@@ -60,10 +60,15 @@ __device__ __forceinline__ void acc2(double &hi, double &lo, double b) { hi += b
 
 constexpr int P2P_T = 128;
 
-template <class T>
+// LOCAL: coordinates are relative to the centre of the particle's leaf (FP32
+// path); a source leaf B is moved into the frame of the target leaf A by the
+// centre offset c_B - c_A = (HG_B - HG_A) h/2, HG = 2 anchor + W the centre in
+// half-grid units (an exact integer below 2^23), so the shift is rounded once.
+template <class T, bool LOCAL>
 __global__ void __launch_bounds__(P2P_T) p2p_k(const typename Vec4<T>::type *__restrict__ xs, const int *__restrict__ leaves,
                                                const int *__restrict__ begin, const int *__restrict__ end,
                                                const int *__restrict__ ptr, const int *__restrict__ src,
+                                               const int4 *__restrict__ xyz, const Box *__restrict__ box,
                                                double4_32a *__restrict__ near)
 {
     using T4 = typename Vec4<T>::type;
@@ -73,6 +78,16 @@ __global__ void __launch_bounds__(P2P_T) p2p_k(const typename Vec4<T>::type *__r
     const int A = leaves[blockIdx.x];
     const int tb = begin[A], te = end[A];
     const int k0 = ptr[A], k1 = ptr[A + 1];
+    int hgA[3] = {0, 0, 0};
+    T hh = T(0);
+    if (LOCAL) {
+        const int4 a = xyz[A];
+        const int W = 1 << (FMM_MAXLEVEL - a.w);
+        hgA[0] = 2 * a.x + W;
+        hgA[1] = 2 * a.y + W;
+        hgA[2] = 2 * a.z + W;
+        hh = (T)(box->h * 0.5);
+    }
     for (int t0 = tb; t0 < te; t0 += 2 * P2P_T) {
         const int nt = min(2 * P2P_T, te - t0);
         const int R = (nt + 1) >> 1;
@@ -93,7 +108,22 @@ __global__ void __launch_bounds__(P2P_T) p2p_k(const typename Vec4<T>::type *__r
                 const int b0 = begin[B] + off;
                 const int blen = end[B] - b0;
                 const int take = min(blen, CH - fill);
-                for (int j = threadIdx.x; j < take; j += P2P_T) sh[fill + j] = xs[b0 + j];
+                if (LOCAL) {
+                    const int4 bb = xyz[B];
+                    const int W = 1 << (FMM_MAXLEVEL - bb.w);
+                    const T sx = (T)(2 * bb.x + W - hgA[0]) * hh;
+                    const T sy = (T)(2 * bb.y + W - hgA[1]) * hh;
+                    const T sz = (T)(2 * bb.z + W - hgA[2]) * hh;
+                    for (int j = threadIdx.x; j < take; j += P2P_T) {
+                        T4 v = xs[b0 + j];
+                        v.x += sx;
+                        v.y += sy;
+                        v.z += sz;
+                        sh[fill + j] = v;
+                    }
+                } else {
+                    for (int j = threadIdx.x; j < take; j += P2P_T) sh[fill + j] = xs[b0 + j];
+                }
                 fill += take;
                 if (take == blen) {
                     k++;
@@ -139,13 +169,13 @@ void near_field(fmm_ctx *h, cudaStream_t s)
     h->near.ensure(sizeof(double4_32a) * (size_t)h->n);
     if (h->nleaves == 0) return;
     if (h->precision == FMM_FP64)
-        p2p_k<double><<<h->nleaves, P2P_T, 0, s>>>(h->xs64.as<double4_32a>(), h->leaves.as<int>(), h->c_begin.as<int>(),
-                                                   h->c_end.as<int>(), h->p2p_ptr.as<int>(), h->p2p_src.as<int>(),
-                                                   h->near.as<double4_32a>());
+        p2p_k<double, false><<<h->nleaves, P2P_T, 0, s>>>(h->xs64.as<double4_32a>(), h->leaves.as<int>(), h->c_begin.as<int>(),
+                                                          h->c_end.as<int>(), h->p2p_ptr.as<int>(), h->p2p_src.as<int>(),
+                                                          h->c_xyz.as<int4>(), h->box.as<Box>(), h->near.as<double4_32a>());
     else
-        p2p_k<float><<<h->nleaves, P2P_T, 0, s>>>(h->xs32.as<float4>(), h->leaves.as<int>(), h->c_begin.as<int>(),
-                                                  h->c_end.as<int>(), h->p2p_ptr.as<int>(), h->p2p_src.as<int>(),
-                                                  h->near.as<double4_32a>());
+        p2p_k<float, true><<<h->nleaves, P2P_T, 0, s>>>(h->xs32.as<float4>(), h->leaves.as<int>(), h->c_begin.as<int>(),
+                                                        h->c_end.as<int>(), h->p2p_ptr.as<int>(), h->p2p_src.as<int>(),
+                                                        h->c_xyz.as<int4>(), h->box.as<Box>(), h->near.as<double4_32a>());
     count_launch(h);
     check_launch("p2p");
 }

@@ -675,6 +675,28 @@ __global__ void leaves_write_k(int nc, const int *__restrict__ nchild, const uns
     if (c < nc && nchild[c] == 0) leaves[off[c]] = c;
 }
 
+// FP32 particle coordinates relative to the centre of their leaf, computed
+// from FP64 positions (mixed precision): the P2P kernel then works with
+// offsets of the size of a cell, so rounding to FP32 costs ~6e-8 of the cell
+// width rather than of the root-box coordinate.
+template <class P4>
+__global__ void local_coords_k(const int *__restrict__ leaves, const int *__restrict__ begin, const int *__restrict__ end,
+                               const int4 *__restrict__ xyz, const Box *__restrict__ box, const P4 *__restrict__ src,
+                               float4 *__restrict__ xs32)
+{
+    const int c = leaves[blockIdx.x];
+    const int4 a = xyz[c];
+    const double h = box->h;
+    const double half = ldexp(1.0, FMM_MAXLEVEL - 1 - a.w);
+    const double cx = __dadd_rn(box->origin[0], __dmul_rn((double)a.x + half, h));
+    const double cy = __dadd_rn(box->origin[1], __dmul_rn((double)a.y + half, h));
+    const double cz = __dadd_rn(box->origin[2], __dmul_rn((double)a.z + half, h));
+    for (int j = begin[c] + threadIdx.x; j < end[c]; j += blockDim.x) {
+        const P4 v = src[j];
+        xs32[j] = make_float4((float)((double)v.x - cx), (float)((double)v.y - cy), (float)((double)v.z - cz), (float)v.w);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // host orchestration
 // ---------------------------------------------------------------------------
@@ -809,6 +831,20 @@ void tree_build(fmm_ctx *h, const void *x, const void *q, int64_t n, int dt)
         FMM_CUDA_TRY(cudaMemcpyAsync(hp, tot, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
         FMM_CUDA_TRY(cudaStreamSynchronize(s));
         h->nleaves = (int)*hp;
+    }
+
+    // mixed precision: FP32 coordinates local to the leaf
+    if (mixed && h->nleaves > 0) {
+        if (need64)
+            local_coords_k<double4_32a><<<h->nleaves, 128, 0, s>>>(h->leaves.as<int>(), h->c_begin.as<int>(), h->c_end.as<int>(),
+                                                                   h->c_xyz.as<int4>(), box, h->xs64.as<double4_32a>(),
+                                                                   h->xs32.as<float4>());
+        else
+            local_coords_k<float4><<<h->nleaves, 128, 0, s>>>(h->leaves.as<int>(), h->c_begin.as<int>(), h->c_end.as<int>(),
+                                                              h->c_xyz.as<int4>(), box, h->xs32.as<float4>(),
+                                                              h->xs32.as<float4>());
+        count_launch(h);
+        check_launch("local coordinates");
     }
 
     // 5. dual traversal

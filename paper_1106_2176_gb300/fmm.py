@@ -41,7 +41,7 @@ class fmm_stats(ctypes.Structure):
                 ("depth", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("n_p2p_pairs", ctypes.c_int64), ("n_m2l_pairs", ctypes.c_int64),
                 ("n_m2l_irregular", ctypes.c_int64), ("n_interactions", ctypes.c_int64),
-                ("n_stencil", ctypes.c_int64), ("m2l_engine", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("n_stencil", ctypes.c_int64), ("m2l_engine", ctypes.c_int32), ("async_error", ctypes.c_int32),
                 ("ms_build", ctypes.c_double), ("ms_evaluate", ctypes.c_double),
                 ("ms_p2m", ctypes.c_double), ("ms_m2m", ctypes.c_double), ("ms_m2l", ctypes.c_double),
                 ("ms_l2l", ctypes.c_double), ("ms_l2p", ctypes.c_double), ("ms_p2p", ctypes.c_double),
@@ -167,6 +167,8 @@ class FMM:
     def evaluate(self, phi=None, grad=None):
         """Potential and gradient at every particle of the last build, input order."""
         n = self._n
+        if self._dtype is None:  # no build yet: the library reports FMM_ESTATE
+            _check(lib().fmm_evaluate(self._h, None, None), self._h)
         if self._host:
             phi = np.empty(n, dtype=self._np_dtype) if phi is None else phi
             grad = np.empty((n, 3), dtype=self._np_dtype) if grad is None else grad

@@ -156,3 +156,28 @@ def test_rebuild_same_handle_is_deterministic():
         outs.append([t.cpu().numpy() for t in f.evaluate()])
     for o in outs[1:]:
         assert np.array_equal(o[0], outs[0][0]) and np.array_equal(o[1], outs[0][1])
+
+
+@pytest.mark.parametrize("P", [4, 6, 8])
+def test_tensor_core_m2l_matches_fp64_expansions(P):
+    # the local expansions of the mixed path (tcgen05 M2L in split TF32) against
+    # the FP64 path's, cell by cell, relative to each cell's largest coefficient
+    x, q = inputs.uniform_cube(60000, 21)
+    _, _, f64 = run_fmm(x, q, P, 0.5, 32, precision="fp64")
+    _, _, fmx = run_fmm(x, q, P, 0.5, 32, precision="mixed", engine="tensor")
+    st = fmx.stats()
+    assert st["m2l_engine"] == 1 and st["async_error"] == 0
+    _, L64 = f64.export_expansions()
+    _, Lmx = fmx.export_expansions()
+    lev = f64.export_tree()["level"]
+    sel = lev >= 2
+    sc = np.max(np.abs(L64[sel]), axis=1, keepdims=True) + 1e-300
+    assert np.max(np.abs(Lmx[sel] - L64[sel]) / sc) < 2e-5
+
+
+def test_tensor_and_cudacore_engines_agree():
+    x, q = inputs.uniform_cube(40000, 22, dtype=np.float32)
+    pt, gt, ft = run_fmm(x, q, 8, 0.5, 64, precision="mixed", dtype=np.float32, engine="tensor")
+    pc, gc, fc = run_fmm(x, q, 8, 0.5, 64, precision="mixed", dtype=np.float32, engine="cudacore")
+    assert ft.stats()["m2l_engine"] == 1 and fc.stats()["m2l_engine"] == 2
+    assert rel(pt, pc) < 1e-6 and rel(gt, gc) < 1e-6
