@@ -390,7 +390,9 @@ __global__ void __launch_bounds__(128, 1)
             if (*(volatile int *)abort_flag) break;
         }
     }
-    // the final MMAs of every stage have completed when all groups are drained
+    // every MMA commit must have arrived before the shared memory goes away
+    if (tid == 0 && !*(volatile int *)abort_flag)
+        for (int u = max(0, nunits - NS); u < nunits; u++) mbar_wait(&mma_done[u % NS], (uint32_t)((u / NS) & 1));
     if (cell >= 0 && !*(volatile int *)abort_flag) {
         float *Lc = L + (size_t)cell * PP;
 #pragma unroll
