@@ -140,17 +140,16 @@ __device__ __forceinline__ int child_octant(int4 a)
     return ((a.x >> bit) & 1) | (((a.y >> bit) & 1) << 1) | (((a.z >> bit) & 1) << 2);
 }
 
-// particle j relative to the cell centre c: absolute FP64 positions minus c,
-// or FP32 coordinates that are already relative to the leaf centre
+// particle j relative to the cell centre c, in FP64
 __device__ __forceinline__ double4_32a rel_pt(const double4_32a *p, int j, const double c[3])
 {
     const double4_32a v = p[j];
     return make_double4_32a(v.x - c[0], v.y - c[1], v.z - c[2], v.w);
 }
-__device__ __forceinline__ double4_32a rel_pt(const float4 *p, int j, const double *)
+__device__ __forceinline__ double4_32a rel_pt(const float4 *p, int j, const double c[3])
 {
     const float4 v = p[j];
-    return make_double4_32a(v.x, v.y, v.z, v.w);
+    return make_double4_32a((double)v.x - c[0], (double)v.y - c[1], (double)v.z - c[2], v.w);
 }
 
 // ---------------------------------------------------------------------------

@@ -3,6 +3,7 @@
 // Data layout in HBM (one handle, n particles, C cells, p terms, PP = p*p):
 //   sorted particles   xs64[n] double4_32a (x, y, z, q)      FP64 path, FP64 input
 //                      xs32[n] float4  (x, y, z, q)      mixed path (P2P)
+//                      xs32lo[n] float4 (x - fl(x), ...)  mixed path, FP64 input
 //   cells (SoA, breadth first, key order within a level)
 //                      level, begin, end, child, nchild, parent: int32[C]
 //                      anchor: uint64[C] (Morton key of the lowest corner)
@@ -156,7 +157,7 @@ struct fmm_ctx {
     fmm::DevBuf x_in, q_in;             // staging of host inputs
     fmm::DevBuf keys, keys2, idx, idx2; // Morton keys and permutation (radix sort ping-pong)
     fmm::DevBuf hist, scan_tmp;
-    fmm::DevBuf xs64, xs32;
+    fmm::DevBuf xs64, xs32, xs32lo;
     fmm::DevBuf c_level, c_anchor, c_begin, c_end, c_child, c_nchild, c_parent, c_xyz;
     fmm::DevBuf split_cnt, split_off, split_bnd;
     fmm::DevBuf leaves;

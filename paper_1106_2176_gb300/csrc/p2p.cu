@@ -60,34 +60,40 @@ __device__ __forceinline__ void acc2(double &hi, double &lo, double b) { hi += b
 
 constexpr int P2P_T = 128;
 
-// LOCAL: coordinates are relative to the centre of the particle's leaf (FP32
-// path); a source leaf B is moved into the frame of the target leaf A by the
-// centre offset c_B - c_A = (HG_B - HG_A) h/2, HG = 2 anchor + W the centre in
-// half-grid units (an exact integer below 2^23), so the shift is rounded once.
-template <class T, bool LOCAL>
-__global__ void __launch_bounds__(P2P_T) p2p_k(const typename Vec4<T>::type *__restrict__ xs, const int *__restrict__ leaves,
-                                               const int *__restrict__ begin, const int *__restrict__ end,
-                                               const int *__restrict__ ptr, const int *__restrict__ src,
-                                               const int4 *__restrict__ xyz, const Box *__restrict__ box,
-                                               double4_32a *__restrict__ near)
+template <class T4>
+__device__ __forceinline__ void interact_ds(const T4 &t, const float4 &tl, const T4 &s, const float4 &sl, float &p, float &gx,
+                                            float &gy, float &gz)
+{
+    const float dx = (t.x - s.x) + (tl.x - sl.x), dy = (t.y - s.y) + (tl.y - sl.y), dz = (t.z - s.z) + (tl.z - sl.z);
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    float ri = rsqrtf(r2);
+    ri = r2 > 0.f ? ri : 0.f;
+    const float qr = s.w * ri;
+    const float qr3 = qr * ri * ri;
+    p += qr;
+    gx -= qr3 * dx;
+    gy -= qr3 * dy;
+    gz -= qr3 * dz;
+}
+
+// DS (FP32 path, FP64 input): every coordinate is carried as an FP32 pair
+// (hi, lo) and a difference is formed as (hi_i - hi_j) + (lo_i - lo_j); for
+// nearby particles hi_i - hi_j is exact, so the near field keeps the accuracy
+// of the FP64 positions. FP32 inputs have lo = 0 and use the plain form.
+template <class T, bool DS>
+__global__ void __launch_bounds__(P2P_T) p2p_k(const typename Vec4<T>::type *__restrict__ xs, const float4 *__restrict__ xlo,
+                                               const int *__restrict__ leaves, const int *__restrict__ begin,
+                                               const int *__restrict__ end, const int *__restrict__ ptr,
+                                               const int *__restrict__ src, double4_32a *__restrict__ near)
 {
     using T4 = typename Vec4<T>::type;
-    constexpr int CH = sizeof(T) == 4 ? 2048 : 1024;
+    constexpr int CH = (DS || sizeof(T) == 8) ? 1024 : 2048;
     __shared__ T4 sh[CH];
+    __shared__ float4 shlo[DS ? CH : 1];
     __shared__ double red[P2P_T * 8];
     const int A = leaves[blockIdx.x];
     const int tb = begin[A], te = end[A];
     const int k0 = ptr[A], k1 = ptr[A + 1];
-    int hgA[3] = {0, 0, 0};
-    T hh = T(0);
-    if (LOCAL) {
-        const int4 a = xyz[A];
-        const int W = 1 << (FMM_MAXLEVEL - a.w);
-        hgA[0] = 2 * a.x + W;
-        hgA[1] = 2 * a.y + W;
-        hgA[2] = 2 * a.z + W;
-        hh = (T)(box->h * 0.5);
-    }
     for (int t0 = tb; t0 < te; t0 += 2 * P2P_T) {
         const int nt = min(2 * P2P_T, te - t0);
         const int R = (nt + 1) >> 1;
@@ -96,8 +102,13 @@ __global__ void __launch_bounds__(P2P_T) p2p_k(const typename Vec4<T>::type *__r
         const bool act = sl < S;
         const bool has1 = act && (row + R < nt);
         T4 x0 = {}, x1 = {};
-        if (act) x0 = xs[t0 + row];
+        float4 l0 = {}, l1 = {};
+        if (act) {
+            x0 = xs[t0 + row];
+            if (DS) l0 = xlo[t0 + row];
+        }
         x1 = has1 ? xs[t0 + row + R] : x0;
+        if (DS) l1 = has1 ? xlo[t0 + row + R] : l0;
         T h[8] = {0, 0, 0, 0, 0, 0, 0, 0}, lo[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         int k = k0, off = 0;
         while (k < k1) {
@@ -108,21 +119,9 @@ __global__ void __launch_bounds__(P2P_T) p2p_k(const typename Vec4<T>::type *__r
                 const int b0 = begin[B] + off;
                 const int blen = end[B] - b0;
                 const int take = min(blen, CH - fill);
-                if (LOCAL) {
-                    const int4 bb = xyz[B];
-                    const int W = 1 << (FMM_MAXLEVEL - bb.w);
-                    const T sx = (T)(2 * bb.x + W - hgA[0]) * hh;
-                    const T sy = (T)(2 * bb.y + W - hgA[1]) * hh;
-                    const T sz = (T)(2 * bb.z + W - hgA[2]) * hh;
-                    for (int j = threadIdx.x; j < take; j += P2P_T) {
-                        T4 v = xs[b0 + j];
-                        v.x += sx;
-                        v.y += sy;
-                        v.z += sz;
-                        sh[fill + j] = v;
-                    }
-                } else {
-                    for (int j = threadIdx.x; j < take; j += P2P_T) sh[fill + j] = xs[b0 + j];
+                for (int j = threadIdx.x; j < take; j += P2P_T) {
+                    sh[fill + j] = xs[b0 + j];
+                    if (DS) shlo[fill + j] = xlo[b0 + j];
                 }
                 fill += take;
                 if (take == blen) {
@@ -139,8 +138,14 @@ __global__ void __launch_bounds__(P2P_T) p2p_k(const typename Vec4<T>::type *__r
 #pragma unroll 4
                     for (int j = j0; j < j1; j++) {
                         const T4 s = sh[j];
-                        interact(x0, s, b[0], b[1], b[2], b[3]);
-                        interact(x1, s, b[4], b[5], b[6], b[7]);
+                        if constexpr (DS) {
+                            const float4 q = shlo[j];
+                            interact_ds(x0, l0, s, q, b[0], b[1], b[2], b[3]);
+                            interact_ds(x1, l1, s, q, b[4], b[5], b[6], b[7]);
+                        } else {
+                            interact(x0, s, b[0], b[1], b[2], b[3]);
+                            interact(x1, s, b[4], b[5], b[6], b[7]);
+                        }
                     }
 #pragma unroll
                     for (int c = 0; c < 8; c++) acc2(h[c], lo[c], b[c]);
@@ -168,14 +173,15 @@ void near_field(fmm_ctx *h, cudaStream_t s)
 {
     h->near.ensure(sizeof(double4_32a) * (size_t)h->n);
     if (h->nleaves == 0) return;
+    const int *lv = h->leaves.as<int>(), *cb = h->c_begin.as<int>(), *ce = h->c_end.as<int>();
+    const int *pp = h->p2p_ptr.as<int>(), *ps = h->p2p_src.as<int>();
+    double4_32a *out = h->near.as<double4_32a>();
     if (h->precision == FMM_FP64)
-        p2p_k<double, false><<<h->nleaves, P2P_T, 0, s>>>(h->xs64.as<double4_32a>(), h->leaves.as<int>(), h->c_begin.as<int>(),
-                                                          h->c_end.as<int>(), h->p2p_ptr.as<int>(), h->p2p_src.as<int>(),
-                                                          h->c_xyz.as<int4>(), h->box.as<Box>(), h->near.as<double4_32a>());
+        p2p_k<double, false><<<h->nleaves, P2P_T, 0, s>>>(h->xs64.as<double4_32a>(), nullptr, lv, cb, ce, pp, ps, out);
+    else if (h->dtype == FMM_F64)
+        p2p_k<float, true><<<h->nleaves, P2P_T, 0, s>>>(h->xs32.as<float4>(), h->xs32lo.as<float4>(), lv, cb, ce, pp, ps, out);
     else
-        p2p_k<float, true><<<h->nleaves, P2P_T, 0, s>>>(h->xs32.as<float4>(), h->leaves.as<int>(), h->c_begin.as<int>(),
-                                                        h->c_end.as<int>(), h->p2p_ptr.as<int>(), h->p2p_src.as<int>(),
-                                                        h->c_xyz.as<int4>(), h->box.as<Box>(), h->near.as<double4_32a>());
+        p2p_k<float, false><<<h->nleaves, P2P_T, 0, s>>>(h->xs32.as<float4>(), nullptr, lv, cb, ce, pp, ps, out);
     count_launch(h);
     check_launch("p2p");
 }

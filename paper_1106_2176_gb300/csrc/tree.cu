@@ -354,9 +354,13 @@ static bool radix_sort(fmm_ctx *h, uint64_t *k, int *v, uint64_t *kt, int *vt, i
     return swapped;
 }
 
+// Sorted particles (x, y, z, q). For the mixed path the FP32 copy holds the
+// rounded coordinates, and xs32lo the FP32 rounding of the remainder x - hi
+// (zero for FP32 inputs), so that a near-field difference can be formed as
+// (hi_i - hi_j) + (lo_i - lo_j) without the rounding of the positions.
 template <class T>
 __global__ void gather_k(const T *__restrict__ x, const T *__restrict__ q, const int *__restrict__ idx, int64_t n,
-                         double4_32a *__restrict__ xs64, float4 *__restrict__ xs32)
+                         double4_32a *__restrict__ xs64, float4 *__restrict__ xs32, float4 *__restrict__ xs32lo)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -364,7 +368,11 @@ __global__ void gather_k(const T *__restrict__ x, const T *__restrict__ q, const
     double a = (double)x[3 * (int64_t)j], b = (double)x[3 * (int64_t)j + 1], c = (double)x[3 * (int64_t)j + 2];
     double d = (double)q[j];
     if (xs64) xs64[i] = make_double4_32a(a, b, c, d);
-    if (xs32) xs32[i] = make_float4((float)a, (float)b, (float)c, (float)d);
+    if (xs32) {
+        const float ha = (float)a, hb = (float)b, hc = (float)c;
+        xs32[i] = make_float4(ha, hb, hc, (float)d);
+        if (xs32lo) xs32lo[i] = make_float4((float)(a - ha), (float)(b - hb), (float)(c - hc), 0.f);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -675,28 +683,6 @@ __global__ void leaves_write_k(int nc, const int *__restrict__ nchild, const uns
     if (c < nc && nchild[c] == 0) leaves[off[c]] = c;
 }
 
-// FP32 particle coordinates relative to the centre of their leaf, computed
-// from FP64 positions (mixed precision): the P2P kernel then works with
-// offsets of the size of a cell, so rounding to FP32 costs ~6e-8 of the cell
-// width rather than of the root-box coordinate.
-template <class P4>
-__global__ void local_coords_k(const int *__restrict__ leaves, const int *__restrict__ begin, const int *__restrict__ end,
-                               const int4 *__restrict__ xyz, const Box *__restrict__ box, const P4 *__restrict__ src,
-                               float4 *__restrict__ xs32)
-{
-    const int c = leaves[blockIdx.x];
-    const int4 a = xyz[c];
-    const double h = box->h;
-    const double half = ldexp(1.0, FMM_MAXLEVEL - 1 - a.w);
-    const double cx = __dadd_rn(box->origin[0], __dmul_rn((double)a.x + half, h));
-    const double cy = __dadd_rn(box->origin[1], __dmul_rn((double)a.y + half, h));
-    const double cz = __dadd_rn(box->origin[2], __dmul_rn((double)a.z + half, h));
-    for (int j = begin[c] + threadIdx.x; j < end[c]; j += blockDim.x) {
-        const P4 v = src[j];
-        xs32[j] = make_float4((float)((double)v.x - cx), (float)((double)v.y - cy), (float)((double)v.z - cz), (float)v.w);
-    }
-}
-
 // ---------------------------------------------------------------------------
 // host orchestration
 // ---------------------------------------------------------------------------
@@ -742,10 +728,17 @@ void tree_build(fmm_ctx *h, const void *x, const void *q, int64_t n, int dt)
     if (mixed) h->xs32.ensure(sizeof(float4) * n);
     double4_32a *xs64 = need64 ? h->xs64.as<double4_32a>() : nullptr;
     float4 *xs32 = mixed ? h->xs32.as<float4>() : nullptr;
+    float4 *xs32lo = nullptr;
+    if (mixed && dt == FMM_F64) {
+        h->xs32lo.ensure(sizeof(float4) * n);
+        xs32lo = h->xs32lo.as<float4>();
+    }
     if (dt == FMM_F64)
-        gather_k<double><<<nblocks(n, TB), TB, 0, s>>>((const double *)x, (const double *)q, h->idx.as<int>(), n, xs64, xs32);
+        gather_k<double><<<nblocks(n, TB), TB, 0, s>>>((const double *)x, (const double *)q, h->idx.as<int>(), n, xs64, xs32,
+                                                       xs32lo);
     else
-        gather_k<float><<<nblocks(n, TB), TB, 0, s>>>((const float *)x, (const float *)q, h->idx.as<int>(), n, xs64, xs32);
+        gather_k<float><<<nblocks(n, TB), TB, 0, s>>>((const float *)x, (const float *)q, h->idx.as<int>(), n, xs64, xs32,
+                                                      xs32lo);
     count_launch(h);
     check_launch("gather");
 
@@ -831,20 +824,6 @@ void tree_build(fmm_ctx *h, const void *x, const void *q, int64_t n, int dt)
         FMM_CUDA_TRY(cudaMemcpyAsync(hp, tot, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
         FMM_CUDA_TRY(cudaStreamSynchronize(s));
         h->nleaves = (int)*hp;
-    }
-
-    // mixed precision: FP32 coordinates local to the leaf
-    if (mixed && h->nleaves > 0) {
-        if (need64)
-            local_coords_k<double4_32a><<<h->nleaves, 128, 0, s>>>(h->leaves.as<int>(), h->c_begin.as<int>(), h->c_end.as<int>(),
-                                                                   h->c_xyz.as<int4>(), box, h->xs64.as<double4_32a>(),
-                                                                   h->xs32.as<float4>());
-        else
-            local_coords_k<float4><<<h->nleaves, 128, 0, s>>>(h->leaves.as<int>(), h->c_begin.as<int>(), h->c_end.as<int>(),
-                                                              h->c_xyz.as<int4>(), box, h->xs32.as<float4>(),
-                                                              h->xs32.as<float4>());
-        count_launch(h);
-        check_launch("local coordinates");
     }
 
     // 5. dual traversal
