@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=100_000)
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg (profiling runs)")
     return ap.parse_args()
 
 
@@ -162,6 +163,37 @@ def p2p_traffic(interactions, n):
         return None
 
 
+def run_e2e(a, x, q, N, ncrit, world, dist, dev):
+    """Same metric through the C ABI with pinned host buffers: every step copies
+    x and q to the device and phi and grad back."""
+    import torch
+    from paper_1106_2176_gb300 import FMM
+    xh = torch.from_numpy(x).pin_memory()
+    qh = torch.from_numpy(q).pin_memory()
+    ph = torch.empty(N, dtype=torch.float32).pin_memory()
+    gh = torch.empty((N, 3), dtype=torch.float32).pin_memory()
+    fh = FMM(N, p=a.p, theta=a.theta, ncrit=ncrit, precision=a.precision)
+    for _ in range(2):
+        fh.build(xh.numpy(), qh.numpy())
+        fh.evaluate(ph.numpy(), gh.numpy())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        fh.build(xh.numpy(), qh.numpy())
+        fh.evaluate(ph.numpy(), gh.numpy())
+    torch.cuda.synchronize()
+    e2e_ms = 1000.0 * (time.perf_counter() - t0) / a.steps
+    if dist:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    fh.close()
+    e2e = {"value": N * world / (e2e_ms / 1000.0), "unit": "particles/s", "ms_per_step": e2e_ms,
+           "h2d_bytes_per_step": int(x.nbytes + q.nbytes), "d2h_bytes_per_step": int(ph.numpy().nbytes + gh.numpy().nbytes)}
+
+    return e2e
+
+
 def main():
     a = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -239,17 +271,20 @@ def main():
     value = N * world / (ms / 1000.0)
 
     # accuracy: sampled targets against the FP64 direct sum on the GPU
-    tg = inputs.sample_targets(N, a.targets, seed=3)
-    tgt = torch.tensor(tg, device=dev)
-    x64, q64 = xt.double(), qt.double()
-    pd, gd = f.direct(x64, q64, tgt)
     rel = lambda u, v: float(torch.linalg.norm(u - v) / torch.linalg.norm(v))
-    err_phi = rel(phi[tgt].double(), pd)
-    err_grad = rel(grad[tgt].double(), gd)
+    x64, q64 = xt.double(), qt.double()
+    err_phi = err_grad = None
+    tg = []
+    if a.targets > 0:
+        tg = inputs.sample_targets(N, a.targets, seed=3)
+        tgt = torch.tensor(tg, device=dev)
+        pd, gd = f.direct(x64, q64, tgt)
+        err_phi = rel(phi[tgt].double(), pd)
+        err_grad = rel(grad[tgt].double(), gd)
 
     # FP64 path on the same GPU (one step, for the mixed-vs-FP64 comparison)
     fp64 = None
-    if not a.no_fp64 and rank == 0:
+    if not a.no_fp64 and rank == 0 and a.targets > 0:
         f64 = FMM(N, p=a.p, theta=a.theta, ncrit=ncrit, precision="fp64")
         p64 = torch.empty(N, dtype=torch.float64, device=dev)
         g64 = torch.empty((N, 3), dtype=torch.float64, device=dev)
@@ -270,29 +305,12 @@ def main():
         del p64, g64
 
     # end to end through the C ABI with pinned host buffers
-    xh = torch.from_numpy(x).pin_memory()
-    qh = torch.from_numpy(q).pin_memory()
-    ph = torch.empty(N, dtype=torch.float32).pin_memory()
-    gh = torch.empty((N, 3), dtype=torch.float32).pin_memory()
-    fh = FMM(N, p=a.p, theta=a.theta, ncrit=ncrit, precision=a.precision)
-    for _ in range(2):
-        fh.build(xh.numpy(), qh.numpy())
-        fh.evaluate(ph.numpy(), gh.numpy())
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(a.steps):
-        fh.build(xh.numpy(), qh.numpy())
-        fh.evaluate(ph.numpy(), gh.numpy())
-    torch.cuda.synchronize()
-    e2e_ms = 1000.0 * (time.perf_counter() - t0) / a.steps
-    if dist:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    fh.close()
-    e2e = {"value": N * world / (e2e_ms / 1000.0), "unit": "particles/s", "ms_per_step": e2e_ms,
-           "h2d_bytes_per_step": int(x.nbytes + q.nbytes), "d2h_bytes_per_step": int(ph.numpy().nbytes + gh.numpy().nbytes)}
+    e2e = None
+    if not a.no_e2e:
+        e2e = run_e2e(a, x, q, N, ncrit, world, dist, dev)
 
+    # roofline of the dominant kernel (P2P, FP32 FMA pipe)
+    qh = torch.from_numpy(q).pin_memory()
     # roofline of the dominant kernel (P2P, FP32 FMA pipe)
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     peaks = {}
