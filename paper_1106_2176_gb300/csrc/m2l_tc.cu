@@ -262,14 +262,28 @@ __global__ void __launch_bounds__(128, 1)
 #pragma unroll
     for (int k = 0; k < (C::COMP ? NP : 1); k++) acc_lo[k] = 0.f;
 
+    // source cells of the next QV vectors, looked up QV vectors ahead of use so
+    // that the lattice-map loads are off the critical path (a shift register:
+    // compile-time indices only)
+    constexpr int QV = 8;
+    auto lookup = [&](int vi) -> int {
+        if (cell < 0 || vi >= nv) return -1;
+        const int4 v = st[e0 + vi];
+        return level_lookup(LD, map_pool, anchor, l, px + v.x, py + v.y, pz + v.z);
+    };
+    int srcq[QV];
+#pragma unroll
+    for (int i = 0; i < QV; i++) srcq[i] = lookup(i);
     int src = -1;
     int issued_b = 0;  // thread 0: operator copies issued
     auto load_unit = [&](int u) {
         const int s = u % NS;
         const int vi = u / KB, kb = u % KB;
         if (kb == 0) {
-            const int4 v = st[e0 + vi];
-            src = (cell >= 0) ? level_lookup(LD, map_pool, anchor, l, px + v.x, py + v.y, pz + v.z) : -1;
+            src = srcq[0];
+#pragma unroll
+            for (int i = 0; i < QV - 1; i++) srcq[i] = srcq[i + 1];
+            srcq[QV - 1] = lookup(vi + QV);
         }
         unsigned char *sa = base + s * C::STAGE;
         const uint32_t ahi = smem_u32(sa), alo = smem_u32(sa + C::A_BYTES);

@@ -32,15 +32,36 @@ struct Vec4<double> { using type = double4_32a; };
 __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 
-template <class T, class T4>
+// One source s against target t. CHECK: the source segment may contain the
+// target itself or particles at the same position (only the target's own
+// leaf can: equal positions have equal Morton keys), which contribute nothing.
+template <bool CHECK, class T, class T4>
 __device__ __forceinline__ void interact(const T4 &t, const T4 &s, T &p, T &gx, T &gy, T &gz)
 {
     const T dx = t.x - s.x, dy = t.y - s.y, dz = t.z - s.z;
     const T r2 = dx * dx + dy * dy + dz * dz;
     T ri = rsq(r2);
-    ri = r2 > T(0) ? ri : T(0);
+    if (CHECK) ri = r2 > T(0) ? ri : T(0);
     const T qr = s.w * ri;
     const T qr3 = qr * ri * ri;
+    p += qr;
+    gx -= qr3 * dx;
+    gy -= qr3 * dy;
+    gz -= qr3 * dz;
+}
+
+// The same with every coordinate carried as an FP32 pair (hi, lo): the
+// difference (hi_i - hi_j) + (lo_i - lo_j) keeps the accuracy of FP64 inputs.
+template <bool CHECK, class T4>
+__device__ __forceinline__ void interact_ds(const T4 &t, const float4 &tl, const T4 &s, const float4 &sl, float &p,
+                                            float &gx, float &gy, float &gz)
+{
+    const float dx = (t.x - s.x) + (tl.x - sl.x), dy = (t.y - s.y) + (tl.y - sl.y), dz = (t.z - s.z) + (tl.z - sl.z);
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    float ri = rsqrtf(r2);
+    if (CHECK) ri = r2 > 0.f ? ri : 0.f;
+    const float qr = s.w * ri;
+    const float qr3 = qr * ri * ri;
     p += qr;
     gx -= qr3 * dx;
     gy -= qr3 * dy;
@@ -60,27 +81,41 @@ __device__ __forceinline__ void acc2(double &hi, double &lo, double b) { hi += b
 
 constexpr int P2P_T = 128;
 
-template <class T4>
-__device__ __forceinline__ void interact_ds(const T4 &t, const float4 &tl, const T4 &s, const float4 &sl, float &p, float &gx,
-                                            float &gy, float &gz)
+// Sources [j0, j1) of the shared chunk against the TPT targets of a thread, in
+// blocks of 64 whose sums are added with TwoSum.
+template <bool CHECK, bool DS, int TPT, class T, class T4>
+__device__ __forceinline__ void p2p_range(int j0, int j1, const T4 *sh, const float4 *shlo, const T4 (&x)[TPT],
+                                          const float4 (&xl)[TPT], T (&h)[4 * TPT], T (&lo)[4 * TPT])
 {
-    const float dx = (t.x - s.x) + (tl.x - sl.x), dy = (t.y - s.y) + (tl.y - sl.y), dz = (t.z - s.z) + (tl.z - sl.z);
-    const float r2 = dx * dx + dy * dy + dz * dz;
-    float ri = rsqrtf(r2);
-    ri = r2 > 0.f ? ri : 0.f;
-    const float qr = s.w * ri;
-    const float qr3 = qr * ri * ri;
-    p += qr;
-    gx -= qr3 * dx;
-    gy -= qr3 * dy;
-    gz -= qr3 * dz;
+    for (int jb = j0; jb < j1; jb += 64) {
+        const int je = min(j1, jb + 64);
+        T b[4 * TPT];
+#pragma unroll
+        for (int c = 0; c < 4 * TPT; c++) b[c] = T(0);
+#pragma unroll 2
+        for (int j = jb; j < je; j++) {
+            const T4 s = sh[j];
+            if constexpr (DS) {
+                const float4 q = shlo[j];
+#pragma unroll
+                for (int k = 0; k < TPT; k++)
+                    interact_ds<CHECK>(x[k], xl[k], s, q, b[4 * k], b[4 * k + 1], b[4 * k + 2], b[4 * k + 3]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < TPT; k++) interact<CHECK>(x[k], s, b[4 * k], b[4 * k + 1], b[4 * k + 2], b[4 * k + 3]);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 4 * TPT; c++) acc2(h[c], lo[c], b[c]);
+    }
 }
 
-// DS (FP32 path, FP64 input): every coordinate is carried as an FP32 pair
-// (hi, lo) and a difference is formed as (hi_i - hi_j) + (lo_i - lo_j); for
-// nearby particles hi_i - hi_j is exact, so the near field keeps the accuracy
-// of the FP64 positions. FP32 inputs have lo = 0 and use the plain form.
-template <class T, bool DS>
+// One block per target leaf. A thread owns TPT targets (rows of R =
+// ceil(n / TPT)) and one of S = 128 / R slices of the source stream; source
+// leaves are concatenated into a shared chunk; the target leaf's own segment is
+// the only one that needs the j == i / r == 0 test. Slices are reduced in FP64
+// in a fixed order. DS: FP32 (hi, lo) coordinates for FP64 inputs.
+template <class T, bool DS, int TPT>
 __global__ void __launch_bounds__(P2P_T) p2p_k(const typename Vec4<T>::type *__restrict__ xs, const float4 *__restrict__ xlo,
                                                const int *__restrict__ leaves, const int *__restrict__ begin,
                                                const int *__restrict__ end, const int *__restrict__ ptr,
@@ -90,30 +125,33 @@ __global__ void __launch_bounds__(P2P_T) p2p_k(const typename Vec4<T>::type *__r
     constexpr int CH = (DS || sizeof(T) == 8) ? 1024 : 2048;
     __shared__ T4 sh[CH];
     __shared__ float4 shlo[DS ? CH : 1];
-    __shared__ double red[P2P_T * 8];
+    static_assert(sizeof(T4) * CH >= sizeof(double) * P2P_T * 4 * TPT, "slice sums reuse the source chunk");
+    double *red = reinterpret_cast<double *>(sh);  // slice sums, after the last chunk
     const int A = leaves[blockIdx.x];
     const int tb = begin[A], te = end[A];
     const int k0 = ptr[A], k1 = ptr[A + 1];
-    for (int t0 = tb; t0 < te; t0 += 2 * P2P_T) {
-        const int nt = min(2 * P2P_T, te - t0);
-        const int R = (nt + 1) >> 1;
+    for (int t0 = tb; t0 < te; t0 += TPT * P2P_T) {
+        const int nt = min(TPT * P2P_T, te - t0);
+        const int R = (nt + TPT - 1) / TPT;
         const int S = max(1, P2P_T / R);
         const int row = threadIdx.x % R, sl = threadIdx.x / R;
         const bool act = sl < S;
-        const bool has1 = act && (row + R < nt);
-        T4 x0 = {}, x1 = {};
-        float4 l0 = {}, l1 = {};
-        if (act) {
-            x0 = xs[t0 + row];
-            if (DS) l0 = xlo[t0 + row];
+        T4 x[TPT];
+        float4 xl[TPT];
+#pragma unroll
+        for (int k = 0; k < TPT; k++) {
+            const int i = (act && row + k * R < nt) ? t0 + row + k * R : t0;
+            x[k] = xs[i];
+            if constexpr (DS) xl[k] = xlo[i];
+            else xl[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        x1 = has1 ? xs[t0 + row + R] : x0;
-        if (DS) l1 = has1 ? xlo[t0 + row + R] : l0;
-        T h[8] = {0, 0, 0, 0, 0, 0, 0, 0}, lo[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        T h[4 * TPT], lo[4 * TPT];
+#pragma unroll
+        for (int c = 0; c < 4 * TPT; c++) h[c] = lo[c] = T(0);
         int k = k0, off = 0;
         while (k < k1) {
             __syncthreads();
-            int fill = 0;
+            int fill = 0, slo = 0, shi = 0;
             while (k < k1 && fill < CH) {
                 const int B = src[k];
                 const int b0 = begin[B] + off;
@@ -121,7 +159,11 @@ __global__ void __launch_bounds__(P2P_T) p2p_k(const typename Vec4<T>::type *__r
                 const int take = min(blen, CH - fill);
                 for (int j = threadIdx.x; j < take; j += P2P_T) {
                     sh[fill + j] = xs[b0 + j];
-                    if (DS) shlo[fill + j] = xlo[b0 + j];
+                    if constexpr (DS) shlo[fill + j] = xlo[b0 + j];
+                }
+                if (B == A) {
+                    slo = fill;
+                    shi = fill + take;
                 }
                 fill += take;
                 if (take == blen) {
@@ -132,39 +174,28 @@ __global__ void __launch_bounds__(P2P_T) p2p_k(const typename Vec4<T>::type *__r
             __syncthreads();
             if (act) {
                 const int jlo = (int)(((long long)fill * sl) / S), jhi = (int)(((long long)fill * (sl + 1)) / S);
-                for (int j0 = jlo; j0 < jhi; j0 += 64) {
-                    const int j1 = min(jhi, j0 + 64);
-                    T b[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-#pragma unroll 4
-                    for (int j = j0; j < j1; j++) {
-                        const T4 s = sh[j];
-                        if constexpr (DS) {
-                            const float4 q = shlo[j];
-                            interact_ds(x0, l0, s, q, b[0], b[1], b[2], b[3]);
-                            interact_ds(x1, l1, s, q, b[4], b[5], b[6], b[7]);
-                        } else {
-                            interact(x0, s, b[0], b[1], b[2], b[3]);
-                            interact(x1, s, b[4], b[5], b[6], b[7]);
-                        }
-                    }
-#pragma unroll
-                    for (int c = 0; c < 8; c++) acc2(h[c], lo[c], b[c]);
-                }
+                p2p_range<false, DS, TPT>(jlo, min(jhi, slo), sh, shlo, x, xl, h, lo);
+                p2p_range<true, DS, TPT>(max(jlo, slo), min(jhi, shi), sh, shlo, x, xl, h, lo);
+                p2p_range<false, DS, TPT>(max(jlo, shi), jhi, sh, shlo, x, xl, h, lo);
             }
         }
         __syncthreads();
         if (act) {
 #pragma unroll
-            for (int c = 0; c < 8; c++) red[(sl * R + row) * 8 + c] = (double)h[c] + (double)lo[c];
+            for (int c = 0; c < 4 * TPT; c++) red[(sl * R + row) * 4 * TPT + c] = (double)h[c] + (double)lo[c];
         }
         __syncthreads();
         if ((int)threadIdx.x < R) {
-            double o[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            double o[4 * TPT];
+#pragma unroll
+            for (int c = 0; c < 4 * TPT; c++) o[c] = 0.0;
             for (int s2 = 0; s2 < S; s2++)
 #pragma unroll
-                for (int c = 0; c < 8; c++) o[c] += red[(s2 * R + threadIdx.x) * 8 + c];
-            near[t0 + threadIdx.x] = make_double4_32a(o[0], o[1], o[2], o[3]);
-            if ((int)threadIdx.x + R < nt) near[t0 + threadIdx.x + R] = make_double4_32a(o[4], o[5], o[6], o[7]);
+                for (int c = 0; c < 4 * TPT; c++) o[c] += red[(s2 * R + threadIdx.x) * 4 * TPT + c];
+#pragma unroll
+            for (int kk = 0; kk < TPT; kk++)
+                if ((int)threadIdx.x + kk * R < nt)
+                    near[t0 + threadIdx.x + kk * R] = make_double4_32a(o[4 * kk], o[4 * kk + 1], o[4 * kk + 2], o[4 * kk + 3]);
         }
     }
 }
@@ -177,11 +208,12 @@ void near_field(fmm_ctx *h, cudaStream_t s)
     const int *pp = h->p2p_ptr.as<int>(), *ps = h->p2p_src.as<int>();
     double4_32a *out = h->near.as<double4_32a>();
     if (h->precision == FMM_FP64)
-        p2p_k<double, false><<<h->nleaves, P2P_T, 0, s>>>(h->xs64.as<double4_32a>(), nullptr, lv, cb, ce, pp, ps, out);
+        p2p_k<double, false, 2><<<h->nleaves, P2P_T, 0, s>>>(h->xs64.as<double4_32a>(), nullptr, lv, cb, ce, pp, ps, out);
     else if (h->dtype == FMM_F64)
-        p2p_k<float, true><<<h->nleaves, P2P_T, 0, s>>>(h->xs32.as<float4>(), h->xs32lo.as<float4>(), lv, cb, ce, pp, ps, out);
+        p2p_k<float, true, 3><<<h->nleaves, P2P_T, 0, s>>>(h->xs32.as<float4>(), h->xs32lo.as<float4>(), lv, cb, ce, pp, ps,
+                                                           out);
     else
-        p2p_k<float, false><<<h->nleaves, P2P_T, 0, s>>>(h->xs32.as<float4>(), nullptr, lv, cb, ce, pp, ps, out);
+        p2p_k<float, false, 3><<<h->nleaves, P2P_T, 0, s>>>(h->xs32.as<float4>(), nullptr, lv, cb, ce, pp, ps, out);
     count_launch(h);
     check_launch("p2p");
 }

@@ -636,26 +636,35 @@ __global__ void oct_count_k(int c0, int nc, const int *__restrict__ level, const
     atomicAdd(&grp[l * 8 + o], 1u);
 }
 
-// one thread: group offsets and tile descriptors, levels 2..depth
+// One thread: group offsets and tile descriptors, levels 2..depth. Within a
+// level the tiles of the 8 octant groups are interleaved (tile k of octant 0,
+// tile k of octant 1, ...): each group is in Morton order, so tiles that run
+// at the same time cover one compact region and share sources in L2.
 __global__ void tiles_k(int depth, int tile, const unsigned *__restrict__ grp, unsigned *__restrict__ goff,
                         M2LTile *__restrict__ tiles, int *__restrict__ ntiles)
 {
     unsigned run = 0;
     int nt = 0;
-    for (int l = 2; l <= depth; l++)
+    for (int l = 2; l <= depth; l++) {
+        unsigned kmax = 0;
         for (int o = 0; o < 8; o++) {
-            unsigned c = grp[l * 8 + o];
+            const unsigned c = grp[l * 8 + o];
             goff[l * 8 + o] = run;
-            for (unsigned t = 0; t < c; t += tile) {
+            run += c;
+            kmax = max(kmax, (c + tile - 1) / tile);
+        }
+        for (unsigned k = 0; k < kmax; k++)
+            for (int o = 0; o < 8; o++) {
+                const unsigned c = grp[l * 8 + o], t = k * tile;
+                if (t >= c) continue;
                 M2LTile d;
-                d.start = (int)(run + t);
+                d.start = (int)(goff[l * 8 + o] + t);
                 d.count = (int)min((unsigned)tile, c - t);
                 d.level = l;
                 d.octant = o;
                 tiles[nt++] = d;
             }
-            run += c;
-        }
+    }
     *ntiles = nt;
 }
 
