@@ -165,6 +165,7 @@ struct fmm_ctx {
     fmm::DevBuf p2p_pairs, m2lx_pairs;
     fmm::DevBuf pair_keys, pair_keys2, pair_vals, pair_vals2;
     fmm::DevBuf p2p_ptr, p2p_src, m2lx_ptr, m2lx_src, row_cnt;
+    fmm::DevBuf p2p_runs, p2p_nrun;     // P2P sources merged into particle runs per target leaf
     fmm::DevBuf counters;
     fmm::DevBuf lvl_desc, map_pool;
     fmm::DevBuf m2l_tgt, m2l_tiles, m2l_misc;

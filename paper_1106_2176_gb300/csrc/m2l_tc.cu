@@ -77,6 +77,10 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32
 {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
 }
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
@@ -166,7 +170,11 @@ struct TcCfg {
     static constexpr int B_BYTES = 2 * NP * 128;          // one k-block of [T_hi ; T_lo]
     static constexpr int STAGE = 2 * A_BYTES + B_BYTES;   // multiple of 1024
     static constexpr int NS = (200 * 1024) / STAGE >= 4 ? 4 : ((200 * 1024) / STAGE >= 3 ? 3 : 2);
-    static constexpr int SMEM = NS * STAGE + 1024 + 1024;  // + barriers, + alignment slack
+    static constexpr int QV = 8;                           // lookahead of the source lookups (vectors)
+    static constexpr int RING = 2 * QV * M * 4;            // lookup ring: 2 QV slots x 128 rows
+    static constexpr int FIXED = NS * STAGE + 256 + RING;  // stages, barriers, lookup ring
+    static constexpr int SMEM_MAX = 227 * 1024 - 1024;     // minus the alignment slack
+    static constexpr int ST_MAX = (SMEM_MAX - FIXED) / 16; // stencil entries that fit in shared memory
     static constexpr int TCOLS = 4 * NP <= 32 ? 32 : (4 * NP <= 64 ? 64 : (4 * NP <= 128 ? 128 : (4 * NP <= 256 ? 256 : 512)));
     static constexpr int GV = 8;                          // vectors per accumulator drain
     static constexpr bool COMP = NP <= 64;                // compensated registers for the drained sums
@@ -202,6 +210,8 @@ __global__ void __launch_bounds__(128, 1)
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *bar = reinterpret_cast<uint64_t *>(base + NS * C::STAGE);
+    int *ring = reinterpret_cast<int *>(base + NS * C::STAGE + 256);          // [2 QV][128]
+    int4 *s_st = reinterpret_cast<int4 *>(base + NS * C::STAGE + 256 + C::RING); // stencil of the octant
     uint64_t *full_a = bar;            // NS, 128 arrivals
     uint64_t *full_b = bar + NS;       // NS, 1 arrival + tx bytes
     uint64_t *mma_done = bar + 2 * NS; // NS, MMA commits
@@ -262,28 +272,45 @@ __global__ void __launch_bounds__(128, 1)
 #pragma unroll
     for (int k = 0; k < (C::COMP ? NP : 1); k++) acc_lo[k] = 0.f;
 
-    // source cells of the next QV vectors, looked up QV vectors ahead of use so
-    // that the lattice-map loads are off the critical path (a shift register:
-    // compile-time indices only)
-    constexpr int QV = 8;
-    auto lookup = [&](int vi) -> int {
-        if (cell < 0 || vi >= nv) return -1;
-        const int4 v = st[e0 + vi];
-        return level_lookup(LD, map_pool, anchor, l, px + v.x, py + v.y, pz + v.z);
+    // The stencil of the octant in shared memory when it fits.
+    const bool st_in_smem = nv <= C::ST_MAX;
+    if (st_in_smem)
+        for (int i = tid; i < nv; i += 128) s_st[i] = st[e0 + i];
+    __syncthreads();
+    const int4 *stp = st_in_smem ? s_st : st + e0;
+
+    // Source cell of vector vi for this row, fetched QV vectors ahead of use
+    // into ring slot vi % (2 QV): with a dense lattice map the entry is copied
+    // by cp.async straight into shared memory, so no load result is waited
+    // for on the critical path; other levels search the level's sorted keys.
+    constexpr int QV = C::QV;
+    auto fetch = [&](int vi) {
+        const uint32_t slot = smem_u32(ring + (vi % (2 * QV)) * 128 + tid);
+        int r = -1;
+        if (cell >= 0 && vi < nv) {
+            const int4 v = stp[vi];
+            const int x = px + v.x, y = py + v.y, z = pz + v.z, side = 1 << l;
+            if (x >= 0 && y >= 0 && z >= 0 && x < side && y < side && z < side) {
+                if (LD.map_off >= 0) {
+                    cp_async4(slot, map_pool + LD.map_off + (long long)morton3((uint32_t)x, (uint32_t)y, (uint32_t)z));
+                    return;
+                }
+                r = level_lookup(LD, map_pool, anchor, l, x, y, z);
+            }
+        }
+        ring[(vi % (2 * QV)) * 128 + tid] = r;
     };
-    int srcq[QV];
-#pragma unroll
-    for (int i = 0; i < QV; i++) srcq[i] = lookup(i);
+    for (int i = 0; i < QV; i++) fetch(i);
+    cp_async_commit();
+    cp_async_wait_all();
     int src = -1;
     int issued_b = 0;  // thread 0: operator copies issued
     auto load_unit = [&](int u) {
         const int s = u % NS;
         const int vi = u / KB, kb = u % KB;
         if (kb == 0) {
-            src = srcq[0];
-#pragma unroll
-            for (int i = 0; i < QV - 1; i++) srcq[i] = srcq[i + 1];
-            srcq[QV - 1] = lookup(vi + QV);
+            src = ring[(vi % (2 * QV)) * 128 + tid];
+            fetch(vi + QV);
         }
         unsigned char *sa = base + s * C::STAGE;
         const uint32_t ahi = smem_u32(sa), alo = smem_u32(sa + C::A_BYTES);
@@ -298,7 +325,7 @@ __global__ void __launch_bounds__(128, 1)
         }
         cp_async_commit();
         if (tid == 0) {
-            const int4 v = st[e0 + vi];
+            const int4 v = stp[vi];
             mbar_arrive_tx(&full_b[s], C::B_BYTES);
             bulk_g2s(smem_u32(sa + 2 * C::A_BYTES), ttab + ((size_t)v.w * KB + kb) * C::B_BYTES, C::B_BYTES, &full_b[s]);
             issued_b = u + 1;
@@ -583,16 +610,20 @@ static void launch_tc(fmm_ctx *h, float *L, const float *M)
     h->msplit.ensure(sizeof(float) * (size_t)nc * KB * 64);
     msplit_k<<<nblk((int64_t)(nc - c0) * KB * 32, 256), 256, 0, s>>>(M, h->p * h->p, KB, c0, nc, h->msplit.as<float>());
     count_launch(h);
-    static bool attr = false;
-    if (!attr) {
-        FMM_CUDA_TRY(cudaFuncSetAttribute(m2l_tc_k<NP, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
-        attr = true;
+    // stencil in shared memory when the largest octant stencil fits
+    int nvmax = 0;
+    for (int o = 0; o < 8; o++) nvmax = std::max(nvmax, h->st_off[o + 1] - h->st_off[o]);
+    const int smem = 1024 + C::FIXED + (nvmax <= C::ST_MAX ? 16 * nvmax : 0);
+    static int attr = 0;
+    if (smem > attr) {
+        FMM_CUDA_TRY(cudaFuncSetAttribute(m2l_tc_k<NP, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        attr = smem;
     }
     const int *st_off = reinterpret_cast<const int *>(h->st_dev.as<char>() + sizeof(int4) * h->st_off[8]);
     const int *ntiles = reinterpret_cast<const int *>(h->m2l_misc.as<unsigned>() + 24 * (FMM_MAXLEVEL + 1));
     int *err = reinterpret_cast<int *>(h->m2l_misc.as<unsigned>() + 24 * (FMM_MAXLEVEL + 1) + 4);
     FMM_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
-    m2l_tc_k<NP, KB><<<h->ntiles_max, 128, C::SMEM, s>>>(h->p, h->m2l_tiles.as<M2LTile>(), ntiles, h->m2l_tgt.as<int>(),
+    m2l_tc_k<NP, KB><<<h->ntiles_max, 128, smem, s>>>(h->p, h->m2l_tiles.as<M2LTile>(), ntiles, h->m2l_tgt.as<int>(),
                                                          h->c_xyz.as<int4>(), h->c_anchor.as<uint64_t>(),
                                                          h->lvl_desc.as<LevelDesc>(), h->map_pool.as<int>(),
                                                          h->st_dev.as<int4>(), st_off, h->msplit.as<float>(),

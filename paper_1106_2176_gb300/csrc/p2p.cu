@@ -110,26 +110,73 @@ __device__ __forceinline__ void p2p_range(int j0, int j1, const T4 *sh, const fl
     }
 }
 
+__device__ __forceinline__ void cpa16(void *dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cpa_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void cpa_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// Where the source stream of a target leaf stands (block-uniform).
+struct RunCursor {
+    int k, k1, off;
+};
+
 // One block per target leaf. A thread owns TPT targets (rows of R =
-// ceil(n / TPT)) and one of S = 128 / R slices of the source stream; source
-// leaves are concatenated into a shared chunk; the target leaf's own segment is
-// the only one that needs the j == i / r == 0 test. Slices are reduced in FP64
-// in a fixed order. DS: FP32 (hi, lo) coordinates for FP64 inputs.
+// ceil(n / TPT)) and one of S = 128 / R slices of the source stream. Sources
+// come as particle runs (adjacent source leaves merged); chunks of CH sources
+// are copied into shared memory with cp.async, the next chunk while the
+// current one is computed (two buffers). Only the target leaf's own particles
+// need the j == i / r == 0 test. Slices are reduced in FP64 in a fixed order.
+// DS: FP32 (hi, lo) coordinates for FP64 inputs.
 template <class T, bool DS, int TPT>
 __global__ void __launch_bounds__(P2P_T) p2p_k(const typename Vec4<T>::type *__restrict__ xs, const float4 *__restrict__ xlo,
                                                const int *__restrict__ leaves, const int *__restrict__ begin,
                                                const int *__restrict__ end, const int *__restrict__ ptr,
-                                               const int *__restrict__ src, double4_32a *__restrict__ near)
+                                               const int2 *__restrict__ runs, const int *__restrict__ nrun,
+                                               double4_32a *__restrict__ near)
 {
     using T4 = typename Vec4<T>::type;
-    constexpr int CH = (DS || sizeof(T) == 8) ? 1024 : 2048;
-    __shared__ T4 sh[CH];
-    __shared__ float4 shlo[DS ? CH : 1];
-    static_assert(sizeof(T4) * CH >= sizeof(double) * P2P_T * 4 * TPT, "slice sums reuse the source chunk");
-    double *red = reinterpret_cast<double *>(sh);  // slice sums, after the last chunk
+    constexpr int CH = DS ? 512 : (sizeof(T) == 8 ? 512 : 1024);
+    __shared__ T4 sh[2][CH];
+    __shared__ float4 shlo[DS ? 2 : 1][DS ? CH : 1];
+    static_assert(sizeof(T4) * 2 * CH >= sizeof(double) * P2P_T * 4 * TPT, "slice sums reuse the source buffers");
+    double *red = reinterpret_cast<double *>(&sh[0][0]);  // slice sums, after the last chunk
     const int A = leaves[blockIdx.x];
     const int tb = begin[A], te = end[A];
-    const int k0 = ptr[A], k1 = ptr[A + 1];
+    const int r0 = ptr[A], r1 = ptr[A] + nrun[A];
+
+    // copy the next chunk into buffer bf; returns its length and where the
+    // target leaf's own particles sit in it ([slo, shi), empty if absent)
+    auto stage = [&](RunCursor &cur, int bf, int &slo, int &shi) -> int {
+        int fill = 0;
+        slo = shi = 0;
+        while (cur.k < cur.k1 && fill < CH) {
+            const int2 rr = runs[cur.k];
+            const int g0 = rr.x + cur.off;
+            const int len = rr.y - g0;
+            const int take = min(len, CH - fill);
+            for (int j = threadIdx.x; j < take; j += P2P_T) {
+                cpa16(&sh[bf][fill + j], xs + g0 + j);
+                if constexpr (DS) cpa16(&shlo[bf][fill + j], xlo + g0 + j);
+            }
+            const int a = max(g0, tb), b = min(g0 + take, te);
+            if (a < b) {
+                slo = fill + a - g0;
+                shi = fill + b - g0;
+            }
+            fill += take;
+            if (take == len) {
+                cur.k++;
+                cur.off = 0;
+            } else cur.off += take;
+        }
+        cpa_commit();
+        return fill;
+    };
+
     for (int t0 = tb; t0 < te; t0 += TPT * P2P_T) {
         const int nt = min(TPT * P2P_T, te - t0);
         const int R = (nt + TPT - 1) / TPT;
@@ -148,38 +195,33 @@ __global__ void __launch_bounds__(P2P_T) p2p_k(const typename Vec4<T>::type *__r
         T h[4 * TPT], lo[4 * TPT];
 #pragma unroll
         for (int c = 0; c < 4 * TPT; c++) h[c] = lo[c] = T(0);
-        int k = k0, off = 0;
-        while (k < k1) {
-            __syncthreads();
-            int fill = 0, slo = 0, shi = 0;
-            while (k < k1 && fill < CH) {
-                const int B = src[k];
-                const int b0 = begin[B] + off;
-                const int blen = end[B] - b0;
-                const int take = min(blen, CH - fill);
-                for (int j = threadIdx.x; j < take; j += P2P_T) {
-                    sh[fill + j] = xs[b0 + j];
-                    if constexpr (DS) shlo[fill + j] = xlo[b0 + j];
-                }
-                if (B == A) {
-                    slo = fill;
-                    shi = fill + take;
-                }
-                fill += take;
-                if (take == blen) {
-                    k++;
-                    off = 0;
-                } else off += take;
+        RunCursor cur{r0, r1, 0};
+        __syncthreads();  // buffers free (previous target block or slice sums)
+        int slo, shi, fill = stage(cur, 0, slo, shi);
+        int bf = 0;
+        while (fill > 0) {
+            int nslo = 0, nshi = 0, nfill = 0;
+            if (cur.k < cur.k1) {
+                nfill = stage(cur, bf ^ 1, nslo, nshi);
+                cpa_wait1();
+            } else {
+                cpa_wait0();
             }
-            __syncthreads();
+            __syncthreads();  // chunk bf complete for every thread
             if (act) {
                 const int jlo = (int)(((long long)fill * sl) / S), jhi = (int)(((long long)fill * (sl + 1)) / S);
-                p2p_range<false, DS, TPT>(jlo, min(jhi, slo), sh, shlo, x, xl, h, lo);
-                p2p_range<true, DS, TPT>(max(jlo, slo), min(jhi, shi), sh, shlo, x, xl, h, lo);
-                p2p_range<false, DS, TPT>(max(jlo, shi), jhi, sh, shlo, x, xl, h, lo);
+                const T4 *sb = sh[bf];
+                const float4 *sbl = shlo[DS ? bf : 0];
+                p2p_range<false, DS, TPT>(jlo, min(jhi, slo), sb, sbl, x, xl, h, lo);
+                p2p_range<true, DS, TPT>(max(jlo, slo), min(jhi, shi), sb, sbl, x, xl, h, lo);
+                p2p_range<false, DS, TPT>(max(jlo, shi), jhi, sb, sbl, x, xl, h, lo);
             }
+            __syncthreads();  // chunk bf consumed before it is refilled
+            bf ^= 1;
+            fill = nfill;
+            slo = nslo;
+            shi = nshi;
         }
-        __syncthreads();
         if (act) {
 #pragma unroll
             for (int c = 0; c < 4 * TPT; c++) red[(sl * R + row) * 4 * TPT + c] = (double)h[c] + (double)lo[c];
@@ -205,15 +247,16 @@ void near_field(fmm_ctx *h, cudaStream_t s)
     h->near.ensure(sizeof(double4_32a) * (size_t)h->n);
     if (h->nleaves == 0) return;
     const int *lv = h->leaves.as<int>(), *cb = h->c_begin.as<int>(), *ce = h->c_end.as<int>();
-    const int *pp = h->p2p_ptr.as<int>(), *ps = h->p2p_src.as<int>();
+    const int *pp = h->p2p_ptr.as<int>(), *nr = h->p2p_nrun.as<int>();
+    const int2 *ru = h->p2p_runs.as<int2>();
     double4_32a *out = h->near.as<double4_32a>();
     if (h->precision == FMM_FP64)
-        p2p_k<double, false, 2><<<h->nleaves, P2P_T, 0, s>>>(h->xs64.as<double4_32a>(), nullptr, lv, cb, ce, pp, ps, out);
+        p2p_k<double, false, 2><<<h->nleaves, P2P_T, 0, s>>>(h->xs64.as<double4_32a>(), nullptr, lv, cb, ce, pp, ru, nr, out);
     else if (h->dtype == FMM_F64)
-        p2p_k<float, true, 3><<<h->nleaves, P2P_T, 0, s>>>(h->xs32.as<float4>(), h->xs32lo.as<float4>(), lv, cb, ce, pp, ps,
-                                                           out);
+        p2p_k<float, true, 3><<<h->nleaves, P2P_T, 0, s>>>(h->xs32.as<float4>(), h->xs32lo.as<float4>(), lv, cb, ce, pp, ru,
+                                                           nr, out);
     else
-        p2p_k<float, false, 3><<<h->nleaves, P2P_T, 0, s>>>(h->xs32.as<float4>(), nullptr, lv, cb, ce, pp, ps, out);
+        p2p_k<float, false, 3><<<h->nleaves, P2P_T, 0, s>>>(h->xs32.as<float4>(), nullptr, lv, cb, ce, pp, ru, nr, out);
     count_launch(h);
     check_launch("p2p");
 }

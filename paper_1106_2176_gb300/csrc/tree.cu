@@ -585,6 +585,30 @@ __global__ void interactions_k(const int *__restrict__ ptr, const int *__restric
     if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, s);
 }
 
+// P2P source leaves of a target leaf that are adjacent in the sorted particle
+// order are merged into runs [begin, end); runs of leaf A are stored at
+// [ptr[A], ptr[A] + nrun[A]) of the run array (never more runs than leaves).
+__global__ void p2p_runs_k(int nleaves, const int *__restrict__ leaves, const int *__restrict__ ptr,
+                           const int *__restrict__ src, const int *__restrict__ begin, const int *__restrict__ end,
+                           int2 *__restrict__ runs, int *__restrict__ nrun)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nleaves) return;
+    const int A = leaves[i];
+    int k = ptr[A], o = ptr[A];
+    const int k1 = ptr[A + 1];
+    while (k < k1) {
+        int b = begin[src[k]], e = end[src[k]];
+        k++;
+        while (k < k1 && begin[src[k]] == e) {
+            e = end[src[k]];
+            k++;
+        }
+        runs[o++] = make_int2(b, e);
+    }
+    nrun[A] = o - ptr[A];
+}
+
 static int bits_for(int64_t v)
 {
     int b = 1;
@@ -918,6 +942,15 @@ void tree_build(fmm_ctx *h, const void *x, const void *q, int64_t n, int dt)
     // 6. CSR lists
     pairs_to_csr(h, h->p2p_pairs.as<int2>(), h->n_p2p, h->p2p_ptr, h->p2p_src, s);
     pairs_to_csr(h, h->m2lx_pairs.as<int2>(), h->n_m2lx, h->m2lx_ptr, h->m2lx_src, s);
+    h->p2p_runs.ensure(sizeof(int2) * (size_t)std::max<int64_t>(h->n_p2p, 1));
+    h->p2p_nrun.ensure(sizeof(int) * (size_t)ncells);
+    if (h->nleaves > 0) {
+        p2p_runs_k<<<nblocks(h->nleaves, 128), 128, 0, s>>>(h->nleaves, h->leaves.as<int>(), h->p2p_ptr.as<int>(),
+                                                            h->p2p_src.as<int>(), h->c_begin.as<int>(), h->c_end.as<int>(),
+                                                            h->p2p_runs.as<int2>(), h->p2p_nrun.as<int>());
+        count_launch(h);
+        check_launch("p2p runs");
+    }
     {
         unsigned long long *acc = reinterpret_cast<unsigned long long *>(h->counters.as<char>() + sizeof(TravCounters) + 8);
         FMM_CUDA_TRY(cudaMemsetAsync(acc, 0, 8, s));
