@@ -159,7 +159,10 @@ __global__ void __launch_bounds__(P2P_T) p2p_k(const typename Vec4<T>::type *__r
             const int len = rr.y - g0;
             const int take = min(len, CH - fill);
             for (int j = threadIdx.x; j < take; j += P2P_T) {
-                cpa16(&sh[bf][fill + j], xs + g0 + j);
+#pragma unroll
+                for (int c = 0; c < (int)(sizeof(T4) / 16); c++)  // 16-byte pieces of one particle
+                    cpa16(reinterpret_cast<char *>(&sh[bf][fill + j]) + 16 * c,
+                          reinterpret_cast<const char *>(xs + g0 + j) + 16 * c);
                 if constexpr (DS) cpa16(&shlo[bf][fill + j], xlo + g0 + j);
             }
             const int a = max(g0, tb), b = min(g0 + take, te);
