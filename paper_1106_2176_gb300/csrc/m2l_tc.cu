@@ -208,7 +208,8 @@ __global__ void __launch_bounds__(128, 1)
     constexpr int NS = C::NS;
     if ((int)blockIdx.x >= *ntiles) return;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    // 1024-byte aligned start for the swizzled tiles (kept as a shared-array offset)
+    unsigned char *base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     uint64_t *bar = reinterpret_cast<uint64_t *>(base + NS * C::STAGE);
     int *ring = reinterpret_cast<int *>(base + NS * C::STAGE + 256);          // [2 QV][128]
     int4 *s_st = reinterpret_cast<int4 *>(base + NS * C::STAGE + 256 + C::RING); // stencil of the octant
@@ -314,14 +315,18 @@ __global__ void __launch_bounds__(128, 1)
         }
         unsigned char *sa = base + s * C::STAGE;
         const uint32_t ahi = smem_u32(sa), alo = smem_u32(sa + C::A_BYTES);
-        const float *row = msplit + ((size_t)(src >= 0 ? src : 0) * KB + kb) * 64;
-        const uint32_t nb = src >= 0 ? 16u : 0u;
-        const uint32_t r8 = (uint32_t)(tid & 7);
+        // the warp copies its 32 rows: 16 lanes per 256-byte (hi | lo) row, so
+        // every instruction reads two whole rows; the source cell of a row
+        // comes from the lane that owns it
+        const int lane = tid & 31, ch = lane & 15;
 #pragma unroll
-        for (int c = 0; c < 8; c++) {
-            const uint32_t off = (uint32_t)tid * 128u + (((uint32_t)c ^ r8) << 4);
-            cp_async16(ahi + off, row + 4 * c, nb);
-            cp_async16(alo + off, row + 32 + 4 * c, nb);
+        for (int i = 0; i < 16; i++) {
+            const int r = 2 * i + (lane >> 4);
+            const int sr = __shfl_sync(0xffffffffu, src, r);
+            const int row = (warp << 5) + r;
+            const float *g = msplit + ((size_t)(sr >= 0 ? sr : 0) * KB + kb) * 64 + ch * 4;
+            const uint32_t dst = (ch < 8 ? ahi : alo) + (uint32_t)row * 128u + ((((uint32_t)ch & 7u) ^ ((uint32_t)row & 7u)) << 4);
+            cp_async16(dst, g, sr >= 0 ? 16u : 0u);
         }
         cp_async_commit();
         if (tid == 0) {
