@@ -189,6 +189,28 @@ FMM_API int fmm_direct(fmm_handle h, const double *x, const double *q, int64_t n
 
 FMM_API int fmm_destroy(fmm_handle h);
 
+/*
+ * Allocation-free Morton keys and stable sort (the paper has no counterpart:
+ * this is an interface for callers that cannot allocate device memory, such
+ * as code recording a CUDA graph, where cudaMalloc cannot be captured, or an
+ * application whose device memory is managed by someone else).
+ *   x: n*3 positions on the device, dtype FMM_F32 or FMM_F64 (no host memory);
+ *   keys[n], perm[n]: device outputs, the same sorted 63-bit Morton keys and
+ *   permutation (perm[k] = input index of the k-th sorted particle) that
+ *   fmm_build computes and fmm_export_tree returns;
+ *   stream: cudaStream_t (NULL = legacy default stream).
+ * No allocation: temporaries live in one fixed array that the library
+ * reserves on every GPU that loads it (about 12.3 MB, held until the process
+ * exits); n above 1048576 is rejected with FMM_EINVAL. The first call on a
+ * device looks up the array's device address with that device current; make
+ * that first call before any stream capture. All calls share the array: calls
+ * that overlap on the GPU (different streams, or different host threads)
+ * race and must be serialised by the caller. Positions must be finite. Runs
+ * asynchronously on the stream; no handle is needed. Errors: FMM_EINVAL,
+ * FMM_ENODEV, FMM_ECUDA (message in fmm_last_error(NULL)).
+ */
+FMM_API int fmm_morton_sort_noalloc(const void *x, int64_t n, int dtype, uint64_t *keys, int32_t *perm, void *stream);
+
 /* Message of the last error on the calling thread ("" if none). */
 FMM_API const char *fmm_last_error(fmm_handle h);
 

@@ -190,6 +190,8 @@ void tree_export(fmm_ctx *h, uint64_t *keys, int32_t *perm, int32_t *level, uint
                  int32_t *begin, int32_t *end, int32_t *child, int32_t *nchild, int32_t *parent,
                  int64_t *p2p_ptr, int32_t *p2p_idx, int64_t *m2l_ptr, int32_t *m2l_idx, double *box);
 int64_t tree_m2l_total(fmm_ctx *h);
+void morton_sort_into(const void *x, int64_t n, int dt, uint64_t *keys, int *perm, uint64_t *keys_tmp, int *perm_tmp,
+                      unsigned *hist, unsigned *bsum, Box *box, int nsm, cudaStream_t s);
 int m2l_tile_size(fmm_ctx *h);
 void scan_exclusive_u32(fmm_ctx *h, const unsigned *in, unsigned *out, int64_t count, unsigned *total_dev,
                         cudaStream_t s);

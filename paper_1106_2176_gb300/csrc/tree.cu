@@ -358,6 +358,49 @@ static bool radix_sort(fmm_ctx *h, uint64_t *k, int *v, uint64_t *kt, int *vt, i
 // rounded coordinates, and xs32lo the FP32 rounding of the remainder x - hi
 // (zero for FP32 inputs), so that a near-field difference can be formed as
 // (hi_i - hi_j) + (lo_i - lo_j) without the rounding of the positions.
+// Morton keys and their stable sort into caller-provided buffers, with every
+// temporary taken from caller-provided scratch (no allocation): the first
+// stages of the tree build, for the allocation-free entry point.
+//   keys[n], perm[n]         results (sorted keys, input index of each)
+//   keys_tmp[n], perm_tmp[n] ping-pong buffers
+//   hist[256 * ceil(n / 4096)], bsum[ceil(256 * ceil(n / 4096) / 4096) + 1]
+//   box                      root-cube scratch
+void morton_sort_into(const void *x, int64_t n64, int dt, uint64_t *keys, int *perm, uint64_t *keys_tmp, int *perm_tmp,
+                      unsigned *hist, unsigned *bsum, Box *box, int nsm, cudaStream_t s)
+{
+    const int n = (int)n64;
+    const int TB = 256;
+    box_init_k<<<1, 1, 0, s>>>(box);
+    const int bb_blocks = std::max(1, std::min((int)nblocks(n, TB), nsm * 8));
+    if (dt == FMM_F64) {
+        bbox_k<double><<<bb_blocks, TB, 0, s>>>((const double *)x, n, box);
+        box_final_k<<<1, 1, 0, s>>>(box);
+        keys_k<double><<<nblocks(n, TB), TB, 0, s>>>((const double *)x, n, box, keys, perm);
+    } else {
+        bbox_k<float><<<bb_blocks, TB, 0, s>>>((const float *)x, n, box);
+        box_final_k<<<1, 1, 0, s>>>(box);
+        keys_k<float><<<nblocks(n, TB), TB, 0, s>>>((const float *)x, n, box, keys, perm);
+    }
+    check_launch("keys");
+    if (n <= 1) return;
+    FMM_CUDA_TRY(cudaFuncSetAttribute(rs_scatter_k<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs_smem()));
+    const int ntiles = (int)nblocks(n, RS_TILE);
+    const int64_t nh = (int64_t)256 * ntiles;
+    const int nb = (int)nblocks(nh, SCAN_TILE);
+    uint64_t *k = keys, *kt = keys_tmp;
+    int *v = perm, *vt = perm_tmp;
+    for (int shift = 0; shift < 63; shift += 8) {  // 8 passes: the result ends in keys / perm
+        rs_hist_k<<<ntiles, RS_T, 0, s>>>(k, n, shift, hist, ntiles);
+        scan_reduce_k<<<nb, SCAN_T, 0, s>>>(hist, nh, bsum);
+        scan_top_k<<<1, SCAN_T, 0, s>>>(bsum, nb, nullptr);
+        scan_apply_k<<<nb, SCAN_T, 0, s>>>(hist, hist, nh, bsum);
+        rs_scatter_k<true><<<ntiles, RS_T, rs_smem(), s>>>(k, v, kt, vt, n, shift, hist, ntiles);
+        check_launch("radix sort");
+        std::swap(k, kt);
+        std::swap(v, vt);
+    }
+}
+
 template <class T>
 __global__ void gather_k(const T *__restrict__ x, const T *__restrict__ q, const int *__restrict__ idx, int64_t n,
                          double4_32a *__restrict__ xs64, float4 *__restrict__ xs32, float4 *__restrict__ xs32lo)

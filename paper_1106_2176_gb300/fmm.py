@@ -83,6 +83,7 @@ def lib():
     L.fmm_export_tree.argtypes = [_vp] + [_vp] * 14
     L.fmm_export_expansions.argtypes = [_vp, _vp, _vp]
     L.fmm_direct.argtypes = [_vp, _vp, _vp, i64, _vp, i64, _vp, _vp]
+    L.fmm_morton_sort_noalloc.argtypes = [_vp, i64, i32, _vp, _vp, _vp]
     L.fmm_destroy.argtypes = [_vp]
     L.fmm_last_error.argtypes = [_vp]
     L.fmm_last_error.restype = ctypes.c_char_p
