@@ -5,7 +5,7 @@
  * The method is the FMM of Yokota & Barba, "A Tuned and Scalable Fast
  * Multipole Method as a Preeminent Algorithm for Exascale Systems"
  * (arXiv:1106.2176): a Morton-indexed octree (Sec. 2.2, Sec. 5), multipole and
- * local expansions truncated after p terms (Sec. 2.1), the operators P2M,
+ * local expansions of p terms (Sec. 2.1), the operators P2M,
  * M2M, M2L, L2L, L2P and the direct near-field P2P (Sec. 2.1, Fig.
  * flow_chart; Sec. 3.1 names P2P and M2L as the dominant kernels).
  *

@@ -11,7 +11,7 @@
  * What the paper fixes, and where (section of the paper):
  *   - Sec. 2.1: the N-body problem (gravitational / electrostatic, O(N^2)
  *     direct interaction), the hierarchical subdivision of space into near and
- *     far regions, multipole and local expansions "truncated after p terms",
+ *     far regions, multipole and local expansions of p terms,
  *     and the operator set P2M, M2M, M2L, L2L, L2P plus the direct P2P
  *     near field (Figs. tree5 and flow_chart).
  *   - Sec. 2.2 and Sec. 5: Morton-indexed boxes, sorted particle indices with
@@ -77,7 +77,7 @@ static double fact(int k) { return fact_tab[k]; }
 static int nm(int n, int m) { return n * n + n + m; }
 
 /* ------------------------------------------------------------------------ */
-/* solid harmonics (Sec. 2.1 "series expansion"; classical definitions)     */
+/* solid harmonics (the expansion basis of Sec. 2.1; classical definitions)  */
 /* ------------------------------------------------------------------------ */
 
 static void to_sph(const double x[3], double *r, double *ct, double *st, double *ph)

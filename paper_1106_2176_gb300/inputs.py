@@ -2,7 +2,7 @@
 benchmark. This module holds none of the method's arithmetic: it only draws
 particle positions and charges.
 
-The paper's workloads are "points placed at random in a cube" (Sec. 3.1,
+The paper's test problems use randomly placed points in a cube (Sec. 3.1,
 Sec. 4); the Plummer sphere stands in for a clustered astrophysical
 distribution. All draws use numpy's PCG64 ``default_rng(seed)``.
 """

@@ -52,7 +52,7 @@ def test_truncation_error_decays_with_p():
 
 
 def test_p3_three_to_four_digits():
-    # Sec. 3.1: p = 3 "will give 3-4 significant digits of accuracy"
+    # Sec. 3.1: p = 3 gives three to four correct digits
     x, q = inputs.uniform_cube(8192, 2)
     pd, _ = oracle.direct(x, q)
     phi, _ = oracle.fmm(x, q, 3, 0.5, 32)
