@@ -169,12 +169,15 @@ struct TcCfg {
     static constexpr int A_BYTES = M * 128;               // one k-block of A (hi or lo)
     static constexpr int B_BYTES = 2 * NP * 128;          // one k-block of [T_hi ; T_lo]
     static constexpr int STAGE = 2 * A_BYTES + B_BYTES;   // multiple of 1024
-    static constexpr int NS = (200 * 1024) / STAGE >= 4 ? 4 : ((200 * 1024) / STAGE >= 3 ? 3 : 2);
+    // three stages at most: the CTA then leaves room on its SM for two P2P
+    // blocks, which run concurrently on the other stream and use the FMA pipes
+    // this latency-bound kernel leaves idle
+    static constexpr int NS = (150 * 1024) / STAGE >= 3 ? 3 : 2;
     static constexpr int QV = 8;                           // lookahead of the source lookups (vectors)
     static constexpr int RING = 2 * QV * M * 4;            // lookup ring: 2 QV slots x 128 rows
     static constexpr int FIXED = NS * STAGE + 256 + RING;  // stages, barriers, lookup ring
     static constexpr int SMEM_MAX = 227 * 1024 - 1024;     // minus the alignment slack
-    static constexpr int ST_MAX = (SMEM_MAX - FIXED) / 16; // stencil entries that fit in shared memory
+    static constexpr int ST_MAX = 0;                       // stencil read through L1 (keeps shared memory small)
     static constexpr int TCOLS = 4 * NP <= 32 ? 32 : (4 * NP <= 64 ? 64 : (4 * NP <= 128 ? 128 : (4 * NP <= 256 ? 256 : 512)));
     static constexpr int GV = 8;                          // vectors per accumulator drain
     static constexpr bool COMP = NP <= 64;                // compensated registers for the drained sums
