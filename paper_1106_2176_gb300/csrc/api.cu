@@ -92,6 +92,8 @@ fmm_ctx::~fmm_ctx()
     if (ev_fork) cudaEventDestroy(ev_fork);
     if (ev_join) cudaEventDestroy(ev_join);
     if (s2) cudaStreamDestroy(s2);
+    if (sfar) cudaStreamDestroy(sfar);
+    if (ev_far) cudaEventDestroy(ev_far);
 }
 
 using fmm::Error;
@@ -161,7 +163,14 @@ int fmm_create(int64_t N, int p, double theta, int ncrit, fmm_handle *out)
     h->theta = theta;
     h->cmac = theta * theta;
     h->ncrit = ncrit;
-    FMM_CUDA_TRY(cudaStreamCreateWithFlags(&h->s2, cudaStreamNonBlocking));
+    // P2P (the compute-bound near field) runs at the lowest stream priority and
+    // the far-field chain at the highest, so that the short far-field kernels
+    // get SMs as soon as P2P blocks retire instead of waiting behind all of them
+    int prio_lo = 0, prio_hi = 0;
+    FMM_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+    FMM_CUDA_TRY(cudaStreamCreateWithPriority(&h->s2, cudaStreamNonBlocking, prio_lo));
+    FMM_CUDA_TRY(cudaStreamCreateWithPriority(&h->sfar, cudaStreamNonBlocking, prio_hi));
+    FMM_CUDA_TRY(cudaEventCreateWithFlags(&h->ev_far, cudaEventDisableTiming));
     FMM_CUDA_TRY(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
     FMM_CUDA_TRY(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
     for (auto &e : h->tm.ev) FMM_CUDA_TRY(cudaEventCreate(&e));
@@ -268,15 +277,21 @@ int fmm_evaluate(fmm_handle h, void *phi, void *grad)
     cudaStream_t s = h->stream;
     cudaEvent_t *ev = h->tm.ev;
     FMM_CUDA_TRY(cudaEventRecord(ev[8], s));
-    // near field on the private stream, concurrently with the far field
+    // near field and far field on two private streams, joined back to the
+    // caller's stream before the combine
     FMM_CUDA_TRY(cudaEventRecord(h->ev_fork, s));
     FMM_CUDA_TRY(cudaStreamWaitEvent(h->s2, h->ev_fork, 0));
+    FMM_CUDA_TRY(cudaStreamWaitEvent(h->sfar, h->ev_fork, 0));
+    h->work = h->sfar;
+    fmm::far_field(h);
+    FMM_CUDA_TRY(cudaEventRecord(h->ev_far, h->sfar));
     FMM_CUDA_TRY(cudaEventRecord(ev[9], h->s2));
     fmm::near_field(h, h->s2);
     FMM_CUDA_TRY(cudaEventRecord(ev[10], h->s2));
     FMM_CUDA_TRY(cudaEventRecord(h->ev_join, h->s2));
-    fmm::far_field(h);
+    h->work = h->stream;
     FMM_CUDA_TRY(cudaStreamWaitEvent(s, h->ev_join, 0));
+    FMM_CUDA_TRY(cudaStreamWaitEvent(s, h->ev_far, 0));
     FMM_CUDA_TRY(cudaEventRecord(ev[11], s));
     const size_t es = h->dtype == FMM_F64 ? 8 : 4;
     void *pd = phi, *gd = grad;
@@ -304,6 +319,7 @@ int fmm_get_stats(fmm_handle h, fmm_stats *out)
     API_BEGIN
     FMM_CUDA_TRY(cudaStreamSynchronize(h->stream));
     FMM_CUDA_TRY(cudaStreamSynchronize(h->s2));
+    FMM_CUDA_TRY(cudaStreamSynchronize(h->sfar));
     std::memset(out, 0, sizeof(*out));
     out->n = h->n;
     out->ncells = h->ncells;

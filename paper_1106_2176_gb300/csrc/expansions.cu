@@ -719,7 +719,7 @@ void operators_init(fmm_ctx *h)
 template <class T, class P4>
 static void far_field_t(fmm_ctx *h, const P4 *xs, const T *rtab)
 {
-    cudaStream_t s = h->stream;
+    cudaStream_t s = h->work;
     const int p = h->p, PP = p * p, ntri = p * (p + 1) / 2, Q = 2 * p - 1;
     const int nc = h->ncells;
     h->Mexp.ensure(sizeof(T) * (size_t)nc * PP);

@@ -121,7 +121,10 @@ struct fmm_ctx {
     // device
     int dev = 0, nsm = 0, cc_major = 0, cc_minor = 0;
     cudaStream_t stream = nullptr;  // caller's stream (or legacy default)
-    cudaStream_t s2 = nullptr;      // private stream for P2P concurrency
+    cudaStream_t s2 = nullptr;      // private low-priority stream: P2P
+    cudaStream_t sfar = nullptr;    // private high-priority stream: the far-field chain
+    cudaStream_t work = nullptr;    // stream the far-field kernels are launched on
+    cudaEvent_t ev_far = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     fmm::Timers tm;
     int64_t launches = 0;

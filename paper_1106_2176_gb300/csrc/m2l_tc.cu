@@ -612,7 +612,7 @@ template <int NP, int KB>
 static void launch_tc(fmm_ctx *h, float *L, const float *M)
 {
     using C = TcCfg<NP, KB>;
-    cudaStream_t s = h->stream;
+    cudaStream_t s = h->work;
     const int c0 = h->depth >= 2 ? h->lvl_start[2] : h->ncells;
     const int nc = h->ncells;
     h->msplit.ensure(sizeof(float) * (size_t)nc * KB * 64);

@@ -256,10 +256,10 @@ void near_field(fmm_ctx *h, cudaStream_t s)
     if (h->precision == FMM_FP64)
         p2p_k<double, false, 2><<<h->nleaves, P2P_T, 0, s>>>(h->xs64.as<double4_32a>(), nullptr, lv, cb, ce, pp, ru, nr, out);
     else if (h->dtype == FMM_F64)
-        p2p_k<float, true, 4><<<h->nleaves, P2P_T, 0, s>>>(h->xs32.as<float4>(), h->xs32lo.as<float4>(), lv, cb, ce, pp, ru,
+        p2p_k<float, true, 3><<<h->nleaves, P2P_T, 0, s>>>(h->xs32.as<float4>(), h->xs32lo.as<float4>(), lv, cb, ce, pp, ru,
                                                            nr, out);
     else
-        p2p_k<float, false, 4><<<h->nleaves, P2P_T, 0, s>>>(h->xs32.as<float4>(), nullptr, lv, cb, ce, pp, ru, nr, out);
+        p2p_k<float, false, 3><<<h->nleaves, P2P_T, 0, s>>>(h->xs32.as<float4>(), nullptr, lv, cb, ce, pp, ru, nr, out);
     count_launch(h);
     check_launch("p2p");
 }
