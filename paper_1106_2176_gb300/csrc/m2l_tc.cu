@@ -160,77 +160,80 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float b)
     hi = s;
 }
 
+__device__ __forceinline__ void cp_async_arrive_noinc(uint64_t *bar)
+{
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // ---------------------------------------------------------------------------
 // tile geometry
 // ---------------------------------------------------------------------------
+// Warp roles: warps 0-3 (128 threads, one per target row) gather, split,
+// drain; warp 4 issues the MMAs. Operands travel compact (raw FP32: 128 B per
+// row and k-block) and are split into TF32 (hi, lo) in shared memory, so the
+// bytes in flight carry twice the work of pre-split rows.
 template <int NP, int KB>
 struct TcCfg {
     static constexpr int M = 128;                         // target rows per tile
-    static constexpr int A_BYTES = M * 128;               // one k-block of A (hi or lo)
-    static constexpr int B_BYTES = 2 * NP * 128;          // one k-block of [T_hi ; T_lo]
-    static constexpr int STAGE = 2 * A_BYTES + B_BYTES;   // multiple of 1024
-    // three stages at most: the CTA then leaves room on its SM for two P2P
-    // blocks, which run concurrently on the other stream and use the FMA pipes
-    // this latency-bound kernel leaves idle
-    static constexpr int NS = (150 * 1024) / STAGE >= 3 ? 3 : 2;
-    static constexpr int QV = 8;                           // lookahead of the source lookups (vectors)
-    static constexpr int RING = 2 * QV * M * 4;            // lookup ring: 2 QV slots x 128 rows
-    static constexpr int FIXED = NS * STAGE + 256 + RING;  // stages, barriers, lookup ring
-    static constexpr int SMEM_MAX = 227 * 1024 - 1024;     // minus the alignment slack
-    static constexpr int ST_MAX = 0;                       // stencil read through L1 (keeps shared memory small)
+    static constexpr int A_RAW = M * 128;                 // raw A k-block (FP32, swizzled)
+    static constexpr int B_RAW = NP * 128;                // raw T k-block (FP32, swizzled)
+    static constexpr int RAW = A_RAW + B_RAW;             // one raw stage (multiple of 1024)
+    static constexpr int CMP = 2 * A_RAW + 2 * B_RAW;     // A_hi, A_lo, [T_hi ; T_lo]
+    static constexpr int CS = 2;                          // compute stages
+    static constexpr int QV = 8;                          // lookahead of the source lookups (vectors)
+    static constexpr int RING = 2 * QV * M * 4;           // lookup ring
+    static constexpr int BUDGET = 210 * 1024 - CS * CMP - RING - 512;
+    static constexpr int RS = BUDGET >= 4 * RAW ? 4 : (BUDGET >= 3 * RAW ? 3 : 2);  // raw stages
+    static constexpr int SMEM = RS * RAW + CS * CMP + RING + 512 + 1024;
     static constexpr int TCOLS = 4 * NP <= 32 ? 32 : (4 * NP <= 64 ? 64 : (4 * NP <= 128 ? 128 : (4 * NP <= 256 ? 256 : 512)));
     static constexpr int GV = 8;                          // vectors per accumulator drain
     static constexpr bool COMP = NP <= 64;                // compensated registers for the drained sums
+    static constexpr int BW = NP / 4;                     // raw T rows per worker warp
 };
 
-// Split the scaled multipoles into TF32 (hi, lo) rows: out[c][kb][hi 32 | lo 32].
-__global__ void msplit_k(const float *__restrict__ M, int PP, int KB, int c0, int nc, float *__restrict__ out)
+// Zero-padded copy of the scaled multipoles: out[c][KB * 32] (only when p^2 is
+// not a multiple of 32; otherwise the kernel reads M~ directly).
+__global__ void mpad_k(const float *__restrict__ M, int PP, int KP, int c0, int nc, float *__restrict__ out)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int KP = KB * 32;
     if (i >= (int64_t)(nc - c0) * KP) return;
     const int c = c0 + (int)(i / KP), k = (int)(i % KP);
-    const float a = k < PP ? M[(size_t)c * PP + k] : 0.f;
-    const float hi = tf32_rn(a);
-    const float lo = tf32_rn(a - hi);
-    const int kb = k >> 5, kk = k & 31;
-    float *o = out + ((size_t)c * KB + kb) * 64;
-    o[kk] = hi;
-    o[32 + kk] = lo;
+    out[(size_t)c * KP + k] = k < PP ? M[(size_t)c * PP + k] : 0.f;
 }
 
 template <int NP, int KB>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(160, 1)
     m2l_tc_k(int p, const M2LTile *__restrict__ tiles, const int *__restrict__ ntiles, const int *__restrict__ tgt,
              const int4 *__restrict__ xyz, const uint64_t *__restrict__ anchor, const LevelDesc *__restrict__ ld,
              const int *__restrict__ map_pool, const int4 *__restrict__ st, const int *__restrict__ st_off,
-             const float *__restrict__ msplit, const unsigned char *__restrict__ ttab, float *__restrict__ L,
+             const float *__restrict__ mrow, const unsigned char *__restrict__ ttab, float *__restrict__ L,
              int *__restrict__ err)
 {
     using C = TcCfg<NP, KB>;
-    constexpr int NS = C::NS;
+    constexpr int RS = C::RS, CS = C::CS, QV = C::QV, KP = KB * 32;
     if ((int)blockIdx.x >= *ntiles) return;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    // 1024-byte aligned start for the swizzled tiles (kept as a shared-array offset)
     unsigned char *base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(base + NS * C::STAGE);
-    int *ring = reinterpret_cast<int *>(base + NS * C::STAGE + 256);          // [2 QV][128]
-    int4 *s_st = reinterpret_cast<int4 *>(base + NS * C::STAGE + 256 + C::RING); // stencil of the octant
-    uint64_t *full_a = bar;            // NS, 128 arrivals
-    uint64_t *full_b = bar + NS;       // NS, 1 arrival + tx bytes
-    uint64_t *mma_done = bar + 2 * NS; // NS, MMA commits
-    uint64_t *acc_full = bar + 3 * NS; // 2, MMA commits
-    uint64_t *acc_empty = bar + 3 * NS + 2; // 2, 128 arrivals
-    uint64_t *fin = bar + 3 * NS + 4;       // 1, final MMA flush after an abort
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 3 * NS + 5);
+    unsigned char *raw = base;                          // RS x (A_RAW + B_RAW)
+    unsigned char *cmp = base + RS * C::RAW;            // CS x (A_hi, A_lo, T_hi, T_lo)
+    int *ring = reinterpret_cast<int *>(cmp + CS * C::CMP);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(cmp + CS * C::CMP + C::RING);
+    uint64_t *raw_full = bar;                 // RS: 128 cp.async arrivals + 4 operator copies
+    uint64_t *cmp_full = bar + RS;            // CS: 128 arrivals after the split
+    uint64_t *cmp_free = bar + RS + CS;       // CS: MMA commits
+    uint64_t *acc_full = bar + RS + 2 * CS;   // 2: MMA commits at the end of a group
+    uint64_t *acc_empty = acc_full + 2;       // 2: 128 arrivals after a drain
+    uint64_t *fin = acc_full + 4;             // 1
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_full + 5);
     int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
 
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool worker = warp < 4;
     const M2LTile td = tiles[blockIdx.x];
     const int PP = p * p;
     const int l = td.level, sh = FMM_MAXLEVEL - l;
     int px = 0, py = 0, pz = 0, cell = -1;
-    if (tid < td.count) {
+    if (worker && tid < td.count) {
         cell = tgt[td.start + tid];
         const int4 a = xyz[cell];
         px = a.x >> sh;
@@ -238,12 +241,16 @@ __global__ void __launch_bounds__(128, 1)
         pz = a.z >> sh;
     }
     const LevelDesc LD = ld[l];
+    const int e0 = st_off[td.octant], e1 = st_off[td.octant + 1];
+    const int nv = e1 - e0;
+    const int nunits = nv * KB;
+    const int ngroups = (nv + C::GV - 1) / C::GV;
 
     if (tid == 0) {
-        for (int s = 0; s < NS; s++) {
-            mbar_init(&full_a[s], 128);
-            mbar_init(&full_b[s], 1);
-            mbar_init(&mma_done[s], 1);
+        for (int s = 0; s < RS; s++) mbar_init(&raw_full[s], 128 + 4);
+        for (int s = 0; s < CS; s++) {
+            mbar_init(&cmp_full[s], 128);
+            mbar_init(&cmp_free[s], 1);
         }
         for (int b = 0; b < 2; b++) {
             mbar_init(&acc_full[b], 1);
@@ -253,8 +260,8 @@ __global__ void __launch_bounds__(128, 1)
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    __syncwarp();
-    if (warp == 0) {
+    if (warp == 4) {
+        __syncwarp();
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"(C::TCOLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -264,137 +271,24 @@ __global__ void __launch_bounds__(128, 1)
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    const int e0 = st_off[td.octant], e1 = st_off[td.octant + 1];
-    const int nv = e1 - e0;
-    const int nunits = nv * KB;
-    const int ngroups = (nv + C::GV - 1) / C::GV;
-
-    // per-thread accumulators of the drained sums (row = tid)
-    float acc_hi[NP], acc_lo[C::COMP ? NP : 1];
-#pragma unroll
-    for (int k = 0; k < NP; k++) acc_hi[k] = 0.f;
-#pragma unroll
-    for (int k = 0; k < (C::COMP ? NP : 1); k++) acc_lo[k] = 0.f;
-
-    // The stencil of the octant in shared memory when it fits.
-    const bool st_in_smem = nv <= C::ST_MAX;
-    if (st_in_smem)
-        for (int i = tid; i < nv; i += 128) s_st[i] = st[e0 + i];
-    __syncthreads();
-    const int4 *stp = st_in_smem ? s_st : st + e0;
-
-    // Source cell of vector vi for this row, fetched QV vectors ahead of use
-    // into ring slot vi % (2 QV): with a dense lattice map the entry is copied
-    // by cp.async straight into shared memory, so no load result is waited
-    // for on the critical path; other levels search the level's sorted keys.
-    constexpr int QV = C::QV;
-    auto fetch = [&](int vi) {
-        const uint32_t slot = smem_u32(ring + (vi % (2 * QV)) * 128 + tid);
-        int r = -1;
-        if (cell >= 0 && vi < nv) {
-            const int4 v = stp[vi];
-            const int x = px + v.x, y = py + v.y, z = pz + v.z, side = 1 << l;
-            if (x >= 0 && y >= 0 && z >= 0 && x < side && y < side && z < side) {
-                if (LD.map_off >= 0) {
-                    cp_async4(slot, map_pool + LD.map_off + (long long)morton3((uint32_t)x, (uint32_t)y, (uint32_t)z));
-                    return;
+    if (!worker) {
+        // ------------------------------------------------------------ MMA warp
+        if (lane == 0) {
+            const uint32_t id_full = idesc_tf32(128, 2 * NP), id_half = idesc_tf32(128, NP);
+            for (int u = 0; u < nunits; u++) {
+                if (*(volatile int *)abort_flag) break;
+                const int c = u % CS;
+                const int vi = u / KB, kb = u % KB, g = vi / C::GV, b = g & 1;
+                bool ok = mbar_wait(&cmp_full[c], (uint32_t)((u / CS) & 1));
+                if (ok && kb == 0 && vi % C::GV == 0 && g >= 2) ok = mbar_wait(&acc_empty[b], (uint32_t)(((g - 2) >> 1) & 1));
+                if (!ok) {
+                    atomicExch(abort_flag, 1);
+                    break;
                 }
-                r = level_lookup(LD, map_pool, anchor, l, x, y, z);
-            }
-        }
-        ring[(vi % (2 * QV)) * 128 + tid] = r;
-    };
-    for (int i = 0; i < QV; i++) fetch(i);
-    cp_async_commit();
-    cp_async_wait_all();
-    int src = -1;
-    int issued_b = 0;  // thread 0: operator copies issued
-    auto load_unit = [&](int u) {
-        const int s = u % NS;
-        const int vi = u / KB, kb = u % KB;
-        if (kb == 0) {
-            src = ring[(vi % (2 * QV)) * 128 + tid];
-            fetch(vi + QV);
-        }
-        unsigned char *sa = base + s * C::STAGE;
-        const uint32_t ahi = smem_u32(sa), alo = smem_u32(sa + C::A_BYTES);
-        // the warp copies its 32 rows: 16 lanes per 256-byte (hi | lo) row, so
-        // every instruction reads two whole rows; the source cell of a row
-        // comes from the lane that owns it
-        const int lane = tid & 31, ch = lane & 15;
-#pragma unroll
-        for (int i = 0; i < 16; i++) {
-            const int r = 2 * i + (lane >> 4);
-            const int sr = __shfl_sync(0xffffffffu, src, r);
-            const int row = (warp << 5) + r;
-            const float *g = msplit + ((size_t)(sr >= 0 ? sr : 0) * KB + kb) * 64 + ch * 4;
-            const uint32_t dst = (ch < 8 ? ahi : alo) + (uint32_t)row * 128u + ((((uint32_t)ch & 7u) ^ ((uint32_t)row & 7u)) << 4);
-            cp_async16(dst, g, sr >= 0 ? 16u : 0u);
-        }
-        cp_async_commit();
-        if (tid == 0) {
-            const int4 v = stp[vi];
-            mbar_arrive_tx(&full_b[s], C::B_BYTES);
-            bulk_g2s(smem_u32(sa + 2 * C::A_BYTES), ttab + ((size_t)v.w * KB + kb) * C::B_BYTES, C::B_BYTES, &full_b[s]);
-            issued_b = u + 1;
-        }
-    };
-
-    auto drain = [&](int g) {
-        const int b = g & 1;
-        __syncwarp();
-        const bool ok = __all_sync(0xffffffffu, mbar_wait(&acc_full[b], (uint32_t)((g >> 1) & 1)));
-        if (!ok) {
-            atomicExch(abort_flag, 1);
-            return;
-        }
-        tc_fence_after();
-        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * 2 * NP);
-        float mv[16], cv[16];
-#pragma unroll
-        for (int k0 = 0; k0 < NP; k0 += 16) {
-            tmem_ld16(taddr + k0, mv);
-            tmem_ld16(taddr + NP + k0, cv);
-#pragma unroll
-            for (int k = 0; k < 16; k++) {
-                const float t = mv[k] + cv[k];
-                if (C::COMP) two_sum_acc(acc_hi[k0 + k], acc_lo[C::COMP ? k0 + k : 0], t);
-                else acc_hi[k0 + k] += t;
-            }
-        }
-        tc_fence_before();
-        mbar_arrive(&acc_empty[b]);
-    };
-
-    // prologue: the first NS-1 units in flight
-    for (int u = 0; u < NS - 1 && u < nunits; u++) load_unit(u);
-
-    const uint32_t id_full = idesc_tf32(128, 2 * NP), id_half = idesc_tf32(128, NP);
-    int drained = 0;
-    int consumed = 0;  // thread 0: units whose operator copy has been waited for
-    for (int u = 0; u < nunits; u++) {
-        if (*(volatile int *)abort_flag) break;
-        const int s = u % NS;
-        // this thread's rows of unit u have landed
-        if (u + NS - 1 <= nunits) cp_async_wait<NS - 2>();
-        else cp_async_wait_all();
-        fence_proxy_async();
-        mbar_arrive(&full_a[s]);
-        if (tid == 0) {
-            const uint32_t par = (uint32_t)((u / NS) & 1);
-            bool ok = mbar_wait(&full_a[s], par) && mbar_wait(&full_b[s], par);
-            if (ok) consumed = u + 1;
-            const int vi = u / KB, kb = u % KB, g = vi / C::GV;
-            const int b = g & 1;
-            // first unit of a group: the buffer must have been drained
-            if (ok && kb == 0 && vi % C::GV == 0 && g >= 2) ok = mbar_wait(&acc_empty[b], (uint32_t)(((g - 2) >> 1) & 1));
-            if (!ok) {
-                atomicExch(abort_flag, 1);
-            } else {
                 fence_proxy_async();
                 tc_fence_after();
-                unsigned char *sa = base + s * C::STAGE;
-                const uint32_t ahi = smem_u32(sa), alo = smem_u32(sa + C::A_BYTES), bb = smem_u32(sa + 2 * C::A_BYTES);
+                unsigned char *cs = cmp + c * C::CMP;
+                const uint32_t ahi = smem_u32(cs), alo = smem_u32(cs + C::A_RAW), bb = smem_u32(cs + 2 * C::A_RAW);
                 const uint32_t dmain = tmem + (uint32_t)(b * 2 * NP), dcorr = dmain + NP;
                 const bool first = (vi % C::GV == 0) && kb == 0;
 #pragma unroll
@@ -403,54 +297,182 @@ __global__ void __launch_bounds__(128, 1)
                     mma_tf32(dmain, sdesc(ahi + 32 * k), sdesc(bb + 32 * k), id_full, (first && k == 0) ? 0u : 1u);
                     mma_tf32(dcorr, sdesc(alo + 32 * k), sdesc(bb + 32 * k), id_half, 1u);
                 }
-                mma_commit(&mma_done[s]);
-                const bool last_of_group = (kb == KB - 1) && ((vi % C::GV == C::GV - 1) || vi == nv - 1);
-                if (last_of_group) mma_commit(&acc_full[b]);
+                mma_commit(&cmp_free[c]);
+                if ((kb == KB - 1) && ((vi % C::GV == C::GV - 1) || vi == nv - 1)) mma_commit(&acc_full[b]);
             }
+            // every commit has arrived before the shared memory goes away
+            mma_commit(fin);
+            mbar_wait(fin, 0);
+            for (int u = max(0, nunits - CS); u < nunits; u++) mbar_wait(&cmp_free[u % CS], (uint32_t)((u / CS) & 1));
         }
-        // refill: unit u + NS - 1 reuses the stage of unit u - 1
-        const int un = u + NS - 1;
-        if (un < nunits) {
-            if (u >= 1 && !mbar_wait(&mma_done[(u - 1) % NS], (uint32_t)(((u - 1) / NS) & 1))) {
+    } else {
+        // ---------------------------------------------------------- worker warps
+        float acc_hi[NP], acc_lo[C::COMP ? NP : 1];
+#pragma unroll
+        for (int k = 0; k < NP; k++) acc_hi[k] = 0.f;
+#pragma unroll
+        for (int k = 0; k < (C::COMP ? NP : 1); k++) acc_lo[k] = 0.f;
+
+        // source cell of vector vi for this row, fetched QV vectors ahead into
+        // ring slot vi % (2 QV) (cp.async of the lattice-map entry when the
+        // level has a dense map, a search of the level's keys otherwise)
+        auto fetch = [&](int vi) {
+            const uint32_t slot = smem_u32(ring + (vi % (2 * QV)) * 128 + tid);
+            int r = -1;
+            if (cell >= 0 && vi < nv) {
+                const int4 v = st[e0 + vi];
+                const int x = px + v.x, y = py + v.y, z = pz + v.z, side = 1 << l;
+                if (x >= 0 && y >= 0 && z >= 0 && x < side && y < side && z < side) {
+                    if (LD.map_off >= 0) {
+                        cp_async4(slot, map_pool + LD.map_off + (long long)morton3((uint32_t)x, (uint32_t)y, (uint32_t)z));
+                        return;
+                    }
+                    r = level_lookup(LD, map_pool, anchor, l, x, y, z);
+                }
+            }
+            ring[(vi % (2 * QV)) * 128 + tid] = r;
+        };
+        for (int i = 0; i < QV; i++) fetch(i);
+        cp_async_commit();
+        cp_async_wait_all();
+
+        int src = -1;
+        int issued = 0;  // lane 0: operator pieces copied (units)
+        // copy unit u (raw rows of this warp + this warp's slice of the raw
+        // operator) into raw stage u % RS; arrivals complete raw_full
+        auto load_unit = [&](int u) {
+            const int r = u % RS, vi = u / KB, kb = u % KB;
+            if (kb == 0) {
+                src = ring[(vi % (2 * QV)) * 128 + tid];
+                fetch(vi + QV);
+            }
+            unsigned char *rs = raw + r * C::RAW;
+            const uint32_t araw = smem_u32(rs);
+            const int ch = lane & 7;
+#pragma unroll
+            for (int i = 0; i < 8; i++) {
+                const int rr = 4 * i + (lane >> 3);  // row within the warp's 32
+                const int sr = __shfl_sync(0xffffffffu, src, rr);
+                const int row = (warp << 5) + rr;
+                const float *g = mrow + ((size_t)(sr >= 0 ? sr : 0) * KP + kb * 32) + ch * 4;
+                cp_async16(araw + (uint32_t)row * 128u + ((((uint32_t)ch) ^ ((uint32_t)row & 7u)) << 4), g,
+                           sr >= 0 ? 16u : 0u);
+            }
+            if (lane == 0) {
+                const int4 v = st[e0 + vi];
+                mbar_arrive_tx(&raw_full[r], C::BW * 128);
+                bulk_g2s(smem_u32(rs + C::A_RAW + warp * C::BW * 128),
+                         ttab + ((size_t)v.w * KB + kb) * C::B_RAW + (size_t)warp * C::BW * 128, C::BW * 128, &raw_full[r]);
+                issued = u + 1;
+            }
+            cp_async_arrive_noinc(&raw_full[r]);
+        };
+
+        auto drain = [&](int g) {
+            const int b = g & 1;
+            __syncwarp();
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(&acc_full[b], (uint32_t)((g >> 1) & 1)));
+            if (!ok) {
+                atomicExch(abort_flag, 1);
+                return;
+            }
+            tc_fence_after();
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * 2 * NP);
+            float mv[16], cv[16];
+#pragma unroll
+            for (int k0 = 0; k0 < NP; k0 += 16) {
+                tmem_ld16(taddr + k0, mv);
+                tmem_ld16(taddr + NP + k0, cv);
+#pragma unroll
+                for (int k = 0; k < 16; k++) {
+                    const float t = mv[k] + cv[k];
+                    if (C::COMP) two_sum_acc(acc_hi[k0 + k], acc_lo[C::COMP ? k0 + k : 0], t);
+                    else acc_hi[k0 + k] += t;
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&acc_empty[b]);
+        };
+
+        for (int u = 0; u < RS && u < nunits; u++) load_unit(u);
+        int drained = 0, consumed = 0;
+        for (int u = 0; u < nunits; u++) {
+            if (*(volatile int *)abort_flag) break;
+            const int r = u % RS, c = u % CS;
+            bool ok = mbar_wait(&raw_full[r], (uint32_t)((u / RS) & 1));
+            if (ok && u >= CS) ok = mbar_wait(&cmp_free[c], (uint32_t)(((u - CS) / CS) & 1));
+            if (!ok) {
                 atomicExch(abort_flag, 1);
                 break;
             }
-            load_unit(un);
-        }
-        // drain group g - 1 once group g is well under way
-        const int vi = u / KB;
-        if ((u % KB) == KB - 1 && vi % C::GV == 2 && vi / C::GV >= 1 && drained < vi / C::GV) {
-            drain(drained);
-            drained++;
-        }
-    }
-    cp_async_wait_all();
-    if (tid == 0 && *(volatile int *)abort_flag) {
-        // wait (bounded) for the operator copies still in flight and the MMAs
-        for (int u = consumed; u < issued_b; u++) mbar_wait(&full_b[u % NS], (uint32_t)((u / NS) & 1));
-        mma_commit(fin);
-        mbar_wait(fin, 0);
-    }
-    __syncthreads();
-    if (!*(volatile int *)abort_flag) {
-        while (drained < ngroups) {
-            drain(drained);
-            drained++;
-            if (*(volatile int *)abort_flag) break;
-        }
-    }
-    // every MMA commit must have arrived before the shared memory goes away
-    if (tid == 0 && !*(volatile int *)abort_flag)
-        for (int u = max(0, nunits - NS); u < nunits; u++) mbar_wait(&mma_done[u % NS], (uint32_t)((u / NS) & 1));
-    if (cell >= 0 && !*(volatile int *)abort_flag) {
-        float *Lc = L + (size_t)cell * PP;
+            consumed = u + 1;
+            // split raw FP32 into TF32 (hi, lo): this thread's A row, and a
+            // slice of this warp's operator rows into T_hi and T_lo
+            unsigned char *rs = raw + r * C::RAW;
+            unsigned char *cs = cmp + c * C::CMP;
+            {
+                const uint32_t off = (uint32_t)tid * 128u;
 #pragma unroll
-        for (int k = 0; k < NP; k++)
-            if (k < PP) Lc[k] += C::COMP ? acc_hi[k] + acc_lo[C::COMP ? k : 0] : acc_hi[k];
+                for (int ch = 0; ch < 8; ch++) {
+                    const uint32_t o = off + ((((uint32_t)ch) ^ ((uint32_t)tid & 7u)) << 4);
+                    const float4 a = *reinterpret_cast<const float4 *>(rs + o);
+                    float4 hi, lo;
+                    hi.x = tf32_rn(a.x); lo.x = tf32_rn(a.x - hi.x);
+                    hi.y = tf32_rn(a.y); lo.y = tf32_rn(a.y - hi.y);
+                    hi.z = tf32_rn(a.z); lo.z = tf32_rn(a.z - hi.z);
+                    hi.w = tf32_rn(a.w); lo.w = tf32_rn(a.w - hi.w);
+                    *reinterpret_cast<float4 *>(cs + o) = hi;
+                    *reinterpret_cast<float4 *>(cs + C::A_RAW + o) = lo;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < C::BW * 8 / 32; j++) {
+                const int id = lane + 32 * j;
+                const int row = warp * C::BW + (id >> 3), ch = id & 7;
+                const uint32_t o = (uint32_t)row * 128u + ((((uint32_t)ch) ^ ((uint32_t)row & 7u)) << 4);
+                const float4 a = *reinterpret_cast<const float4 *>(rs + C::A_RAW + o);
+                float4 hi, lo;
+                hi.x = tf32_rn(a.x); lo.x = tf32_rn(a.x - hi.x);
+                hi.y = tf32_rn(a.y); lo.y = tf32_rn(a.y - hi.y);
+                hi.z = tf32_rn(a.z); lo.z = tf32_rn(a.z - hi.z);
+                hi.w = tf32_rn(a.w); lo.w = tf32_rn(a.w - hi.w);
+                *reinterpret_cast<float4 *>(cs + 2 * C::A_RAW + o) = hi;
+                *reinterpret_cast<float4 *>(cs + 2 * C::A_RAW + NP * 128 + o) = lo;
+            }
+            fence_proxy_async();
+            mbar_arrive(&cmp_full[c]);
+            // this warp's part of raw stage r is consumed: refill with u + RS
+            __syncwarp();
+            if (u + RS < nunits) load_unit(u + RS);
+            // drain group g - 1 once group g is well under way
+            const int vi = u / KB;
+            if ((u % KB) == KB - 1 && vi % C::GV == 2 && vi / C::GV >= 1 && drained < vi / C::GV) {
+                drain(drained);
+                drained++;
+            }
+        }
+        cp_async_wait_all();
+        if (*(volatile int *)abort_flag) {
+            // the operator pieces still in flight (bounded waits)
+            if (lane == 0)
+                for (int u = consumed; u < issued; u++) mbar_wait(&raw_full[u % RS], (uint32_t)((u / RS) & 1));
+        } else {
+            while (drained < ngroups) {
+                drain(drained);
+                drained++;
+                if (*(volatile int *)abort_flag) break;
+            }
+        }
+        if (cell >= 0 && !*(volatile int *)abort_flag) {
+            float *Lc = L + (size_t)cell * PP;
+#pragma unroll
+            for (int k = 0; k < NP; k++)
+                if (k < PP) Lc[k] += C::COMP ? acc_hi[k] + acc_lo[C::COMP ? k : 0] : acc_hi[k];
+        }
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 4) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TCOLS));
     }
     if (tid == 0 && *(volatile int *)abort_flag) atomicExch(err, 1);
@@ -541,7 +563,7 @@ void tensor_tables_update(fmm_ctx *h)
     if (!sh.NP) return;
     if (h->ttab_nv == h->nV && h->ttab.p) return;
     const int p = h->p, PP = p * p, Q = 2 * p - 1, NP = sh.NP, KB = sh.KB;
-    const size_t bbytes = (size_t)2 * NP * 128;
+    const size_t bbytes = (size_t)NP * 128;  // one k-block of the raw operator
     const size_t per_v = (size_t)KB * bbytes;
     std::vector<unsigned char> img((size_t)h->nV * per_v, 0);
     std::vector<int> seen(h->nV, 0);
@@ -587,19 +609,14 @@ void tensor_tables_update(fmm_ctx *h)
                             if (m) T[(size_t)im_i(n, m) * PP + col] = si;
                         }
                 }
+        // raw FP32 image, rows = output coefficients, 128B-swizzled per k-block
         unsigned char *dst = img.data() + (size_t)id * per_v;
         for (int r = 0; r < PP; r++)
             for (int c = 0; c < PP; c++) {
-                const double t = T[(size_t)r * PP + c];
-                const float hi = tf32_rn_host((float)t);
-                const float lo = tf32_rn_host((float)(t - (double)hi));
+                const float v = (float)T[(size_t)r * PP + c];
                 const int kb = c >> 5, cc = c & 31;
-                for (int part = 0; part < 2; part++) {
-                    const int row = r + part * NP;
-                    const size_t off = (size_t)kb * bbytes + (size_t)row * 128 + (size_t)((((cc >> 2) ^ (row & 7)) << 4) + (cc & 3) * 4);
-                    const float v = part ? lo : hi;
-                    memcpy(dst + off, &v, 4);
-                }
+                const size_t off = (size_t)kb * bbytes + (size_t)r * 128 + (size_t)((((cc >> 2) ^ (r & 7)) << 4) + (cc & 3) * 4);
+                memcpy(dst + off, &v, 4);
             }
     }
     h->ttab.ensure(img.size());
@@ -614,28 +631,28 @@ static void launch_tc(fmm_ctx *h, float *L, const float *M)
     using C = TcCfg<NP, KB>;
     cudaStream_t s = h->work;
     const int c0 = h->depth >= 2 ? h->lvl_start[2] : h->ncells;
-    const int nc = h->ncells;
-    h->msplit.ensure(sizeof(float) * (size_t)nc * KB * 64);
-    msplit_k<<<nblk((int64_t)(nc - c0) * KB * 32, 256), 256, 0, s>>>(M, h->p * h->p, KB, c0, nc, h->msplit.as<float>());
-    count_launch(h);
-    // stencil in shared memory when the largest octant stencil fits
-    int nvmax = 0;
-    for (int o = 0; o < 8; o++) nvmax = std::max(nvmax, h->st_off[o + 1] - h->st_off[o]);
-    const int smem = 1024 + C::FIXED + (nvmax <= C::ST_MAX ? 16 * nvmax : 0);
-    static int attr = 0;
-    if (smem > attr) {
-        FMM_CUDA_TRY(cudaFuncSetAttribute(m2l_tc_k<NP, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        attr = smem;
+    const int nc = h->ncells, PP = h->p * h->p, KP = KB * 32;
+    const float *mrow = M;
+    if (PP != KP) {  // zero-padded rows of KB * 32 coefficients
+        h->msplit.ensure(sizeof(float) * (size_t)nc * KP);
+        mpad_k<<<nblk((int64_t)(nc - c0) * KP, 256), 256, 0, s>>>(M, PP, KP, c0, nc, h->msplit.as<float>());
+        count_launch(h);
+        mrow = h->msplit.as<float>();
+    }
+    static bool attr = false;
+    if (!attr) {
+        FMM_CUDA_TRY(cudaFuncSetAttribute(m2l_tc_k<NP, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+        attr = true;
     }
     const int *st_off = reinterpret_cast<const int *>(h->st_dev.as<char>() + sizeof(int4) * h->st_off[8]);
     const int *ntiles = reinterpret_cast<const int *>(h->m2l_misc.as<unsigned>() + 24 * (FMM_MAXLEVEL + 1));
     int *err = reinterpret_cast<int *>(h->m2l_misc.as<unsigned>() + 24 * (FMM_MAXLEVEL + 1) + 4);
     FMM_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
-    m2l_tc_k<NP, KB><<<h->ntiles_max, 128, smem, s>>>(h->p, h->m2l_tiles.as<M2LTile>(), ntiles, h->m2l_tgt.as<int>(),
-                                                         h->c_xyz.as<int4>(), h->c_anchor.as<uint64_t>(),
-                                                         h->lvl_desc.as<LevelDesc>(), h->map_pool.as<int>(),
-                                                         h->st_dev.as<int4>(), st_off, h->msplit.as<float>(),
-                                                         h->ttab.as<unsigned char>(), L, err);
+    m2l_tc_k<NP, KB><<<h->ntiles_max, 160, C::SMEM, s>>>(h->p, h->m2l_tiles.as<M2LTile>(), ntiles, h->m2l_tgt.as<int>(),
+                                                          h->c_xyz.as<int4>(), h->c_anchor.as<uint64_t>(),
+                                                          h->lvl_desc.as<LevelDesc>(), h->map_pool.as<int>(),
+                                                          h->st_dev.as<int4>(), st_off, mrow, h->ttab.as<unsigned char>(),
+                                                          L, err);
     count_launch(h);
     check_launch("m2l tensor");
 }
