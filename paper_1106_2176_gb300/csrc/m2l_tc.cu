@@ -145,6 +145,18 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
     for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
 }
 
+// 8 consecutive TMEM columns of this warp's 32 lanes
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v)
+{
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; i++) v[i] = __uint_as_float(r[i]);
+}
+
 __device__ __forceinline__ float tf32_rn(float a)
 {
     uint32_t r;
@@ -160,6 +172,11 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float b)
     hi = s;
 }
 
+__device__ __forceinline__ void named_barrier_sync(int id, int nthreads)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
 __device__ __forceinline__ void cp_async_arrive_noinc(uint64_t *bar)
 {
     asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
@@ -168,13 +185,16 @@ __device__ __forceinline__ void cp_async_arrive_noinc(uint64_t *bar)
 // ---------------------------------------------------------------------------
 // tile geometry
 // ---------------------------------------------------------------------------
-// Warp roles: warps 0-3 (128 threads, one per target row) gather, split,
-// drain; warp 4 issues the MMAs. Operands travel compact (raw FP32: 128 B per
-// row and k-block) and are split into TF32 (hi, lo) in shared memory, so the
-// bytes in flight carry twice the work of pre-split rows.
+// Warp roles: warps 0-7 (256 threads: target row r = tid % 128 and half
+// h = tid / 128 of the coefficients) gather, split and drain; warp 8 issues
+// the MMAs. Operands travel compact (raw FP32: 128 B per row and k-block) and
+// are split into TF32 (hi, lo) in shared memory, so the bytes in flight carry
+// twice the work of pre-split rows.
 template <int NP, int KB>
 struct TcCfg {
     static constexpr int M = 128;                         // target rows per tile
+    static constexpr int NW = 8;                          // worker warps
+    static constexpr int NT = NW * 32 + 32;               // threads (workers + MMA warp)
     static constexpr int A_RAW = M * 128;                 // raw A k-block (FP32, swizzled)
     static constexpr int B_RAW = NP * 128;                // raw T k-block (FP32, swizzled)
     static constexpr int RAW = A_RAW + B_RAW;             // one raw stage (multiple of 1024)
@@ -187,8 +207,9 @@ struct TcCfg {
     static constexpr int SMEM = RS * RAW + CS * CMP + RING + 512 + 1024;
     static constexpr int TCOLS = 4 * NP <= 32 ? 32 : (4 * NP <= 64 ? 64 : (4 * NP <= 128 ? 128 : (4 * NP <= 256 ? 256 : 512)));
     static constexpr int GV = 8;                          // vectors per accumulator drain
-    static constexpr bool COMP = NP <= 64;                // compensated registers for the drained sums
-    static constexpr int BW = NP / 4;                     // raw T rows per worker warp
+    static constexpr int HN = NP / 2;                     // coefficients per thread
+    static constexpr bool COMP = true;                    // compensated registers for the drained sums
+    static constexpr int BW = NP / NW;                    // raw T rows per worker warp
 };
 
 // Zero-padded copy of the scaled multipoles: out[c][KB * 32] (only when p^2 is
@@ -202,7 +223,7 @@ __global__ void mpad_k(const float *__restrict__ M, int PP, int KP, int c0, int 
 }
 
 template <int NP, int KB>
-__global__ void __launch_bounds__(160, 1)
+__global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
     m2l_tc_k(int p, const M2LTile *__restrict__ tiles, const int *__restrict__ ntiles, const int *__restrict__ tgt,
              const int4 *__restrict__ xyz, const uint64_t *__restrict__ anchor, const LevelDesc *__restrict__ ld,
              const int *__restrict__ map_pool, const int4 *__restrict__ st, const int *__restrict__ st_off,
@@ -218,23 +239,24 @@ __global__ void __launch_bounds__(160, 1)
     unsigned char *cmp = base + RS * C::RAW;            // CS x (A_hi, A_lo, T_hi, T_lo)
     int *ring = reinterpret_cast<int *>(cmp + CS * C::CMP);
     uint64_t *bar = reinterpret_cast<uint64_t *>(cmp + CS * C::CMP + C::RING);
-    uint64_t *raw_full = bar;                 // RS: 128 cp.async arrivals + 4 operator copies
-    uint64_t *cmp_full = bar + RS;            // CS: 128 arrivals after the split
+    uint64_t *raw_full = bar;                 // RS: 256 cp.async arrivals + 8 operator copies
+    uint64_t *cmp_full = bar + RS;            // CS: 256 arrivals after the split
     uint64_t *cmp_free = bar + RS + CS;       // CS: MMA commits
     uint64_t *acc_full = bar + RS + 2 * CS;   // 2: MMA commits at the end of a group
-    uint64_t *acc_empty = acc_full + 2;       // 2: 128 arrivals after a drain
+    uint64_t *acc_empty = acc_full + 2;       // 2: 256 arrivals after a drain
     uint64_t *fin = acc_full + 4;             // 1
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_full + 5);
     int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const bool worker = warp < 4;
+    const bool worker = warp < C::NW;
+    const int row = tid & 127, half = (tid >> 7) & 1;  // worker: target row and coefficient half
     const M2LTile td = tiles[blockIdx.x];
     const int PP = p * p;
     const int l = td.level, sh = FMM_MAXLEVEL - l;
     int px = 0, py = 0, pz = 0, cell = -1;
-    if (worker && tid < td.count) {
-        cell = tgt[td.start + tid];
+    if (worker && row < td.count) {
+        cell = tgt[td.start + row];
         const int4 a = xyz[cell];
         px = a.x >> sh;
         py = a.y >> sh;
@@ -247,20 +269,20 @@ __global__ void __launch_bounds__(160, 1)
     const int ngroups = (nv + C::GV - 1) / C::GV;
 
     if (tid == 0) {
-        for (int s = 0; s < RS; s++) mbar_init(&raw_full[s], 128 + 4);
+        for (int s = 0; s < RS; s++) mbar_init(&raw_full[s], 32 * C::NW + C::NW);
         for (int s = 0; s < CS; s++) {
-            mbar_init(&cmp_full[s], 128);
+            mbar_init(&cmp_full[s], 32 * C::NW);
             mbar_init(&cmp_free[s], 1);
         }
         for (int b = 0; b < 2; b++) {
             mbar_init(&acc_full[b], 1);
-            mbar_init(&acc_empty[b], 128);
+            mbar_init(&acc_empty[b], 32 * C::NW);
         }
         mbar_init(fin, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 4) {
+    if (warp == C::NW) {
         __syncwarp();
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"(C::TCOLS));
@@ -307,17 +329,19 @@ __global__ void __launch_bounds__(160, 1)
         }
     } else {
         // ---------------------------------------------------------- worker warps
-        float acc_hi[NP], acc_lo[C::COMP ? NP : 1];
+        constexpr int HN = C::HN;
+        float acc_hi[HN], acc_lo[HN];
 #pragma unroll
-        for (int k = 0; k < NP; k++) acc_hi[k] = 0.f;
-#pragma unroll
-        for (int k = 0; k < (C::COMP ? NP : 1); k++) acc_lo[k] = 0.f;
+        for (int k = 0; k < HN; k++) acc_hi[k] = acc_lo[k] = 0.f;
 
-        // source cell of vector vi for this row, fetched QV vectors ahead into
-        // ring slot vi % (2 QV) (cp.async of the lattice-map entry when the
-        // level has a dense map, a search of the level's keys otherwise)
+        // source cell of vector vi for row `row`, fetched QV vectors ahead into
+        // ring slot vi % (2 QV) by the row's half-0 thread (cp.async of the
+        // lattice-map entry when the level has a dense map, a search of the
+        // level's keys otherwise); it is visible to the half-1 thread through
+        // the raw-stage barrier of the unit whose loads issued it
         auto fetch = [&](int vi) {
-            const uint32_t slot = smem_u32(ring + (vi % (2 * QV)) * 128 + tid);
+            if (half) return;
+            const uint32_t slot = smem_u32(ring + (vi % (2 * QV)) * 128 + row);
             int r = -1;
             if (cell >= 0 && vi < nv) {
                 const int4 v = st[e0 + vi];
@@ -330,32 +354,33 @@ __global__ void __launch_bounds__(160, 1)
                     r = level_lookup(LD, map_pool, anchor, l, x, y, z);
                 }
             }
-            ring[(vi % (2 * QV)) * 128 + tid] = r;
+            ring[(vi % (2 * QV)) * 128 + row] = r;
         };
         for (int i = 0; i < QV; i++) fetch(i);
         cp_async_commit();
         cp_async_wait_all();
+        named_barrier_sync(1, 32 * C::NW);  // the first ring entries, for every worker
 
         int src = -1;
         int issued = 0;  // lane 0: operator pieces copied (units)
-        // copy unit u (raw rows of this warp + this warp's slice of the raw
-        // operator) into raw stage u % RS; arrivals complete raw_full
+        // copy unit u into raw stage u % RS: this warp's 32 rows, its half of
+        // each row (64 B), and its slice of the raw operator rows
         auto load_unit = [&](int u) {
             const int r = u % RS, vi = u / KB, kb = u % KB;
             if (kb == 0) {
-                src = ring[(vi % (2 * QV)) * 128 + tid];
+                src = ring[(vi % (2 * QV)) * 128 + row];
                 fetch(vi + QV);
             }
             unsigned char *rs = raw + r * C::RAW;
             const uint32_t araw = smem_u32(rs);
-            const int ch = lane & 7;
+            const int ch = 4 * half + (lane & 3);
 #pragma unroll
-            for (int i = 0; i < 8; i++) {
-                const int rr = 4 * i + (lane >> 3);  // row within the warp's 32
+            for (int i = 0; i < 4; i++) {
+                const int rr = 8 * i + (lane >> 2);  // row within the warp's 32
                 const int sr = __shfl_sync(0xffffffffu, src, rr);
-                const int row = (warp << 5) + rr;
+                const int ro = ((warp & 3) << 5) + rr;
                 const float *g = mrow + ((size_t)(sr >= 0 ? sr : 0) * KP + kb * 32) + ch * 4;
-                cp_async16(araw + (uint32_t)row * 128u + ((((uint32_t)ch) ^ ((uint32_t)row & 7u)) << 4), g,
+                cp_async16(araw + (uint32_t)ro * 128u + ((((uint32_t)ch) ^ ((uint32_t)ro & 7u)) << 4), g,
                            sr >= 0 ? 16u : 0u);
             }
             if (lane == 0) {
@@ -377,18 +402,20 @@ __global__ void __launch_bounds__(160, 1)
                 return;
             }
             tc_fence_after();
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * 2 * NP);
+            const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(b * 2 * NP + half * HN);
             float mv[16], cv[16];
 #pragma unroll
-            for (int k0 = 0; k0 < NP; k0 += 16) {
-                tmem_ld16(taddr + k0, mv);
-                tmem_ld16(taddr + NP + k0, cv);
-#pragma unroll
-                for (int k = 0; k < 16; k++) {
-                    const float t = mv[k] + cv[k];
-                    if (C::COMP) two_sum_acc(acc_hi[k0 + k], acc_lo[C::COMP ? k0 + k : 0], t);
-                    else acc_hi[k0 + k] += t;
+            for (int k0 = 0; k0 < HN; k0 += 16) {
+                if (k0 + 16 <= HN) {
+                    tmem_ld16(taddr + k0, mv);
+                    tmem_ld16(taddr + NP + k0, cv);
+                } else {  // HN = 8 (p <= 4): 8 columns
+                    tmem_ld8(taddr + k0, mv);
+                    tmem_ld8(taddr + NP + k0, cv);
                 }
+#pragma unroll
+                for (int k = 0; k < 16; k++)
+                    if (k0 + k < HN) two_sum_acc(acc_hi[k0 + k], acc_lo[k0 + k], mv[k] + cv[k]);
             }
             tc_fence_before();
             mbar_arrive(&acc_empty[b]);
@@ -406,30 +433,26 @@ __global__ void __launch_bounds__(160, 1)
                 break;
             }
             consumed = u + 1;
-            // split raw FP32 into TF32 (hi, lo): this thread's A row, and a
-            // slice of this warp's operator rows into T_hi and T_lo
+            // split raw FP32 into TF32 (hi, lo): this thread's half of its A
+            // row, and a slice of this warp's operator rows into T_hi, T_lo
             unsigned char *rs = raw + r * C::RAW;
             unsigned char *cs = cmp + c * C::CMP;
-            {
-                const uint32_t off = (uint32_t)tid * 128u;
 #pragma unroll
-                for (int ch = 0; ch < 8; ch++) {
-                    const uint32_t o = off + ((((uint32_t)ch) ^ ((uint32_t)tid & 7u)) << 4);
-                    const float4 a = *reinterpret_cast<const float4 *>(rs + o);
-                    float4 hi, lo;
-                    hi.x = tf32_rn(a.x); lo.x = tf32_rn(a.x - hi.x);
-                    hi.y = tf32_rn(a.y); lo.y = tf32_rn(a.y - hi.y);
-                    hi.z = tf32_rn(a.z); lo.z = tf32_rn(a.z - hi.z);
-                    hi.w = tf32_rn(a.w); lo.w = tf32_rn(a.w - hi.w);
-                    *reinterpret_cast<float4 *>(cs + o) = hi;
-                    *reinterpret_cast<float4 *>(cs + C::A_RAW + o) = lo;
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < C::BW * 8 / 32; j++) {
-                const int id = lane + 32 * j;
-                const int row = warp * C::BW + (id >> 3), ch = id & 7;
+            for (int j = 0; j < 4; j++) {
+                const int ch = 4 * half + j;
                 const uint32_t o = (uint32_t)row * 128u + ((((uint32_t)ch) ^ ((uint32_t)row & 7u)) << 4);
+                const float4 a = *reinterpret_cast<const float4 *>(rs + o);
+                float4 hi, lo;
+                hi.x = tf32_rn(a.x); lo.x = tf32_rn(a.x - hi.x);
+                hi.y = tf32_rn(a.y); lo.y = tf32_rn(a.y - hi.y);
+                hi.z = tf32_rn(a.z); lo.z = tf32_rn(a.z - hi.z);
+                hi.w = tf32_rn(a.w); lo.w = tf32_rn(a.w - hi.w);
+                *reinterpret_cast<float4 *>(cs + o) = hi;
+                *reinterpret_cast<float4 *>(cs + C::A_RAW + o) = lo;
+            }
+            for (int id = lane; id < C::BW * 8; id += 32) {
+                const int br = warp * C::BW + (id >> 3), ch = id & 7;
+                const uint32_t o = (uint32_t)br * 128u + ((((uint32_t)ch) ^ ((uint32_t)br & 7u)) << 4);
                 const float4 a = *reinterpret_cast<const float4 *>(rs + C::A_RAW + o);
                 float4 hi, lo;
                 hi.x = tf32_rn(a.x); lo.x = tf32_rn(a.x - hi.x);
@@ -464,15 +487,15 @@ __global__ void __launch_bounds__(160, 1)
             }
         }
         if (cell >= 0 && !*(volatile int *)abort_flag) {
-            float *Lc = L + (size_t)cell * PP;
+            float *Lc = L + (size_t)cell * PP + half * HN;
 #pragma unroll
-            for (int k = 0; k < NP; k++)
-                if (k < PP) Lc[k] += C::COMP ? acc_hi[k] + acc_lo[C::COMP ? k : 0] : acc_hi[k];
+            for (int k = 0; k < HN; k++)
+                if (half * HN + k < PP) Lc[k] += acc_hi[k] + acc_lo[k];
         }
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 4) {
+    if (warp == C::NW) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TCOLS));
     }
     if (tid == 0 && *(volatile int *)abort_flag) atomicExch(err, 1);
@@ -648,7 +671,7 @@ static void launch_tc(fmm_ctx *h, float *L, const float *M)
     const int *ntiles = reinterpret_cast<const int *>(h->m2l_misc.as<unsigned>() + 24 * (FMM_MAXLEVEL + 1));
     int *err = reinterpret_cast<int *>(h->m2l_misc.as<unsigned>() + 24 * (FMM_MAXLEVEL + 1) + 4);
     FMM_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
-    m2l_tc_k<NP, KB><<<h->ntiles_max, 160, C::SMEM, s>>>(h->p, h->m2l_tiles.as<M2LTile>(), ntiles, h->m2l_tgt.as<int>(),
+    m2l_tc_k<NP, KB><<<h->ntiles_max, C::NT, C::SMEM, s>>>(h->p, h->m2l_tiles.as<M2LTile>(), ntiles, h->m2l_tgt.as<int>(),
                                                           h->c_xyz.as<int4>(), h->c_anchor.as<uint64_t>(),
                                                           h->lvl_desc.as<LevelDesc>(), h->map_pool.as<int>(),
                                                           h->st_dev.as<int4>(), st_off, mrow, h->ttab.as<unsigned char>(),
