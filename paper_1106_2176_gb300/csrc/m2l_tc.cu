@@ -187,18 +187,18 @@ __device__ __forceinline__ void cp_async_arrive_noinc(uint64_t *bar)
 // ---------------------------------------------------------------------------
 // Warp roles: warps 0-7 (256 threads: target row r = tid % 128 and half
 // h = tid / 128 of the coefficients) gather, split and drain; warp 8 issues
-// the MMAs. Operands travel compact (raw FP32: 128 B per row and k-block) and
-// are split into TF32 (hi, lo) in shared memory, so the bytes in flight carry
-// twice the work of pre-split rows.
+// the MMAs. The gathered multipoles travel compact (raw FP32: 128 B per row and
+// k-block) and are split into TF32 (hi, lo) in shared memory; the operator
+// image arrives pre-split and is read by the MMAs where it lands.
 template <int NP, int KB>
 struct TcCfg {
     static constexpr int M = 128;                         // target rows per tile
     static constexpr int NW = 8;                          // worker warps
     static constexpr int NT = NW * 32 + 32;               // threads (workers + MMA warp)
     static constexpr int A_RAW = M * 128;                 // raw A k-block (FP32, swizzled)
-    static constexpr int B_RAW = NP * 128;                // raw T k-block (FP32, swizzled)
+    static constexpr int B_RAW = 2 * NP * 128;            // [T_hi ; T_lo] k-block (TF32 pair, swizzled)
     static constexpr int RAW = A_RAW + B_RAW;             // one raw stage (multiple of 1024)
-    static constexpr int CMP = 2 * A_RAW + 2 * B_RAW;     // A_hi, A_lo, [T_hi ; T_lo]
+    static constexpr int CMP = 2 * A_RAW;                 // A_hi, A_lo
     static constexpr int CS = 2;                          // compute stages
     static constexpr int QV = 8;                          // lookahead of the source lookups (vectors)
     static constexpr int RING = 2 * QV * M * 4;           // lookup ring
@@ -209,7 +209,7 @@ struct TcCfg {
     static constexpr int GV = 8;                          // vectors per accumulator drain
     static constexpr int HN = NP / 2;                     // coefficients per thread
     static constexpr bool COMP = true;                    // compensated registers for the drained sums
-    static constexpr int BW = NP / NW;                    // raw T rows per worker warp
+    static constexpr int BW = 2 * NP / NW;                // operator rows copied per worker warp
 };
 
 // Zero-padded copy of the scaled multipoles: out[c][KB * 32] (only when p^2 is
@@ -310,7 +310,8 @@ __global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
                 fence_proxy_async();
                 tc_fence_after();
                 unsigned char *cs = cmp + c * C::CMP;
-                const uint32_t ahi = smem_u32(cs), alo = smem_u32(cs + C::A_RAW), bb = smem_u32(cs + 2 * C::A_RAW);
+                const uint32_t ahi = smem_u32(cs), alo = smem_u32(cs + C::A_RAW);
+                const uint32_t bb = smem_u32(raw + (u % RS) * C::RAW + C::A_RAW);
                 const uint32_t dmain = tmem + (uint32_t)(b * 2 * NP), dcorr = dmain + NP;
                 const bool first = (vi % C::GV == 0) && kb == 0;
 #pragma unroll
@@ -433,8 +434,9 @@ __global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
                 break;
             }
             consumed = u + 1;
-            // split raw FP32 into TF32 (hi, lo): this thread's half of its A
-            // row, and a slice of this warp's operator rows into T_hi, T_lo
+            // split raw FP32 into TF32 (hi, lo), this thread's half of its row:
+            // hi rounded to nearest, lo = a - hi (exact in FP32; the MMA reads
+            // its leading 11 bits, an error below 2^-21 of a)
             unsigned char *rs = raw + r * C::RAW;
             unsigned char *cs = cmp + c * C::CMP;
 #pragma unroll
@@ -443,30 +445,25 @@ __global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
                 const uint32_t o = (uint32_t)row * 128u + ((((uint32_t)ch) ^ ((uint32_t)row & 7u)) << 4);
                 const float4 a = *reinterpret_cast<const float4 *>(rs + o);
                 float4 hi, lo;
-                hi.x = tf32_rn(a.x); lo.x = tf32_rn(a.x - hi.x);
-                hi.y = tf32_rn(a.y); lo.y = tf32_rn(a.y - hi.y);
-                hi.z = tf32_rn(a.z); lo.z = tf32_rn(a.z - hi.z);
-                hi.w = tf32_rn(a.w); lo.w = tf32_rn(a.w - hi.w);
+                hi.x = tf32_rn(a.x); lo.x = a.x - hi.x;
+                hi.y = tf32_rn(a.y); lo.y = a.y - hi.y;
+                hi.z = tf32_rn(a.z); lo.z = a.z - hi.z;
+                hi.w = tf32_rn(a.w); lo.w = a.w - hi.w;
                 *reinterpret_cast<float4 *>(cs + o) = hi;
                 *reinterpret_cast<float4 *>(cs + C::A_RAW + o) = lo;
             }
-            for (int id = lane; id < C::BW * 8; id += 32) {
-                const int br = warp * C::BW + (id >> 3), ch = id & 7;
-                const uint32_t o = (uint32_t)br * 128u + ((((uint32_t)ch) ^ ((uint32_t)br & 7u)) << 4);
-                const float4 a = *reinterpret_cast<const float4 *>(rs + C::A_RAW + o);
-                float4 hi, lo;
-                hi.x = tf32_rn(a.x); lo.x = tf32_rn(a.x - hi.x);
-                hi.y = tf32_rn(a.y); lo.y = tf32_rn(a.y - hi.y);
-                hi.z = tf32_rn(a.z); lo.z = tf32_rn(a.z - hi.z);
-                hi.w = tf32_rn(a.w); lo.w = tf32_rn(a.w - hi.w);
-                *reinterpret_cast<float4 *>(cs + 2 * C::A_RAW + o) = hi;
-                *reinterpret_cast<float4 *>(cs + 2 * C::A_RAW + NP * 128 + o) = lo;
-            }
             fence_proxy_async();
             mbar_arrive(&cmp_full[c]);
-            // this warp's part of raw stage r is consumed: refill with u + RS
-            __syncwarp();
-            if (u + RS < nunits) load_unit(u + RS);
+            // raw stage of unit u - 1 (its operator was read by MMA u - 1):
+            // refill with unit u - 1 + RS
+            if (u >= 1 && u - 1 + RS < nunits) {
+                if (!mbar_wait(&cmp_free[(u - 1) % CS], (uint32_t)(((u - 1) / CS) & 1))) {
+                    atomicExch(abort_flag, 1);
+                    break;
+                }
+                __syncwarp();
+                load_unit(u - 1 + RS);
+            }
             // drain group g - 1 once group g is well under way
             const int vi = u / KB;
             if ((u % KB) == KB - 1 && vi % C::GV == 2 && vi / C::GV >= 1 && drained < vi / C::GV) {
@@ -586,7 +583,7 @@ void tensor_tables_update(fmm_ctx *h)
     if (!sh.NP) return;
     if (h->ttab_nv == h->nV && h->ttab.p) return;
     const int p = h->p, PP = p * p, Q = 2 * p - 1, NP = sh.NP, KB = sh.KB;
-    const size_t bbytes = (size_t)NP * 128;  // one k-block of the raw operator
+    const size_t bbytes = (size_t)2 * NP * 128;  // one k-block of [T_hi ; T_lo]
     const size_t per_v = (size_t)KB * bbytes;
     std::vector<unsigned char> img((size_t)h->nV * per_v, 0);
     std::vector<int> seen(h->nV, 0);
@@ -632,14 +629,21 @@ void tensor_tables_update(fmm_ctx *h)
                             if (m) T[(size_t)im_i(n, m) * PP + col] = si;
                         }
                 }
-        // raw FP32 image, rows = output coefficients, 128B-swizzled per k-block
+        // per k-block the 128B-swizzled image of [T_hi ; T_lo]: rows 0..NP-1
+        // hold hi = TF32(T) (round to nearest), rows NP..2NP-1 lo = T - hi
         unsigned char *dst = img.data() + (size_t)id * per_v;
         for (int r = 0; r < PP; r++)
             for (int c = 0; c < PP; c++) {
-                const float v = (float)T[(size_t)r * PP + c];
+                const double t = T[(size_t)r * PP + c];
+                const float hi = tf32_rn_host((float)t);
+                const float lo = (float)(t - (double)hi);
                 const int kb = c >> 5, cc = c & 31;
-                const size_t off = (size_t)kb * bbytes + (size_t)r * 128 + (size_t)((((cc >> 2) ^ (r & 7)) << 4) + (cc & 3) * 4);
-                memcpy(dst + off, &v, 4);
+                for (int part = 0; part < 2; part++) {
+                    const int row = r + part * NP;
+                    const size_t off = (size_t)kb * bbytes + (size_t)row * 128 + (size_t)((((cc >> 2) ^ (row & 7)) << 4) + (cc & 3) * 4);
+                    const float v = part ? lo : hi;
+                    memcpy(dst + off, &v, 4);
+                }
             }
     }
     h->ttab.ensure(img.size());
