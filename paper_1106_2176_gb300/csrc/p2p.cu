@@ -81,30 +81,44 @@ __device__ __forceinline__ void acc2(double &hi, double &lo, double b) { hi += b
 
 constexpr int P2P_T = 128;
 
-// Sources [j0, j1) of the shared chunk against the TPT targets of a thread, in
-// blocks of 64 whose sums are added with TwoSum.
+// One source against the TPT targets of a thread.
+template <bool CHECK, bool DS, int TPT, class T, class T4>
+__device__ __forceinline__ void p2p_one(const T4 &s, const float4 &q, const T4 (&x)[TPT], const float4 (&xl)[TPT],
+                                        T (&b)[4 * TPT])
+{
+    if constexpr (DS) {
+#pragma unroll
+        for (int k = 0; k < TPT; k++) interact_ds<CHECK>(x[k], xl[k], s, q, b[4 * k], b[4 * k + 1], b[4 * k + 2], b[4 * k + 3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < TPT; k++) interact<CHECK>(x[k], s, b[4 * k], b[4 * k + 1], b[4 * k + 2], b[4 * k + 3]);
+    }
+}
+
+// Sources [j0, j1) of the shared chunk against the TPT targets of a thread:
+// full blocks of 64 sources (fixed trip count, unrolled by 8) and a remainder;
+// each block's sums are added to (h, lo) with TwoSum.
 template <bool CHECK, bool DS, int TPT, class T, class T4>
 __device__ __forceinline__ void p2p_range(int j0, int j1, const T4 *sh, const float4 *shlo, const T4 (&x)[TPT],
                                           const float4 (&xl)[TPT], T (&h)[4 * TPT], T (&lo)[4 * TPT])
 {
-    for (int jb = j0; jb < j1; jb += 64) {
-        const int je = min(j1, jb + 64);
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    int j = j0;
+    for (; j + 64 <= j1; j += 64) {
+        T b[4 * TPT];
+#pragma unroll
+        for (int c = 0; c < 4 * TPT; c++) b[c] = T(0);
+#pragma unroll 8
+        for (int jj = 0; jj < 64; jj++) p2p_one<CHECK, DS, TPT>(sh[j + jj], DS ? shlo[j + jj] : zero, x, xl, b);
+#pragma unroll
+        for (int c = 0; c < 4 * TPT; c++) acc2(h[c], lo[c], b[c]);
+    }
+    if (j < j1) {
         T b[4 * TPT];
 #pragma unroll
         for (int c = 0; c < 4 * TPT; c++) b[c] = T(0);
 #pragma unroll 4
-        for (int j = jb; j < je; j++) {
-            const T4 s = sh[j];
-            if constexpr (DS) {
-                const float4 q = shlo[j];
-#pragma unroll
-                for (int k = 0; k < TPT; k++)
-                    interact_ds<CHECK>(x[k], xl[k], s, q, b[4 * k], b[4 * k + 1], b[4 * k + 2], b[4 * k + 3]);
-            } else {
-#pragma unroll
-                for (int k = 0; k < TPT; k++) interact<CHECK>(x[k], s, b[4 * k], b[4 * k + 1], b[4 * k + 2], b[4 * k + 3]);
-            }
-        }
+        for (; j < j1; j++) p2p_one<CHECK, DS, TPT>(sh[j], DS ? shlo[j] : zero, x, xl, b);
 #pragma unroll
         for (int c = 0; c < 4 * TPT; c++) acc2(h[c], lo[c], b[c]);
     }
