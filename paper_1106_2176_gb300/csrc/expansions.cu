@@ -216,6 +216,106 @@ __global__ void __launch_bounds__(64) p2m_k(int p, const int *__restrict__ leave
     }
 }
 
+// P2M with the order fixed at compile time: one warp per leaf, each lane runs
+// the regular-harmonic recurrences of its particles in registers and adds
+// q conj(R_n^m) into its own accumulators; a butterfly over the warp sums them
+// and lane k writes coefficients k, k+32, ...  (Sec. 2.1, P2M.)
+template <int P, class T>
+__device__ __forceinline__ void p2m_accum(T x, T y, T z, T q, T *are, T *aim)
+{
+    const T r2 = x * x + y * y + z * z;
+    T mre = T(1), mim = T(0);
+#pragma unroll
+    for (int m = 0; m < P; m++) {
+        if (m > 0) {
+            const T f = T(1) / T(2 * m);
+            const T a = (mre * x - mim * y) * f;
+            const T b = (mre * y + mim * x) * f;
+            mre = a;
+            mim = b;
+        }
+        are[tri(m, m)] += q * mre;
+        aim[tri(m, m)] -= q * mim;
+        if (m + 1 < P) {
+            T p2re = mre, p2im = mim, p1re = z * mre, p1im = z * mim;
+            are[tri(m + 1, m)] += q * p1re;
+            aim[tri(m + 1, m)] -= q * p1im;
+#pragma unroll
+            for (int n = m + 2; n < P; n++) {
+                const T a = T(2 * n - 1), b = T(1) / T((n + m) * (n - m));
+                const T cre = (a * z * p1re - r2 * p2re) * b;
+                const T cim = (a * z * p1im - r2 * p2im) * b;
+                are[tri(n, m)] += q * cre;
+                aim[tri(n, m)] -= q * cim;
+                p2re = p1re; p2im = p1im; p1re = cre; p1im = cim;
+            }
+        }
+    }
+}
+
+constexpr int P2M_WARPS = 8;
+constexpr int P2M_WARP_MAXP = 10;
+
+template <int P, class P4>
+__global__ void __launch_bounds__(32 * P2M_WARPS) p2m_warp_k(int nleaves, const int *__restrict__ leaves,
+                                                             const int *__restrict__ begin, const int *__restrict__ end,
+                                                             const int4 *__restrict__ xyz, const Box *__restrict__ box,
+                                                             const P4 *__restrict__ xs, float *__restrict__ M)
+{
+    constexpr int NT = P * (P + 1) / 2;
+    const int lane = threadIdx.x & 31;
+    const int li = blockIdx.x * P2M_WARPS + (threadIdx.x >> 5);
+    if (li >= nleaves) return;
+    const int c = leaves[li];
+    double cen[3], w;
+    cell_geom(box, xyz[c], cen, w);
+    const double iw = 1.0 / w;
+    const int b = begin[c], e = end[c];
+    float are[NT], aim[NT];
+#pragma unroll
+    for (int k = 0; k < NT; k++) are[k] = aim[k] = 0.f;
+    for (int j = b + lane; j < e; j += 32) {
+        const double4_32a pt = rel_pt(xs, j, cen);
+        p2m_accum<P, float>((float)(pt.x * iw), (float)(pt.y * iw), (float)(pt.z * iw), (float)pt.w, are, aim);
+    }
+#pragma unroll
+    for (int k = 0; k < NT; k++) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            are[k] += __shfl_xor_sync(0xffffffffu, are[k], o);
+            aim[k] += __shfl_xor_sync(0xffffffffu, aim[k], o);
+        }
+    }
+    float *Mc = M + (size_t)c * (P * P);
+#pragma unroll
+    for (int n = 0; n < P; n++)
+#pragma unroll
+        for (int m = 0; m <= n; m++) {
+            const int k = tri(n, m);
+            if (lane == (k & 31)) {
+                Mc[re_idx(n, m)] = are[k];
+                if (m) Mc[im_idx(n, m)] = aim[k];
+            }
+        }
+}
+
+template <class P4>
+static bool p2m_warp_launch(int p, int nleaves, const int *leaves, const int *begin, const int *end, const int4 *xyz,
+                            const Box *box, const P4 *xs, float *M, cudaStream_t s)
+{
+    const unsigned g = nblk(nleaves, P2M_WARPS);
+    const unsigned bs = 32 * P2M_WARPS;
+    switch (p) {
+#define FMM_P2M_CASE(PV) \
+    case PV: p2m_warp_k<PV, P4><<<g, bs, 0, s>>>(nleaves, leaves, begin, end, xyz, box, xs, M); return true;
+        FMM_P2M_CASE(2) FMM_P2M_CASE(3) FMM_P2M_CASE(4) FMM_P2M_CASE(5) FMM_P2M_CASE(6)
+        FMM_P2M_CASE(7) FMM_P2M_CASE(8) FMM_P2M_CASE(9) FMM_P2M_CASE(10)
+#undef FMM_P2M_CASE
+    default: return false;
+    }
+}
+static_assert(P2M_WARP_MAXP == 10, "p2m_warp_launch instantiates p = 2 .. 10");
+
 // ---------------------------------------------------------------------------
 // M2M: one thread per (parent cell, output coefficient)
 // ---------------------------------------------------------------------------
@@ -730,7 +830,17 @@ static void far_field_t(fmm_ctx *h, const P4 *xs, const T *rtab)
 
     // P2M
     FMM_CUDA_TRY(cudaEventRecord(ev[2], s));
-    {
+    bool p2m_done = false;
+    if constexpr (std::is_same<T, float>::value) {
+        if (h->nleaves > 0)
+            p2m_done = p2m_warp_launch<P4>(p, h->nleaves, h->leaves.as<int>(), h->c_begin.as<int>(), h->c_end.as<int>(),
+                                           h->c_xyz.as<int4>(), box, xs, M, s);
+        if (p2m_done) {
+            count_launch(h);
+            check_launch("p2m");
+        }
+    }
+    if (!p2m_done) {
         int chunk = std::min(64, (int)((48 * 1024) / (sizeof(T) * 2 * ntri)));
         chunk = std::max(chunk, 1);
         size_t smem = sizeof(T) * 2 * (size_t)ntri * chunk;

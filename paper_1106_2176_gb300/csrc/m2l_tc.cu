@@ -16,15 +16,19 @@
 // the accumulator is drained into per-thread FP32 (hi, lo) TwoSum registers;
 // two TMEM buffers alternate so the drain overlaps the next MMAs.
 //
-// Per CTA (128 threads, one per target row), for every unit (v, k-block):
-//   - the thread finds its source cell (lattice lookup) and copies its 256 B
-//     (hi, lo) row with cp.async into the 128B-swizzled A tiles (zero fill if
-//     the cell is absent);
-//   - thread 0 bulk-copies the pre-swizzled [T_hi ; T_lo] k-block image and,
-//     once all rows of the stage are in, issues the tcgen05.mma and commits to
-//     the stage's mbarrier.
-// Stages rotate through NS buffers. Every wait is bounded; on a timeout the
-// kernel records an error code and leaves after releasing its TMEM.
+// Per CTA (288 threads: 8 worker warps and 1 MMA warp), for every unit
+// (v, k-block) of 32 coefficients:
+//   - worker warp w copies, with cp.async, half of each of 32 target rows'
+//     raw FP32 multipole block (source found by a lattice lookup fetched QV
+//     vectors ahead into a shared ring; zero fill if the cell is absent) into
+//     a 128B-swizzled raw stage, and its lane 0 bulk-copies one eighth of the
+//     pre-split, pre-swizzled [T_hi ; T_lo] operator block into the same stage;
+//   - once a raw stage is full the workers split A into TF32 hi and lo
+//     (lo = a - hi) into a compute stage;
+//   - one thread of the MMA warp issues the tcgen05.mma of the compute stage
+//     and commits to its "free" mbarrier.
+// RS raw stages and CS compute stages rotate. Every wait is bounded; on a
+// timeout the kernel records an error code and leaves after releasing its TMEM.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -203,7 +207,7 @@ struct TcCfg {
     static constexpr int QV = 8;                          // lookahead of the source lookups (vectors)
     static constexpr int RING = 2 * QV * M * 4;           // lookup ring
     static constexpr int BUDGET = 210 * 1024 - CS * CMP - RING - 512;
-    static constexpr int RS = BUDGET >= 4 * RAW ? 4 : (BUDGET >= 3 * RAW ? 3 : 2);  // raw stages
+    static constexpr int RS = BUDGET >= 3 * RAW ? 3 : 2;  // raw stages (3 leaves room for a P2P block on the SM)
     static constexpr int SMEM = RS * RAW + CS * CMP + RING + 512 + 1024;
     static constexpr int TCOLS = 4 * NP <= 32 ? 32 : (4 * NP <= 64 ? 64 : (4 * NP <= 128 ? 128 : (4 * NP <= 256 ? 256 : 512)));
     static constexpr int GV = 8;                          // vectors per accumulator drain

@@ -530,6 +530,10 @@ __device__ __forceinline__ unsigned long long warp_reserve(unsigned long long *c
     return base + (x - cnt);
 }
 
+// One thread per (frontier pair, slot): the pair (A, B) expands into at most
+// 8 x 8 child pairs; slot k takes child a = child[A] + k of A (or A itself)
+// against the children of B (or B itself), at most 8 pairs, classified in
+// registers and written after one warp-aggregated reservation per list.
 __global__ void __launch_bounds__(256) expand_k(const int2 *__restrict__ F, unsigned nF, const int4 *__restrict__ xyz,
                                                 const int *__restrict__ child, const int *__restrict__ nchild, double cm,
                                                 int2 *__restrict__ p2p, unsigned long long cap_p2p,
@@ -537,58 +541,47 @@ __global__ void __launch_bounds__(256) expand_k(const int2 *__restrict__ F, unsi
                                                 int2 *__restrict__ next, unsigned long long cap_next,
                                                 TravCounters *ctr)
 {
-    const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
-    int a0 = 0, na = 0, b0 = 0, nb = 0;
+    const unsigned long long t = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned i = (unsigned)(t >> 3), slot = (unsigned)(t & 7);
+    int a = -1, b0 = 0, nb = 0;
     if (i < nF) {
         const int2 pr = F[i];
         const int A = pr.x, B = pr.y;
         const int ncA = nchild[A], ncB = nchild[B];
         const int lA = xyz[A].w, lB = xyz[B].w;
         const bool la = ncA == 0, lb = ncB == 0;
-        if (!la && (lb || lA < lB)) {
-            a0 = child[A]; na = ncA; b0 = B; nb = 1;
-        } else if (!lb && (la || lB < lA)) {
-            a0 = A; na = 1; b0 = child[B]; nb = ncB;
-        } else {
-            a0 = child[A]; na = ncA; b0 = child[B]; nb = ncB;
+        if (!la && (lb || lA < lB)) {  // split A only
+            if ((int)slot < ncA) { a = child[A] + slot; b0 = B; nb = 1; }
+        } else if (!lb && (la || lB < lA)) {  // split B only
+            if (slot == 0) { a = A; b0 = child[B]; nb = ncB; }
+        } else {  // both, same level
+            if ((int)slot < ncA) { a = child[A] + slot; b0 = child[B]; nb = ncB; }
         }
     }
-    unsigned cP = 0, cX = 0, cN = 0, cI = 0;
-    for (int a = a0; a < a0 + na; a++) {
+    unsigned mP = 0, mX = 0, mN = 0, cI = 0;
+    if (a >= 0) {
         const int4 xa = xyz[a];
         const bool leafa = nchild[a] == 0;
-        for (int b = b0; b < b0 + nb; b++) {
+        for (int k = 0; k < nb; k++) {
+            const int b = b0 + k;
             const int4 xb = xyz[b];
             if (mac_accept(xa, xb, cm)) {
                 if (xa.w == xb.w) cI++;
-                else cX++;
-            } else if (leafa && nchild[b] == 0) cP++;
-            else cN++;
+                else mX |= 1u << k;
+            } else if (leafa && nchild[b] == 0) mP |= 1u << k;
+            else mN |= 1u << k;
         }
     }
-    unsigned long long oP = warp_reserve(&ctr->n_p2p, cP);
-    unsigned long long oX = warp_reserve(&ctr->n_m2lx, cX);
-    unsigned long long oN = warp_reserve(&ctr->n_next, cN);
+    unsigned long long oP = warp_reserve(&ctr->n_p2p, __popc(mP));
+    unsigned long long oX = warp_reserve(&ctr->n_m2lx, __popc(mX));
+    unsigned long long oN = warp_reserve(&ctr->n_next, __popc(mN));
     warp_reserve(&ctr->n_m2l_implicit, cI);
-    for (int a = a0; a < a0 + na; a++) {
-        const int4 xa = xyz[a];
-        const bool leafa = nchild[a] == 0;
-        for (int b = b0; b < b0 + nb; b++) {
-            const int4 xb = xyz[b];
-            if (mac_accept(xa, xb, cm)) {
-                if (xa.w != xb.w) {
-                    if (oX < cap_m2lx) m2lx[oX] = make_int2(a, b);
-                    oX++;
-                }
-            } else if (leafa && nchild[b] == 0) {
-                if (oP < cap_p2p) p2p[oP] = make_int2(a, b);
-                oP++;
-            } else {
-                if (oN < cap_next) next[oN] = make_int2(a, b);
-                oN++;
-            }
-        }
-    }
+    for (; mP; mP &= mP - 1, oP++)
+        if (oP < cap_p2p) p2p[oP] = make_int2(a, b0 + __ffs(mP) - 1);
+    for (; mX; mX &= mX - 1, oX++)
+        if (oX < cap_m2lx) m2lx[oX] = make_int2(a, b0 + __ffs(mX) - 1);
+    for (; mN; mN &= mN - 1, oN++)
+        if (oN < cap_next) next[oN] = make_int2(a, b0 + __ffs(mN) - 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -940,7 +933,7 @@ void tree_build(fmm_ctx *h, const void *x, const void *q, int64_t n, int dt)
                 *hp = start;
                 FMM_CUDA_TRY(cudaMemcpyAsync(dc, hp, sizeof(TravCounters), cudaMemcpyHostToDevice, s));
                 size_t cn = h->frontB.cap / sizeof(int2);
-                expand_k<<<nblocks(nF, 256), 256, 0, s>>>(h->frontA.as<int2>(), (unsigned)nF, h->c_xyz.as<int4>(),
+                expand_k<<<nblocks(nF * 8, 256), 256, 0, s>>>(h->frontA.as<int2>(), (unsigned)nF, h->c_xyz.as<int4>(),
                                                           h->c_child.as<int>(), h->c_nchild.as<int>(), h->cmac,
                                                           h->p2p_pairs.as<int2>(), cap_p2p, h->m2lx_pairs.as<int2>(),
                                                           cap_m2lx, h->frontB.as<int2>(), cn, dc);
