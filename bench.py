@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=100_000)
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg (profiling runs)")
+    ap.add_argument("--overlap", type=int, default=0, choices=[0, 1],
+                    help="0 (default): far and near field in turn on one stream, so the P2P events time the kernel "
+                         "alone; 1: on concurrent streams")
     return ap.parse_args()
 
 
@@ -172,7 +175,7 @@ def run_e2e(a, x, q, N, ncrit, world, dist, dev):
     qh = torch.from_numpy(q).pin_memory()
     ph = torch.empty(N, dtype=torch.float32).pin_memory()
     gh = torch.empty((N, 3), dtype=torch.float32).pin_memory()
-    fh = FMM(N, p=a.p, theta=a.theta, ncrit=ncrit, precision=a.precision)
+    fh = FMM(N, p=a.p, theta=a.theta, ncrit=ncrit, precision=a.precision, overlap=bool(a.overlap))
     for _ in range(2):
         fh.build(xh.numpy(), qh.numpy())
         fh.evaluate(ph.numpy(), gh.numpy())
@@ -229,7 +232,7 @@ def main():
     tune_ms = None
     if ncrit == 0:
         ncrit, tune_ms = tune.tune_ncrit(xt, qt, a.p, a.theta, precision=a.precision)
-    f = FMM(N, p=a.p, theta=a.theta, ncrit=ncrit, precision=a.precision)
+    f = FMM(N, p=a.p, theta=a.theta, ncrit=ncrit, precision=a.precision, overlap=bool(a.overlap))
     phi = torch.empty(N, dtype=torch.float32, device=dev)
     grad = torch.empty((N, 3), dtype=torch.float32, device=dev)
     for _ in range(max(a.warmup, 3)):
@@ -310,8 +313,6 @@ def main():
         e2e = run_e2e(a, x, q, N, ncrit, world, dist, dev)
 
     # roofline of the dominant kernel (P2P, FP32 FMA pipe)
-    qh = torch.from_numpy(q).pin_memory()
-    # roofline of the dominant kernel (P2P, FP32 FMA pipe)
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     peaks = {}
     try:
@@ -347,6 +348,7 @@ def main():
                                       "%s precision" % (N, a.p, a.theta, a.precision),
                           "N": N, "p": a.p, "theta": a.theta, "ncrit": ncrit, "ncrit_tuning_ms": tune_ms,
                           "precision": a.precision, "parallelism": "replicas" if world > 1 else "single",
+                          "schedule": "far and near field concurrent" if a.overlap else "far field, then near field",
                           "l2": "inputs (x, q: %d MB) and the step's working set exceed the 129 MB L2"
                                 % ((x.nbytes + q.nbytes) // 2 ** 20)},
                "rel_l2_phi": err_phi, "rel_l2_grad": err_grad, "error_targets": len(tg),

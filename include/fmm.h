@@ -115,6 +115,15 @@ FMM_API int fmm_set_precision(fmm_handle h, int mode);
 /* Select the M2L engine for FMM_MIXED (FMM_M2L_AUTO uses the tensor cores). */
 FMM_API int fmm_set_m2l_engine(fmm_handle h, int engine);
 
+/* Scheduling of fmm_evaluate. on = 1 (default): the far field (P2M .. L2P)
+ * and the near field (P2P) run concurrently on two library streams, joined
+ * back to the caller's stream before the combine. on = 0: both run in turn on
+ * the caller's stream, so the phase times in fmm_stats are those of each
+ * phase alone. Results are bitwise the same either way. The paper runs the two
+ * in turn on one device; this is an addition. Returns FMM_EINVAL for a NULL
+ * handle or on not 0/1. */
+FMM_API int fmm_set_overlap(fmm_handle h, int on);
+
 /* Use the given cudaStream_t (NULL = legacy default stream) for all work. */
 FMM_API int fmm_set_stream(fmm_handle h, void *stream);
 

@@ -224,6 +224,14 @@ int fmm_set_m2l_engine(fmm_handle h, int engine)
     return FMM_OK;
 }
 
+int fmm_set_overlap(fmm_handle h, int on)
+{
+    if (!h) return fail(FMM_EINVAL, "fmm_set_overlap: NULL handle");
+    if (on != 0 && on != 1) return fail(FMM_EINVAL, "fmm_set_overlap: on must be 0 or 1");
+    h->overlap = on;
+    return FMM_OK;
+}
+
 int fmm_set_stream(fmm_handle h, void *stream)
 {
     if (!h) return fail(FMM_EINVAL, "fmm_set_stream: NULL handle");
@@ -277,21 +285,30 @@ int fmm_evaluate(fmm_handle h, void *phi, void *grad)
     cudaStream_t s = h->stream;
     cudaEvent_t *ev = h->tm.ev;
     FMM_CUDA_TRY(cudaEventRecord(ev[8], s));
-    // near field and far field on two private streams, joined back to the
-    // caller's stream before the combine
-    FMM_CUDA_TRY(cudaEventRecord(h->ev_fork, s));
-    FMM_CUDA_TRY(cudaStreamWaitEvent(h->s2, h->ev_fork, 0));
-    FMM_CUDA_TRY(cudaStreamWaitEvent(h->sfar, h->ev_fork, 0));
-    h->work = h->sfar;
-    fmm::far_field(h);
-    FMM_CUDA_TRY(cudaEventRecord(h->ev_far, h->sfar));
-    FMM_CUDA_TRY(cudaEventRecord(ev[9], h->s2));
-    fmm::near_field(h, h->s2);
-    FMM_CUDA_TRY(cudaEventRecord(ev[10], h->s2));
-    FMM_CUDA_TRY(cudaEventRecord(h->ev_join, h->s2));
-    h->work = h->stream;
-    FMM_CUDA_TRY(cudaStreamWaitEvent(s, h->ev_join, 0));
-    FMM_CUDA_TRY(cudaStreamWaitEvent(s, h->ev_far, 0));
+    if (h->overlap) {
+        // near field and far field on two private streams, joined back to the
+        // caller's stream before the combine
+        FMM_CUDA_TRY(cudaEventRecord(h->ev_fork, s));
+        FMM_CUDA_TRY(cudaStreamWaitEvent(h->s2, h->ev_fork, 0));
+        FMM_CUDA_TRY(cudaStreamWaitEvent(h->sfar, h->ev_fork, 0));
+        h->work = h->sfar;
+        fmm::far_field(h);
+        FMM_CUDA_TRY(cudaEventRecord(h->ev_far, h->sfar));
+        FMM_CUDA_TRY(cudaEventRecord(ev[9], h->s2));
+        fmm::near_field(h, h->s2);
+        FMM_CUDA_TRY(cudaEventRecord(ev[10], h->s2));
+        FMM_CUDA_TRY(cudaEventRecord(h->ev_join, h->s2));
+        h->work = h->stream;
+        FMM_CUDA_TRY(cudaStreamWaitEvent(s, h->ev_join, 0));
+        FMM_CUDA_TRY(cudaStreamWaitEvent(s, h->ev_far, 0));
+    } else {
+        // in turn on the caller's stream
+        h->work = s;
+        fmm::far_field(h);
+        FMM_CUDA_TRY(cudaEventRecord(ev[9], s));
+        fmm::near_field(h, s);
+        FMM_CUDA_TRY(cudaEventRecord(ev[10], s));
+    }
     FMM_CUDA_TRY(cudaEventRecord(ev[11], s));
     const size_t es = h->dtype == FMM_F64 ? 8 : 4;
     void *pd = phi, *gd = grad;

@@ -736,13 +736,14 @@ int m2l_tile_size(fmm_ctx *h)
 // a target in octant o of its parent, the lattice offsets v with
 // 3 < fl(theta^2 |v|^2) (the MAC accepts the pair) whose parent offset
 // u = floor((o + v) / 2) has 3 >= fl(theta^2 |u|^2) (the parents were
-// rejected). Offsets are bounded by the lattice of the deepest level, so a tiny
-// theta on a shallow tree stays small. Rebuilt only when the bound grows.
+// rejected). Offsets are bounded by the largest coordinate difference of two
+// existing cells of one level, so a tiny theta stays small on shallow trees
+// and on deep chains of a few cells alike. Rebuilt only when the bound grows.
 void stencil_update(fmm_ctx *h)
 {
     const double c = h->cmac;
     const int Rfull = 2 * (int)std::ceil(std::sqrt(3.0 / c)) + 3;
-    const int R = std::min(Rfull, h->depth >= 20 ? Rfull : (1 << h->depth));
+    const int R = std::min(Rfull, h->lattice_extent);
     if (R <= h->st_R && h->st_dev.p) return;
     std::map<std::tuple<int, int, int>, int> vid;
     int nv = 0;

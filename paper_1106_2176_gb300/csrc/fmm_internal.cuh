@@ -136,6 +136,8 @@ struct fmm_ctx {
     bool host_mem = false;
     int precision = FMM_FP64;
     int engine_used = 0;
+    int overlap = 1;  // far and near field on concurrent streams
+    int lattice_extent = 0;  // largest same-level coordinate difference of existing cells
     int ncells = 0, depth = 0, nleaves = 0;
     std::vector<int> lvl_start;  // cells of level l are [lvl_start[l], lvl_start[l+1])
     int64_t n_p2p = 0, n_m2lx = 0, n_m2l_implicit = 0, n_interactions = 0;

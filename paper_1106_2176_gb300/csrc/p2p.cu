@@ -15,6 +15,7 @@
 // sources whose totals are added with TwoSum, and slices are combined in FP64
 // in a fixed order, so the result does not depend on scheduling.
 #include <algorithm>
+#include <type_traits>
 
 #include "fmm_internal.cuh"
 
@@ -80,6 +81,15 @@ __device__ __forceinline__ void acc2(float &hi, float &lo, float b)
 __device__ __forceinline__ void acc2(double &hi, double &lo, double b) { hi += b; }
 
 constexpr int P2P_T = 128;
+// compile-time tuning knobs: targets per thread of the FP32 paths, and the
+// minimum number of resident blocks per SM given to __launch_bounds__ (1
+// leaves the register count to the compiler)
+#ifndef FMM_P2P_TPT
+#define FMM_P2P_TPT 2
+#endif
+#ifndef FMM_P2P_MINB
+#define FMM_P2P_MINB 6
+#endif
 
 // One source against the TPT targets of a thread.
 template <bool CHECK, bool DS, int TPT, class T, class T4>
@@ -124,6 +134,146 @@ __device__ __forceinline__ void p2p_range(int j0, int j1, const T4 *sh, const fl
     }
 }
 
+// ---------------------------------------------------------------------------
+// Packed FP32 pairs (sm_100 and later: add/sub/mul/fma .f32x2). Two sources
+// are handled per instruction against one target; the shared chunk holds the
+// sources as pair records (x0 x1 y0 y1 | z0 z1 q0 q1), so one 16-byte load
+// gives two packed operands. Each packed instruction does the work of two
+// FP32 ones in one issue slot.
+// ---------------------------------------------------------------------------
+typedef unsigned long long f2;
+
+__device__ __forceinline__ f2 f2_sub(f2 a, f2 b)
+{
+    f2 d;
+    asm("sub.rn.ftz.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b)
+{
+    f2 d;
+    asm("add.rn.ftz.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b)
+{
+    f2 d;
+    asm("mul.rn.ftz.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c)
+{
+    f2 d;
+    asm("fma.rn.ftz.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2 f2_pack(float lo, float hi)
+{
+    f2 d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+    return d;
+}
+__device__ __forceinline__ void f2_unpack(f2 a, float &lo, float &hi) { asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a)); }
+
+// Two sources (packed sx..sq) against one target (tx, ty, tz duplicated in
+// both halves): p += q / r, g += q (x_j - x_i) / r^3, per half.
+template <bool CHECK>
+__device__ __forceinline__ void interact_pk(f2 sx, f2 sy, f2 sz, f2 sq, f2 tx, f2 ty, f2 tz, f2 &p, f2 &gx, f2 &gy,
+                                            f2 &gz)
+{
+    const f2 dx = f2_sub(sx, tx), dy = f2_sub(sy, ty), dz = f2_sub(sz, tz);
+    const f2 r2 = f2_fma(dz, dz, f2_fma(dy, dy, f2_mul(dx, dx)));
+    float a, b;
+    f2_unpack(r2, a, b);
+    float ra = rsqrtf(a), rb = rsqrtf(b);
+    if (CHECK) {
+        ra = a > 0.f ? ra : 0.f;
+        rb = b > 0.f ? rb : 0.f;
+    }
+    const f2 ri = f2_pack(ra, rb);
+    const f2 qr = f2_mul(sq, ri);
+    p = f2_add(p, qr);
+    const f2 qr3 = f2_mul(qr, f2_mul(ri, ri));
+    gx = f2_fma(qr3, dx, gx);
+    gy = f2_fma(qr3, dy, gy);
+    gz = f2_fma(qr3, dz, gz);
+}
+
+// Sources [j0, j1) of a pair-record chunk against the TPT targets of a
+// thread. An odd source at either end is taken alone; the pairs between run in
+// blocks of 32 pairs (64 sources) whose two halves are added and then summed
+// into (h, lo) with TwoSum, as in the unpacked path.
+template <bool CHECK, int TPT>
+__device__ __forceinline__ void p2p_range_pk(int j0, int j1, const float *shf, const f2 (&tx)[TPT], const f2 (&ty)[TPT],
+                                             const f2 (&tz)[TPT], float (&h)[4 * TPT], float (&lo)[4 * TPT])
+{
+    auto single = [&](int j) {
+        const float *r = shf + 8 * (j >> 1) + (j & 1);
+        const float4 sj = make_float4(r[0], r[2], r[4], r[6]);
+#pragma unroll
+        for (int k = 0; k < TPT; k++) {
+            float xi, yi, zi, u;
+            f2_unpack(tx[k], xi, u);
+            f2_unpack(ty[k], yi, u);
+            f2_unpack(tz[k], zi, u);
+            float pp = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+            interact<CHECK>(make_float4(xi, yi, zi, 0.f), sj, pp, gx, gy, gz);
+            acc2(h[4 * k], lo[4 * k], pp);
+            acc2(h[4 * k + 1], lo[4 * k + 1], gx);
+            acc2(h[4 * k + 2], lo[4 * k + 2], gy);
+            acc2(h[4 * k + 3], lo[4 * k + 3], gz);
+        }
+    };
+    int a = j0, b = j1;
+    if (a < b && (a & 1)) single(a++);
+    if (a < b && (b & 1)) single(--b);
+    const ulonglong2 *pr = reinterpret_cast<const ulonglong2 *>(shf);
+    auto fold = [&](const f2 (&acc)[4 * TPT]) {
+#pragma unroll
+        for (int c = 0; c < 4 * TPT; c++) {
+            float u, v;
+            f2_unpack(acc[c], u, v);
+            acc2(h[c], lo[c], u + v);
+        }
+    };
+    int k = a >> 1;
+    const int k1 = b >> 1;
+    for (; k + 32 <= k1; k += 32) {
+        f2 acc[4 * TPT];
+#pragma unroll
+        for (int c = 0; c < 4 * TPT; c++) acc[c] = 0ull;
+#pragma unroll 8
+        for (int kk = 0; kk < 32; kk++) {
+            const ulonglong2 A = pr[2 * (k + kk)], B = pr[2 * (k + kk) + 1];
+#pragma unroll
+            for (int t = 0; t < TPT; t++)
+                interact_pk<CHECK>(A.x, A.y, B.x, B.y, tx[t], ty[t], tz[t], acc[4 * t], acc[4 * t + 1], acc[4 * t + 2],
+                                   acc[4 * t + 3]);
+        }
+        fold(acc);
+    }
+    if (k < k1) {
+        f2 acc[4 * TPT];
+#pragma unroll
+        for (int c = 0; c < 4 * TPT; c++) acc[c] = 0ull;
+#pragma unroll 4
+        for (; k < k1; k++) {
+            const ulonglong2 A = pr[2 * k], B = pr[2 * k + 1];
+#pragma unroll
+            for (int t = 0; t < TPT; t++)
+                interact_pk<CHECK>(A.x, A.y, B.x, B.y, tx[t], ty[t], tz[t], acc[4 * t], acc[4 * t + 1], acc[4 * t + 2],
+                                   acc[4 * t + 3]);
+        }
+        fold(acc);
+    }
+}
+
+__device__ __forceinline__ void cpa4(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+
 __device__ __forceinline__ void cpa16(void *dst, const void *src)
 {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
@@ -146,13 +296,14 @@ struct RunCursor {
 // need the j == i / r == 0 test. Slices are reduced in FP64 in a fixed order.
 // DS: FP32 (hi, lo) coordinates for FP64 inputs.
 template <class T, bool DS, int TPT>
-__global__ void __launch_bounds__(P2P_T) p2p_k(const typename Vec4<T>::type *__restrict__ xs, const float4 *__restrict__ xlo,
+__global__ void __launch_bounds__(P2P_T, sizeof(T) == 4 ? FMM_P2P_MINB : 1) p2p_k(const typename Vec4<T>::type *__restrict__ xs, const float4 *__restrict__ xlo,
                                                const int *__restrict__ leaves, const int *__restrict__ begin,
                                                const int *__restrict__ end, const int *__restrict__ ptr,
                                                const int2 *__restrict__ runs, const int *__restrict__ nrun,
                                                double4_32a *__restrict__ near)
 {
     using T4 = typename Vec4<T>::type;
+    constexpr bool PK = std::is_same<T, float>::value && !DS;  // packed pairs (pair-record chunks)
     constexpr int CH = DS ? 512 : (sizeof(T) == 8 ? 512 : 1024);
     __shared__ T4 sh[2][CH];
     __shared__ float4 shlo[DS ? 2 : 1][DS ? CH : 1];
@@ -173,11 +324,21 @@ __global__ void __launch_bounds__(P2P_T) p2p_k(const typename Vec4<T>::type *__r
             const int len = rr.y - g0;
             const int take = min(len, CH - fill);
             for (int j = threadIdx.x; j < take; j += P2P_T) {
+                if constexpr (PK) {  // source c -> pair record c / 2, half c % 2
+                    const int c = fill + j;
+                    float *d = reinterpret_cast<float *>(&sh[bf][0]) + 8 * (c >> 1) + (c & 1);
+                    const float *g = reinterpret_cast<const float *>(xs + g0 + j);
+                    cpa4(d, g);
+                    cpa4(d + 2, g + 1);
+                    cpa4(d + 4, g + 2);
+                    cpa4(d + 6, g + 3);
+                } else {
 #pragma unroll
-                for (int c = 0; c < (int)(sizeof(T4) / 16); c++)  // 16-byte pieces of one particle
-                    cpa16(reinterpret_cast<char *>(&sh[bf][fill + j]) + 16 * c,
-                          reinterpret_cast<const char *>(xs + g0 + j) + 16 * c);
-                if constexpr (DS) cpa16(&shlo[bf][fill + j], xlo + g0 + j);
+                    for (int c = 0; c < (int)(sizeof(T4) / 16); c++)  // 16-byte pieces of one particle
+                        cpa16(reinterpret_cast<char *>(&sh[bf][fill + j]) + 16 * c,
+                              reinterpret_cast<const char *>(xs + g0 + j) + 16 * c);
+                    if constexpr (DS) cpa16(&shlo[bf][fill + j], xlo + g0 + j);
+                }
             }
             const int a = max(g0, tb), b = min(g0 + take, te);
             if (a < b) {
@@ -209,6 +370,15 @@ __global__ void __launch_bounds__(P2P_T) p2p_k(const typename Vec4<T>::type *__r
             if constexpr (DS) xl[k] = xlo[i];
             else xl[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
+        f2 tx[TPT], ty[TPT], tz[TPT];
+#pragma unroll
+        for (int k = 0; k < TPT; k++) {
+            if constexpr (PK) {
+                tx[k] = f2_pack((float)x[k].x, (float)x[k].x);
+                ty[k] = f2_pack((float)x[k].y, (float)x[k].y);
+                tz[k] = f2_pack((float)x[k].z, (float)x[k].z);
+            } else tx[k] = ty[k] = tz[k] = 0ull;
+        }
         T h[4 * TPT], lo[4 * TPT];
 #pragma unroll
         for (int c = 0; c < 4 * TPT; c++) h[c] = lo[c] = T(0);
@@ -226,12 +396,24 @@ __global__ void __launch_bounds__(P2P_T) p2p_k(const typename Vec4<T>::type *__r
             }
             __syncthreads();  // chunk bf complete for every thread
             if (act) {
-                const int jlo = (int)(((long long)fill * sl) / S), jhi = (int)(((long long)fill * (sl + 1)) / S);
-                const T4 *sb = sh[bf];
-                const float4 *sbl = shlo[DS ? bf : 0];
-                p2p_range<false, DS, TPT>(jlo, min(jhi, slo), sb, sbl, x, xl, h, lo);
-                p2p_range<true, DS, TPT>(max(jlo, slo), min(jhi, shi), sb, sbl, x, xl, h, lo);
-                p2p_range<false, DS, TPT>(max(jlo, shi), jhi, sb, sbl, x, xl, h, lo);
+                if constexpr (PK) {
+                    // slice bounds on even sources, so only the target leaf's
+                    // own segment and an odd chunk end leave single sources
+                    const int np = (fill + 1) >> 1;
+                    const int jlo = min(fill, 2 * (int)(((long long)np * sl) / S));
+                    const int jhi = min(fill, 2 * (int)(((long long)np * (sl + 1)) / S));
+                    const float *sb = reinterpret_cast<const float *>(&sh[bf][0]);
+                    p2p_range_pk<false, TPT>(jlo, min(jhi, slo), sb, tx, ty, tz, h, lo);
+                    p2p_range_pk<true, TPT>(max(jlo, slo), min(jhi, shi), sb, tx, ty, tz, h, lo);
+                    p2p_range_pk<false, TPT>(max(jlo, shi), jhi, sb, tx, ty, tz, h, lo);
+                } else {
+                    const int jlo = (int)(((long long)fill * sl) / S), jhi = (int)(((long long)fill * (sl + 1)) / S);
+                    const T4 *sb = sh[bf];
+                    const float4 *sbl = shlo[DS ? bf : 0];
+                    p2p_range<false, DS, TPT>(jlo, min(jhi, slo), sb, sbl, x, xl, h, lo);
+                    p2p_range<true, DS, TPT>(max(jlo, slo), min(jhi, shi), sb, sbl, x, xl, h, lo);
+                    p2p_range<false, DS, TPT>(max(jlo, shi), jhi, sb, sbl, x, xl, h, lo);
+                }
             }
             __syncthreads();  // chunk bf consumed before it is refilled
             bf ^= 1;
@@ -270,10 +452,10 @@ void near_field(fmm_ctx *h, cudaStream_t s)
     if (h->precision == FMM_FP64)
         p2p_k<double, false, 2><<<h->nleaves, P2P_T, 0, s>>>(h->xs64.as<double4_32a>(), nullptr, lv, cb, ce, pp, ru, nr, out);
     else if (h->dtype == FMM_F64)
-        p2p_k<float, true, 3><<<h->nleaves, P2P_T, 0, s>>>(h->xs32.as<float4>(), h->xs32lo.as<float4>(), lv, cb, ce, pp, ru,
+        p2p_k<float, true, FMM_P2P_TPT><<<h->nleaves, P2P_T, 0, s>>>(h->xs32.as<float4>(), h->xs32lo.as<float4>(), lv, cb, ce, pp, ru,
                                                            nr, out);
     else
-        p2p_k<float, false, 3><<<h->nleaves, P2P_T, 0, s>>>(h->xs32.as<float4>(), nullptr, lv, cb, ce, pp, ru, nr, out);
+        p2p_k<float, false, FMM_P2P_TPT><<<h->nleaves, P2P_T, 0, s>>>(h->xs32.as<float4>(), nullptr, lv, cb, ce, pp, ru, nr, out);
     count_launch(h);
     check_launch("p2p");
 }

@@ -530,6 +530,32 @@ __device__ __forceinline__ unsigned long long warp_reserve(unsigned long long *c
     return base + (x - cnt);
 }
 
+// Per level, the smallest and largest lattice coordinate of the existing
+// cells (ext[0..66): minima, level-major x y z; ext[66..132): maxima). Lanes
+// of one level reduce in the warp first; cells are level-contiguous.
+__global__ void extent_k(int nc, const int4 *__restrict__ xyz, int *__restrict__ ext)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool in = i < nc;
+    const int4 a = in ? xyz[i] : make_int4(0, 0, 0, 0);
+    const int l = in ? a.w : -1;
+    const unsigned grp = __match_any_sync(0xffffffffu, l);
+    if (!in) return;
+    const int sh = FMM_MAXLEVEL - l;
+    const int x = a.x >> sh, y = a.y >> sh, z = a.z >> sh;
+    const int mnx = __reduce_min_sync(grp, x), mny = __reduce_min_sync(grp, y), mnz = __reduce_min_sync(grp, z);
+    const int mxx = __reduce_max_sync(grp, x), mxy = __reduce_max_sync(grp, y), mxz = __reduce_max_sync(grp, z);
+    if ((int)(threadIdx.x & 31) == __ffs(grp) - 1) {
+        int *mn = ext + 3 * l, *mx = ext + 3 * (FMM_MAXLEVEL + 1) + 3 * l;
+        atomicMin(mn, mnx);
+        atomicMin(mn + 1, mny);
+        atomicMin(mn + 2, mnz);
+        atomicMax(mx, mxx);
+        atomicMax(mx + 1, mxy);
+        atomicMax(mx + 2, mxz);
+    }
+}
+
 // One thread per (frontier pair, slot): the pair (A, B) expands into at most
 // 8 x 8 child pairs; slot k takes child a = child[A] + k of A (or A itself)
 // against the children of B (or B itself), at most 8 pairs, classified in
@@ -761,8 +787,8 @@ void tree_build(fmm_ctx *h, const void *x, const void *q, int64_t n, int dt)
     const int TB = 256;
     h->box.ensure(sizeof(Box));
     Box *box = h->box.as<Box>();
-    h->counters.ensure(sizeof(TravCounters) + 64);
-    h->hpin.ensure(4096);
+    h->counters.ensure(sizeof(TravCounters) + 64 + sizeof(int) * 6 * (FMM_MAXLEVEL + 1));
+    h->hpin.ensure(8192);
 
     // 1. bounding cube, keys
     box_init_k<<<1, 1, 0, s>>>(box);
@@ -889,10 +915,25 @@ void tree_build(fmm_ctx *h, const void *x, const void *q, int64_t n, int dt)
         leaves_write_k<<<nblocks(ncells, TB), TB, 0, s>>>(ncells, h->c_nchild.as<int>(), h->split_off.as<unsigned>(),
                                                           h->leaves.as<int>());
         count_launch(h);
+        // lattice extent of the cells of every level: no same-level pair is
+        // farther apart, which bounds the M2L stencil on deep adaptive trees
+        constexpr int NE = 3 * (FMM_MAXLEVEL + 1);
+        int *ext = reinterpret_cast<int *>(h->counters.as<char>() + sizeof(TravCounters) + 64);
+        FMM_CUDA_TRY(cudaMemsetAsync(ext, 0x7f, sizeof(int) * NE, s));
+        FMM_CUDA_TRY(cudaMemsetAsync(ext + NE, 0xff, sizeof(int) * NE, s));
+        extent_k<<<nblocks(ncells, TB), TB, 0, s>>>(ncells, h->c_xyz.as<int4>(), ext);
+        count_launch(h);
         unsigned *hp = h->hpin.as<unsigned>();
+        int *hext = reinterpret_cast<int *>(h->hpin.as<char>() + 4096);
         FMM_CUDA_TRY(cudaMemcpyAsync(hp, tot, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+        FMM_CUDA_TRY(cudaMemcpyAsync(hext, ext, sizeof(int) * 2 * NE, cudaMemcpyDeviceToHost, s));
         FMM_CUDA_TRY(cudaStreamSynchronize(s));
         h->nleaves = (int)*hp;
+        int E = 0;
+        for (int l = 0; l <= depth; l++)
+            for (int d = 0; d < 3; d++)
+                if (hext[NE + 3 * l + d] >= hext[3 * l + d]) E = std::max(E, hext[NE + 3 * l + d] - hext[3 * l + d]);
+        h->lattice_extent = E;
     }
 
     // 5. dual traversal

@@ -75,6 +75,7 @@ def lib():
     L.fmm_create.argtypes = [i64, i32, d, i32, ctypes.POINTER(_vp)]
     L.fmm_set_precision.argtypes = [_vp, i32]
     L.fmm_set_m2l_engine.argtypes = [_vp, i32]
+    L.fmm_set_overlap.argtypes = [_vp, i32]
     L.fmm_set_stream.argtypes = [_vp, _vp]
     L.fmm_build.argtypes = [_vp, _vp, _vp, i64, i32]
     L.fmm_evaluate.argtypes = [_vp, _vp, _vp]
@@ -111,12 +112,13 @@ def _stream_ptr():
 class FMM:
     """Handle of one FMM configuration (N, p, theta, ncrit) on the current GPU."""
 
-    def __init__(self, N, p=8, theta=0.5, ncrit=64, precision="fp64", m2l_engine="auto"):
+    def __init__(self, N, p=8, theta=0.5, ncrit=64, precision="fp64", m2l_engine="auto", overlap=True):
         self._h = _vp()
         _check(lib().fmm_create(int(N), int(p), float(theta), int(ncrit), ctypes.byref(self._h)))
         self.N, self.p, self.theta, self.ncrit = int(N), int(p), float(theta), int(ncrit)
         self.set_precision(precision)
         self.set_m2l_engine(m2l_engine)
+        self.set_overlap(overlap)
         self._n = 0
         self._dtype = None
         self._host = False
@@ -130,6 +132,11 @@ class FMM:
     def set_m2l_engine(self, engine):
         e = {"auto": FMM_M2L_AUTO, "tensor": FMM_M2L_TENSOR, "cudacore": FMM_M2L_CUDACORE}[engine]
         _check(lib().fmm_set_m2l_engine(self._h, e), self._h)
+
+    def set_overlap(self, on):
+        """True: far and near field run concurrently; False: in turn (per-phase times)."""
+        _check(lib().fmm_set_overlap(self._h, 1 if on else 0), self._h)
+        self.overlap = bool(on)
 
     # -- the two calls of the method ------------------------------------------
     def build(self, x, q):

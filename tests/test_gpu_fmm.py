@@ -68,6 +68,39 @@ def test_small_theta_is_direct_sum():
     assert rel(phi, pd) <= 1e-13 and rel(grad, gd) <= 1e-13
 
 
+@pytest.mark.parametrize("gen,ncrit", [("uniform", 32), ("uniform", 7), ("plummer", 13)])
+def test_mixed_near_field_matches_direct_sum(gen, ncrit):
+    # theta -> 0 leaves only P2P: the FP32 near-field kernel (packed pairs,
+    # odd slice ends, several shared-memory chunks, the r = 0 test on
+    # coincident particles of one leaf) against the FP64 direct sum of the
+    # same FP32-rounded inputs
+    n = 5000
+    x, q = (inputs.uniform_cube(n, 23) if gen == "uniform" else inputs.plummer(n, 23))
+    x = x.astype(np.float32)
+    q = q.astype(np.float32)
+    x[100:111] = x[100]  # eleven coincident particles
+    x64, q64 = x.astype(np.float64), q.astype(np.float64)
+    pd, gd = oracle.direct(x64, q64)
+    phi, grad, f = run_fmm(x, q, 3, 0.001, ncrit, precision="mixed", dtype=np.float32)
+    assert f.stats()["n_m2l_pairs"] == 0
+    assert rel(phi, pd) <= MIXED_SLACK and rel(grad, gd) <= MIXED_SLACK
+
+
+def test_serial_schedule_is_bitwise_identical():
+    # fmm_set_overlap(0) runs the far and near field in turn on one stream;
+    # every kernel's result is independent of the schedule
+    x, q = inputs.uniform_cube(50000, 24, dtype=np.float32)
+    p1, g1, f1 = run_fmm(x, q, 8, 0.5, 64, precision="mixed", dtype=np.float32)
+    torch = torch_cuda()
+    f1.set_overlap(False)
+    xt, qt = torch.tensor(x, device="cuda"), torch.tensor(q, device="cuda")
+    f1.build(xt, qt)
+    p2, g2 = [t.cpu().numpy().astype(np.float64) for t in f1.evaluate()]
+    st = f1.stats()
+    assert np.array_equal(p1, p2) and np.array_equal(g1, g2)
+    assert st["ms_p2p"] > 0 and st["ms_m2l"] > 0
+
+
 def test_single_and_coincident_particles():
     for x in (np.array([[0.1, 0.2, 0.3]]), np.tile([[0.5, 0.5, 0.5]], (40, 1))):
         q = np.linspace(1, 2, len(x))
