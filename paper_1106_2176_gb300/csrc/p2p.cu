@@ -80,7 +80,10 @@ __device__ __forceinline__ void acc2(float &hi, float &lo, float b)
 }
 __device__ __forceinline__ void acc2(double &hi, double &lo, double b) { hi += b; }
 
-constexpr int P2P_T = 128;
+#ifndef FMM_P2P_T
+#define FMM_P2P_T 128
+#endif
+constexpr int P2P_T = FMM_P2P_T;  // threads per block (one target leaf)
 // compile-time tuning knobs: targets per thread of the FP32 paths, and the
 // minimum number of resident blocks per SM given to __launch_bounds__ (1
 // leaves the register count to the compiler)
@@ -88,8 +91,25 @@ constexpr int P2P_T = 128;
 #define FMM_P2P_TPT 2
 #endif
 #ifndef FMM_P2P_MINB
-#define FMM_P2P_MINB 6
+#define FMM_P2P_MINB 7
 #endif
+// sources per shared-memory chunk of the FP32-input path, and the number of
+// chunk buffers (2: the next chunk is copied while the current one is
+// computed; 3: the next two)
+#ifndef FMM_P2P_CH
+#define FMM_P2P_CH 704
+#endif
+#ifndef FMM_P2P_NBUF
+#define FMM_P2P_NBUF 2
+#endif
+// source pairs per TwoSum block and the unroll of the pair loop
+#ifndef FMM_P2P_BLK
+#define FMM_P2P_BLK 64
+#endif
+#ifndef FMM_P2P_UNROLL
+#define FMM_P2P_UNROLL 8
+#endif
+constexpr int P2P_UNROLL = FMM_P2P_UNROLL;
 
 // One source against the TPT targets of a thread.
 template <bool CHECK, bool DS, int TPT, class T, class T4>
@@ -201,12 +221,14 @@ __device__ __forceinline__ void interact_pk(f2 sx, f2 sy, f2 sz, f2 sq, f2 tx, f
 
 // Sources [j0, j1) of a pair-record chunk against the TPT targets of a
 // thread. An odd source at either end is taken alone; the pairs between run in
-// blocks of 32 pairs (64 sources) whose two halves are added and then summed
-// into (h, lo) with TwoSum, as in the unpacked path.
+// blocks of BLK pairs whose two halves are added and then summed with TwoSum
+// into the thread's (hi, lo) state, kept in shared memory (hl[c * P2P_T] and
+// hl[(4 TPT + c) * P2P_T]) since it is touched once per block only.
 template <bool CHECK, int TPT>
 __device__ __forceinline__ void p2p_range_pk(int j0, int j1, const float *shf, const f2 (&tx)[TPT], const f2 (&ty)[TPT],
-                                             const f2 (&tz)[TPT], float (&h)[4 * TPT], float (&lo)[4 * TPT])
+                                             const f2 (&tz)[TPT], float *hl)
 {
+    auto add = [&](int c, float v) { acc2(hl[c * P2P_T], hl[(4 * TPT + c) * P2P_T], v); };
     auto single = [&](int j) {
         const float *r = shf + 8 * (j >> 1) + (j & 1);
         const float4 sj = make_float4(r[0], r[2], r[4], r[6]);
@@ -218,10 +240,10 @@ __device__ __forceinline__ void p2p_range_pk(int j0, int j1, const float *shf, c
             f2_unpack(tz[k], zi, u);
             float pp = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
             interact<CHECK>(make_float4(xi, yi, zi, 0.f), sj, pp, gx, gy, gz);
-            acc2(h[4 * k], lo[4 * k], pp);
-            acc2(h[4 * k + 1], lo[4 * k + 1], gx);
-            acc2(h[4 * k + 2], lo[4 * k + 2], gy);
-            acc2(h[4 * k + 3], lo[4 * k + 3], gz);
+            add(4 * k, pp);
+            add(4 * k + 1, gx);
+            add(4 * k + 2, gy);
+            add(4 * k + 3, gz);
         }
     };
     int a = j0, b = j1;
@@ -233,17 +255,17 @@ __device__ __forceinline__ void p2p_range_pk(int j0, int j1, const float *shf, c
         for (int c = 0; c < 4 * TPT; c++) {
             float u, v;
             f2_unpack(acc[c], u, v);
-            acc2(h[c], lo[c], u + v);
+            add(c, u + v);
         }
     };
     int k = a >> 1;
     const int k1 = b >> 1;
-    for (; k + 32 <= k1; k += 32) {
+    for (; k + FMM_P2P_BLK <= k1; k += FMM_P2P_BLK) {
         f2 acc[4 * TPT];
 #pragma unroll
         for (int c = 0; c < 4 * TPT; c++) acc[c] = 0ull;
-#pragma unroll 8
-        for (int kk = 0; kk < 32; kk++) {
+#pragma unroll P2P_UNROLL
+        for (int kk = 0; kk < FMM_P2P_BLK; kk++) {
             const ulonglong2 A = pr[2 * (k + kk)], B = pr[2 * (k + kk) + 1];
 #pragma unroll
             for (int t = 0; t < TPT; t++)
@@ -304,10 +326,13 @@ __global__ void __launch_bounds__(P2P_T, sizeof(T) == 4 ? FMM_P2P_MINB : 1) p2p_
 {
     using T4 = typename Vec4<T>::type;
     constexpr bool PK = std::is_same<T, float>::value && !DS;  // packed pairs (pair-record chunks)
-    constexpr int CH = DS ? 512 : (sizeof(T) == 8 ? 512 : 1024);
-    __shared__ T4 sh[2][CH];
+    constexpr int CH = DS ? 512 : (sizeof(T) == 8 ? 512 : FMM_P2P_CH);
+    constexpr int NB = PK ? FMM_P2P_NBUF : 2;
+    static_assert(NB == 2 || NB == 3, "two or three chunk buffers");
+    __shared__ T4 sh[NB][CH];
     __shared__ float4 shlo[DS ? 2 : 1][DS ? CH : 1];
-    static_assert(sizeof(T4) * 2 * CH >= sizeof(double) * P2P_T * 4 * TPT, "slice sums reuse the source buffers");
+    __shared__ float hls[PK ? 8 * TPT * P2P_T : 1];  // packed path: per-thread TwoSum state, column-major
+    static_assert(sizeof(T4) * NB * CH >= sizeof(double) * P2P_T * 4 * TPT, "slice sums reuse the source buffers");
     double *red = reinterpret_cast<double *>(&sh[0][0]);  // slice sums, after the last chunk
     const int A = leaves[blockIdx.x];
     const int tb = begin[A], te = end[A];
@@ -382,30 +407,46 @@ __global__ void __launch_bounds__(P2P_T, sizeof(T) == 4 ? FMM_P2P_MINB : 1) p2p_
         T h[4 * TPT], lo[4 * TPT];
 #pragma unroll
         for (int c = 0; c < 4 * TPT; c++) h[c] = lo[c] = T(0);
+        if constexpr (PK) {
+#pragma unroll
+            for (int c = 0; c < 8 * TPT; c++) hls[c * P2P_T + threadIdx.x] = 0.f;
+        }
         RunCursor cur{r0, r1, 0};
         __syncthreads();  // buffers free (previous target block or slice sums)
         int slo, shi, fill = stage(cur, 0, slo, shi);
         int bf = 0;
+        // NB = 3: chunk i + 1 is staged ahead as well; chunk i + 2 goes into
+        // the buffer of chunk i - 1 once every thread has passed the barrier
+        // that follows chunk i - 1
+        int nslo = 0, nshi = 0, nfill = 0;
+        if (NB == 3 && cur.k < cur.k1) nfill = stage(cur, 1, nslo, nshi);
         while (fill > 0) {
-            int nslo = 0, nshi = 0, nfill = 0;
-            if (cur.k < cur.k1) {
-                nfill = stage(cur, bf ^ 1, nslo, nshi);
-                cpa_wait1();
+            int n2lo = 0, n2hi = 0, n2fill = 0;
+            if constexpr (NB == 3) {
+                if (nfill > 0) cpa_wait1();
+                else cpa_wait0();
+                __syncthreads();  // chunk bf complete; chunk bf - 1 consumed by every thread
+                if (cur.k < cur.k1) n2fill = stage(cur, bf == 0 ? 2 : bf - 1, n2lo, n2hi);
             } else {
+                // one barrier per chunk: after it, chunk bf is complete and
+                // every thread has finished chunk bf - 1, whose buffer then
+                // takes chunk bf + 1 while chunk bf is computed
                 cpa_wait0();
+                __syncthreads();
+                nfill = cur.k < cur.k1 ? stage(cur, bf ^ 1, nslo, nshi) : 0;
             }
-            __syncthreads();  // chunk bf complete for every thread
             if (act) {
                 if constexpr (PK) {
                     // slice bounds on even sources, so only the target leaf's
                     // own segment and an odd chunk end leave single sources
-                    const int np = (fill + 1) >> 1;
-                    const int jlo = min(fill, 2 * (int)(((long long)np * sl) / S));
-                    const int jhi = min(fill, 2 * (int)(((long long)np * (sl + 1)) / S));
+                    const int np = (fill + 1) >> 1;  // np * S <= (CH / 2) * P2P_T fits in 32 bits
+                    const int jlo = min(fill, 2 * ((np * sl) / S));
+                    const int jhi = min(fill, 2 * ((np * (sl + 1)) / S));
                     const float *sb = reinterpret_cast<const float *>(&sh[bf][0]);
-                    p2p_range_pk<false, TPT>(jlo, min(jhi, slo), sb, tx, ty, tz, h, lo);
-                    p2p_range_pk<true, TPT>(max(jlo, slo), min(jhi, shi), sb, tx, ty, tz, h, lo);
-                    p2p_range_pk<false, TPT>(max(jlo, shi), jhi, sb, tx, ty, tz, h, lo);
+                    float *hl = hls + threadIdx.x;
+                    p2p_range_pk<false, TPT>(jlo, min(jhi, slo), sb, tx, ty, tz, hl);
+                    p2p_range_pk<true, TPT>(max(jlo, slo), min(jhi, shi), sb, tx, ty, tz, hl);
+                    p2p_range_pk<false, TPT>(max(jlo, shi), jhi, sb, tx, ty, tz, hl);
                 } else {
                     const int jlo = (int)(((long long)fill * sl) / S), jhi = (int)(((long long)fill * (sl + 1)) / S);
                     const T4 *sb = sh[bf];
@@ -415,13 +456,30 @@ __global__ void __launch_bounds__(P2P_T, sizeof(T) == 4 ? FMM_P2P_MINB : 1) p2p_
                     p2p_range<false, DS, TPT>(max(jlo, shi), jhi, sb, sbl, x, xl, h, lo);
                 }
             }
-            __syncthreads();  // chunk bf consumed before it is refilled
-            bf ^= 1;
-            fill = nfill;
-            slo = nslo;
-            shi = nshi;
+            if constexpr (NB == 3) {
+                bf = bf == 2 ? 0 : bf + 1;
+                fill = nfill;
+                slo = nslo;
+                shi = nshi;
+                nfill = n2fill;
+                nslo = n2lo;
+                nshi = n2hi;
+            } else {
+                bf ^= 1;
+                fill = nfill;
+                slo = nslo;
+                shi = nshi;
+            }
         }
+        __syncthreads();  // the last chunk consumed before the slice sums reuse it
         if (act) {
+            if constexpr (PK) {
+#pragma unroll
+                for (int c = 0; c < 4 * TPT; c++) {
+                    h[c] = hls[c * P2P_T + threadIdx.x];
+                    lo[c] = hls[(4 * TPT + c) * P2P_T + threadIdx.x];
+                }
+            }
 #pragma unroll
             for (int c = 0; c < 4 * TPT; c++) red[(sl * R + row) * 4 * TPT + c] = (double)h[c] + (double)lo[c];
         }
