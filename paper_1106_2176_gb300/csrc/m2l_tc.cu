@@ -16,19 +16,20 @@
 // the accumulator is drained into per-thread FP32 (hi, lo) TwoSum registers;
 // two TMEM buffers alternate so the drain overlaps the next MMAs.
 //
-// Per CTA (288 threads: 8 worker warps and 1 MMA warp), for every unit
-// (v, k-block) of 32 coefficients:
+// Per CTA (320 threads: 8 worker warps, 1 MMA warp, 1 operator warp), for
+// every unit (v, k-block) of 32 coefficients:
 //   - worker warp w copies, with cp.async, half of each of 32 target rows'
 //     raw FP32 multipole block (source found by a lattice lookup fetched QV
 //     vectors ahead into a shared ring; zero fill if the cell is absent) into
-//     a 128B-swizzled raw stage, and its lane 0 bulk-copies one eighth of the
-//     pre-split, pre-swizzled [T_hi ; T_lo] operator block into the same stage;
-//   - once a raw stage is full the workers split A into TF32 hi and lo
-//     (lo = a - hi) into a compute stage;
+//     a 128B-swizzled stage of the A ring;
+//   - the operator warp bulk-copies the pre-split, pre-swizzled [T_hi ; T_lo]
+//     operator block into a stage of the operator ring;
+//   - once its A stage is full, each worker splits its part into TF32 hi and
+//     lo (lo = a - hi) in a compute stage and refills the A stage;
 //   - one thread of the MMA warp issues the tcgen05.mma of the compute stage
-//     and commits to its "free" mbarrier.
-// RS raw stages and CS compute stages rotate. Every wait is bounded; on a
-// timeout the kernel records an error code and leaves after releasing its TMEM.
+//     and the operator stage and commits to their "free" mbarriers.
+// Every wait is bounded; on a timeout the kernel records an error code and
+// leaves after its copies have landed and its TMEM is released.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -191,29 +192,33 @@ __device__ __forceinline__ void cp_async_arrive_noinc(uint64_t *bar)
 // ---------------------------------------------------------------------------
 // Warp roles: warps 0-7 (256 threads: target row r = tid % 128 and half
 // h = tid / 128 of the coefficients) gather, split and drain; warp 8 issues
-// the MMAs. The gathered multipoles travel compact (raw FP32: 128 B per row and
-// k-block) and are split into TF32 (hi, lo) in shared memory; the operator
-// image arrives pre-split and is read by the MMAs where it lands.
+// the MMAs; warp 9 copies the operator blocks. Three rings of stages:
+//   A raw (RS): the gathered FP32 multipoles of a unit, 128 B per row and
+//     k-block. A worker warp fills and reads only its own 32 rows x half, so it
+//     refills a stage right after its own split of it, with no MMA wait.
+//   operator (BS): the pre-split [T_hi ; T_lo] block of a unit, one bulk copy,
+//     read by the MMAs where it lands and freed by their commit.
+//   compute (CS): A_hi, A_lo after the split, freed by the MMA commit.
 template <int NP, int KB>
 struct TcCfg {
-    static constexpr int M = 128;                         // target rows per tile
-    static constexpr int NW = 8;                          // worker warps
-    static constexpr int NT = NW * 32 + 32;               // threads (workers + MMA warp)
-    static constexpr int A_RAW = M * 128;                 // raw A k-block (FP32, swizzled)
-    static constexpr int B_RAW = 2 * NP * 128;            // [T_hi ; T_lo] k-block (TF32 pair, swizzled)
-    static constexpr int RAW = A_RAW + B_RAW;             // one raw stage (multiple of 1024)
-    static constexpr int CMP = 2 * A_RAW;                 // A_hi, A_lo
-    static constexpr int CS = 2;                          // compute stages
-    static constexpr int QV = 8;                          // lookahead of the source lookups (vectors)
-    static constexpr int RING = 2 * QV * M * 4;           // lookup ring
-    static constexpr int BUDGET = 210 * 1024 - CS * CMP - RING - 512;
-    static constexpr int RS = BUDGET >= 3 * RAW ? 3 : 2;  // raw stages (3 leaves room for a P2P block on the SM)
-    static constexpr int SMEM = RS * RAW + CS * CMP + RING + 512 + 1024;
+    static constexpr int M = 128;                  // target rows per tile
+    static constexpr int NW = 8;                   // worker warps
+    static constexpr int MMA_WARP = NW, B_WARP = NW + 1;
+    static constexpr int NT = NW * 32 + 64;        // threads (workers, MMA warp, operator warp)
+    static constexpr int A_RAW = M * 128;          // raw A k-block (FP32, swizzled)
+    static constexpr int B_RAW = 2 * NP * 128;     // [T_hi ; T_lo] k-block (TF32 pair, swizzled)
+    static constexpr int CMP = 2 * A_RAW;          // A_hi, A_lo
+    static constexpr int QV = 8;                   // lookahead of the source lookups (vectors)
+    static constexpr int RING = 2 * QV * M * 4;    // lookup ring
+    static constexpr int CS = 3;                   // compute stages
+    static constexpr int BUDGET = 220 * 1024 - RING - 512 - 1024 - CS * CMP;
+    static constexpr int BS = BUDGET >= 4 * B_RAW + 3 * A_RAW ? 4 : (BUDGET >= 3 * B_RAW + 2 * A_RAW ? 3 : 2);
+    static constexpr int RS = BUDGET >= BS * B_RAW + 3 * A_RAW ? 3 : 2;
+    static constexpr int SMEM = RS * A_RAW + BS * B_RAW + CS * CMP + RING + 512 + 1024;
+    static_assert(SMEM <= 227 * 1024, "shared memory of one CTA");
     static constexpr int TCOLS = 4 * NP <= 32 ? 32 : (4 * NP <= 64 ? 64 : (4 * NP <= 128 ? 128 : (4 * NP <= 256 ? 256 : 512)));
-    static constexpr int GV = 8;                          // vectors per accumulator drain
-    static constexpr int HN = NP / 2;                     // coefficients per thread
-    static constexpr bool COMP = true;                    // compensated registers for the drained sums
-    static constexpr int BW = 2 * NP / NW;                // operator rows copied per worker warp
+    static constexpr int GV = 8;                   // vectors per accumulator drain
+    static constexpr int HN = NP / 2;              // coefficients per thread
 };
 
 // Zero-padded copy of the scaled multipoles: out[c][KB * 32] (only when p^2 is
@@ -235,18 +240,21 @@ __global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
              int *__restrict__ err)
 {
     using C = TcCfg<NP, KB>;
-    constexpr int RS = C::RS, CS = C::CS, QV = C::QV, KP = KB * 32;
+    constexpr int RS = C::RS, BS = C::BS, CS = C::CS, QV = C::QV, KP = KB * 32;
     if ((int)blockIdx.x >= *ntiles) return;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-    unsigned char *raw = base;                          // RS x (A_RAW + B_RAW)
-    unsigned char *cmp = base + RS * C::RAW;            // CS x (A_hi, A_lo, T_hi, T_lo)
+    unsigned char *araw = base;                        // RS x A_RAW
+    unsigned char *bops = araw + RS * C::A_RAW;        // BS x B_RAW
+    unsigned char *cmp = bops + BS * C::B_RAW;         // CS x (A_hi, A_lo)
     int *ring = reinterpret_cast<int *>(cmp + CS * C::CMP);
     uint64_t *bar = reinterpret_cast<uint64_t *>(cmp + CS * C::CMP + C::RING);
-    uint64_t *raw_full = bar;                 // RS: 256 cp.async arrivals + 8 operator copies
-    uint64_t *cmp_full = bar + RS;            // CS: 256 arrivals after the split
-    uint64_t *cmp_free = bar + RS + CS;       // CS: MMA commits
-    uint64_t *acc_full = bar + RS + 2 * CS;   // 2: MMA commits at the end of a group
+    uint64_t *a_full = bar;                   // RS: 256 cp.async arrivals
+    uint64_t *b_full = a_full + RS;           // BS: operator copy (transaction bytes)
+    uint64_t *b_free = b_full + BS;           // BS: MMA commits
+    uint64_t *cmp_full = b_free + BS;         // CS: 256 arrivals after the split
+    uint64_t *cmp_free = cmp_full + CS;       // CS: MMA commits
+    uint64_t *acc_full = cmp_free + CS;       // 2: MMA commits at the end of a group
     uint64_t *acc_empty = acc_full + 2;       // 2: 256 arrivals after a drain
     uint64_t *fin = acc_full + 4;             // 1
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_full + 5);
@@ -273,7 +281,11 @@ __global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
     const int ngroups = (nv + C::GV - 1) / C::GV;
 
     if (tid == 0) {
-        for (int s = 0; s < RS; s++) mbar_init(&raw_full[s], 32 * C::NW + C::NW);
+        for (int s = 0; s < RS; s++) mbar_init(&a_full[s], 32 * C::NW);
+        for (int s = 0; s < BS; s++) {
+            mbar_init(&b_full[s], 1);
+            mbar_init(&b_free[s], 1);
+        }
         for (int s = 0; s < CS; s++) {
             mbar_init(&cmp_full[s], 32 * C::NW);
             mbar_init(&cmp_free[s], 1);
@@ -286,7 +298,7 @@ __global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == C::NW) {
+    if (warp == C::MMA_WARP) {
         __syncwarp();
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"(C::TCOLS));
@@ -297,15 +309,16 @@ __global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    if (!worker) {
+    if (warp == C::MMA_WARP) {
         // ------------------------------------------------------------ MMA warp
         if (lane == 0) {
             const uint32_t id_full = idesc_tf32(128, 2 * NP), id_half = idesc_tf32(128, NP);
             for (int u = 0; u < nunits; u++) {
                 if (*(volatile int *)abort_flag) break;
-                const int c = u % CS;
+                const int c = u % CS, bs = u % BS;
                 const int vi = u / KB, kb = u % KB, g = vi / C::GV, b = g & 1;
                 bool ok = mbar_wait(&cmp_full[c], (uint32_t)((u / CS) & 1));
+                if (ok) ok = mbar_wait(&b_full[bs], (uint32_t)((u / BS) & 1));
                 if (ok && kb == 0 && vi % C::GV == 0 && g >= 2) ok = mbar_wait(&acc_empty[b], (uint32_t)(((g - 2) >> 1) & 1));
                 if (!ok) {
                     atomicExch(abort_flag, 1);
@@ -315,7 +328,7 @@ __global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
                 tc_fence_after();
                 unsigned char *cs = cmp + c * C::CMP;
                 const uint32_t ahi = smem_u32(cs), alo = smem_u32(cs + C::A_RAW);
-                const uint32_t bb = smem_u32(raw + (u % RS) * C::RAW + C::A_RAW);
+                const uint32_t bb = smem_u32(bops + bs * C::B_RAW);
                 const uint32_t dmain = tmem + (uint32_t)(b * 2 * NP), dcorr = dmain + NP;
                 const bool first = (vi % C::GV == 0) && kb == 0;
 #pragma unroll
@@ -325,12 +338,35 @@ __global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
                     mma_tf32(dcorr, sdesc(alo + 32 * k), sdesc(bb + 32 * k), id_half, 1u);
                 }
                 mma_commit(&cmp_free[c]);
+                mma_commit(&b_free[bs]);
                 if ((kb == KB - 1) && ((vi % C::GV == C::GV - 1) || vi == nv - 1)) mma_commit(&acc_full[b]);
             }
             // every commit has arrived before the shared memory goes away
             mma_commit(fin);
             mbar_wait(fin, 0);
             for (int u = max(0, nunits - CS); u < nunits; u++) mbar_wait(&cmp_free[u % CS], (uint32_t)((u / CS) & 1));
+        }
+    } else if (warp == C::B_WARP) {
+        // ------------------------------------------------------- operator warp
+        if (lane == 0) {
+            int issued = 0;
+            for (int u = 0; u < nunits; u++) {
+                if (*(volatile int *)abort_flag) break;
+                const int bs = u % BS;
+                if (u >= BS && !mbar_wait(&b_free[bs], (uint32_t)(((u - BS) / BS) & 1))) {
+                    atomicExch(abort_flag, 1);
+                    break;
+                }
+                const int4 v = st[e0 + u / KB];
+                mbar_arrive_tx(&b_full[bs], C::B_RAW);
+                bulk_g2s(smem_u32(bops + bs * C::B_RAW), ttab + ((size_t)v.w * KB + u % KB) * C::B_RAW, C::B_RAW,
+                         &b_full[bs]);
+                issued = u + 1;
+            }
+            // copies still in flight when the pipeline stopped early land
+            // before the shared memory goes away (bounded waits)
+            if (*(volatile int *)abort_flag)
+                for (int u = max(0, issued - BS); u < issued; u++) mbar_wait(&b_full[u % BS], (uint32_t)((u / BS) & 1));
         }
     } else {
         // ---------------------------------------------------------- worker warps
@@ -367,17 +403,15 @@ __global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
         named_barrier_sync(1, 32 * C::NW);  // the first ring entries, for every worker
 
         int src = -1;
-        int issued = 0;  // lane 0: operator pieces copied (units)
-        // copy unit u into raw stage u % RS: this warp's 32 rows, its half of
-        // each row (64 B), and its slice of the raw operator rows
+        // copy unit u into raw stage u % RS: this warp's 32 rows and its half
+        // of each row (64 B)
         auto load_unit = [&](int u) {
             const int r = u % RS, vi = u / KB, kb = u % KB;
             if (kb == 0) {
                 src = ring[(vi % (2 * QV)) * 128 + row];
                 fetch(vi + QV);
             }
-            unsigned char *rs = raw + r * C::RAW;
-            const uint32_t araw = smem_u32(rs);
+            const uint32_t ar = smem_u32(araw + r * C::A_RAW);
             const int ch = 4 * half + (lane & 3);
 #pragma unroll
             for (int i = 0; i < 4; i++) {
@@ -385,17 +419,11 @@ __global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
                 const int sr = __shfl_sync(0xffffffffu, src, rr);
                 const int ro = ((warp & 3) << 5) + rr;
                 const float *g = mrow + ((size_t)(sr >= 0 ? sr : 0) * KP + kb * 32) + ch * 4;
-                cp_async16(araw + (uint32_t)ro * 128u + ((((uint32_t)ch) ^ ((uint32_t)ro & 7u)) << 4), g,
+                cp_async16(ar + (uint32_t)ro * 128u + ((((uint32_t)ch) ^ ((uint32_t)ro & 7u)) << 4), g,
                            sr >= 0 ? 16u : 0u);
             }
-            if (lane == 0) {
-                const int4 v = st[e0 + vi];
-                mbar_arrive_tx(&raw_full[r], C::BW * 128);
-                bulk_g2s(smem_u32(rs + C::A_RAW + warp * C::BW * 128),
-                         ttab + ((size_t)v.w * KB + kb) * C::B_RAW + (size_t)warp * C::BW * 128, C::BW * 128, &raw_full[r]);
-                issued = u + 1;
-            }
-            cp_async_arrive_noinc(&raw_full[r]);
+            if (kb == 0) __threadfence_block();  // a ring entry stored directly by fetch() is ordered before the arrival
+            cp_async_arrive_noinc(&a_full[r]);
         };
 
         auto drain = [&](int g) {
@@ -427,21 +455,20 @@ __global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
         };
 
         for (int u = 0; u < RS && u < nunits; u++) load_unit(u);
-        int drained = 0, consumed = 0;
+        int drained = 0;
         for (int u = 0; u < nunits; u++) {
             if (*(volatile int *)abort_flag) break;
             const int r = u % RS, c = u % CS;
-            bool ok = mbar_wait(&raw_full[r], (uint32_t)((u / RS) & 1));
+            bool ok = mbar_wait(&a_full[r], (uint32_t)((u / RS) & 1));
             if (ok && u >= CS) ok = mbar_wait(&cmp_free[c], (uint32_t)(((u - CS) / CS) & 1));
             if (!ok) {
                 atomicExch(abort_flag, 1);
                 break;
             }
-            consumed = u + 1;
             // split raw FP32 into TF32 (hi, lo), this thread's half of its row:
             // hi rounded to nearest, lo = a - hi (exact in FP32; the MMA reads
             // its leading 11 bits, an error below 2^-21 of a)
-            unsigned char *rs = raw + r * C::RAW;
+            unsigned char *rs = araw + r * C::A_RAW;
             unsigned char *cs = cmp + c * C::CMP;
 #pragma unroll
             for (int j = 0; j < 4; j++) {
@@ -458,16 +485,9 @@ __global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
             }
             fence_proxy_async();
             mbar_arrive(&cmp_full[c]);
-            // raw stage of unit u - 1 (its operator was read by MMA u - 1):
-            // refill with unit u - 1 + RS
-            if (u >= 1 && u - 1 + RS < nunits) {
-                if (!mbar_wait(&cmp_free[(u - 1) % CS], (uint32_t)(((u - 1) / CS) & 1))) {
-                    atomicExch(abort_flag, 1);
-                    break;
-                }
-                __syncwarp();
-                load_unit(u - 1 + RS);
-            }
+            // this warp has read its part of raw stage r: refill it with unit u + RS
+            __syncwarp();
+            if (u + RS < nunits) load_unit(u + RS);
             // drain group g - 1 once group g is well under way
             const int vi = u / KB;
             if ((u % KB) == KB - 1 && vi % C::GV == 2 && vi / C::GV >= 1 && drained < vi / C::GV) {
@@ -476,11 +496,7 @@ __global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
             }
         }
         cp_async_wait_all();
-        if (*(volatile int *)abort_flag) {
-            // the operator pieces still in flight (bounded waits)
-            if (lane == 0)
-                for (int u = consumed; u < issued; u++) mbar_wait(&raw_full[u % RS], (uint32_t)((u / RS) & 1));
-        } else {
+        if (!*(volatile int *)abort_flag) {
             while (drained < ngroups) {
                 drain(drained);
                 drained++;
