@@ -166,6 +166,47 @@ def p2p_traffic(interactions, n):
         return None
 
 
+def phase_rooflines(phase, st, N, p, peaks, nsm):
+    """Achieved rates of the phases other than P2P, from algorithmic bytes or
+    flops per phase (the minimal traffic each phase must move, FP32 storage):
+    HBM-bound phases against the measured copy bandwidth, M2L against the TF32
+    dense peak (half the measured BF16 peak, the nominal 1.1 : 2.25 ratio)."""
+    pp4 = 4 * p * p  # bytes of one expansion
+    nc, nl = st["ncells"], st["nleaves"]
+    by = {
+        # 8 LSD passes over (key 8 B, index 4 B), read and written, plus the
+        # gather of the sorted float4 particles (16 B in, 16 B out)
+        "build": 8 * 2 * 12 * N + 32 * N,
+        # particles in, leaf multipoles out
+        "p2m": 16 * N + nl * pp4,
+        # every non-root cell's multipole read once, every parent written once
+        "m2m": (nc - 1) * pp4 + (nc - nl) * pp4,
+        # every non-root cell's local expansion read, updated and written; its parent read
+        "l2l": 3 * (nc - 1) * pp4,
+        # particles and leaf local expansions in, double4 far field out
+        "l2p": 16 * N + nl * pp4 + 32 * N,
+        # far and near double4 and the permutation in, phi and grad (FP32) out
+        "combine": 64 * N + 4 * N + 16 * N,
+    }
+    ms = {"build": phase["ms_build"], "p2m": phase["ms_p2m"], "m2m": phase["ms_m2m"], "l2l": phase["ms_l2l"],
+          "l2p": phase["ms_l2p"], "combine": phase["ms_combine"]}
+    hbm = float(peaks.get("hbm_gbs", 6783.5))
+    out = {}
+    for k, b in by.items():
+        if ms[k] > 0:
+            gbs = b / (ms[k] / 1000.0) / 1e9
+            out[k] = {"bound": "hbm", "bytes": b, "ms": ms[k], "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                      "frac": gbs / hbm}
+    tf32 = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1919.0))) / 2.0
+    flops = 2.0 * p ** 4 * st["n_m2l_pairs"]
+    if phase["ms_m2l"] > 0:
+        tf = flops / (phase["ms_m2l"] / 1000.0) / 1e12
+        out["m2l"] = {"bound": "tensor", "flops": flops, "ms": phase["ms_m2l"], "achieved": tf, "peak": tf32,
+                      "unit": "TFLOP/s", "frac": tf / tf32,
+                      "note": "useful 2 p^4 flop per pair; the split-TF32 scheme issues 3 MMA passes of it"}
+    return out
+
+
 def run_e2e(a, x, q, N, ncrit, world, dist, dev):
     """Same metric through the C ABI with pinned host buffers: every step copies
     x and q to the device and phi and grad back."""
@@ -329,6 +370,7 @@ def main():
                 "peak_note": "FP32 FMA: %d SMs x 128 lanes x 2 flop x %.0f MHz (max SM clock); 20 flop per interaction"
                              % (nsm, sm_max),
                 "interactions": inter, "p2p_ms": p2p_avg}
+    phases_roof = phase_rooflines(phase, st1, N, a.p, peaks, nsm)
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -356,7 +398,8 @@ def main():
                                                                              "n_p2p_pairs", "n_m2l_pairs",
                                                                              "n_m2l_irregular", "n_interactions",
                                                                              "m2l_engine")},
-               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": ck}
+               "roofline": roofline, "phase_rooflines": phases_roof, "cpu_baseline": cpu, "e2e": e2e,
+               "gpu_launches": launches, "clocks": ck}
         print(json.dumps(out), flush=True)
     f.close()
     if dist:
