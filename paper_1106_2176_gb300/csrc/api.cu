@@ -78,7 +78,7 @@ void PinnedBuf::release()
 
 fmm_ctx::~fmm_ctx()
 {
-    fmm::DevBuf *bufs[] = {&st_dev, &rtab64, &rtab32, &ttab, &box, &x_in, &q_in, &keys, &keys2, &idx,
+    fmm::DevBuf *bufs[] = {&st_dev, &rtab64, &rtab32, &m2m_mat, &l2l_mat, &ttab, &box, &x_in, &q_in, &keys, &keys2, &idx, &inv, &pcell, &cgeo,
                            &idx2, &hist, &scan_tmp, &xs64, &xs32, &xs32lo, &c_level, &c_anchor, &c_begin, &c_end, &c_child,
                            &c_nchild, &c_parent, &c_xyz, &split_cnt, &split_off, &split_bnd, &leaves, &frontA,
                            &frontB, &p2p_pairs, &m2lx_pairs, &pair_keys, &pair_keys2, &pair_vals, &pair_vals2,

@@ -22,6 +22,7 @@
 //   L2P  phi = Re sum L~ conj(R(x^)) / w, grad from d_z R_n^m = R_{n-1}^m and
 //        (d_x + i d_y) R_n^m = -R_{n-1}^{m+1}, divided by w^2.
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 #include <map>
 #include <tuple>
@@ -391,6 +392,121 @@ __global__ void l2l_k(int p, int ls, int le, const int *__restrict__ parent, con
     if (l) Lc[im_idx(k, l)] += sc * si;
 }
 
+// M2M and L2L of the mixed path as dense maps: one warp per cell, lane i
+// owns output rows i, i + 32, ... (NR of them); the input expansion is staged
+// in shared memory and every lane reads the map column by column (coalesced).
+constexpr int MV_WARPS = 8;
+
+// M2M: one block per parent, warp w maps child w; the partial expansions are
+// added in child order, so the result does not depend on scheduling
+template <int NR>
+__global__ void __launch_bounds__(32 * MV_WARPS) m2m_mv_k(int PP, int ls, int le, const int *__restrict__ child,
+                                                         const int *__restrict__ nchild, const int4 *__restrict__ xyz,
+                                                         const float *__restrict__ mat, float *__restrict__ M)
+{
+    extern __shared__ float sm_mv[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int c = ls + blockIdx.x;
+    const int nc = nchild[c];
+    if (nc == 0) return;  // a leaf keeps its P2M expansion
+    float *sx = sm_mv + w * PP;                 // child expansion
+    float *part = sm_mv + MV_WARPS * PP;        // [child][PP] partial results
+    if (w < nc) {
+        const int ch = child[c] + w;
+        const float *T = mat + (size_t)child_octant(xyz[ch]) * PP * PP;
+        const float *Mc = M + (size_t)ch * PP;
+        for (int j = lane; j < PP; j += 32) sx[j] = Mc[j];
+        __syncwarp();
+        float acc[NR];
+#pragma unroll
+        for (int r = 0; r < NR; r++) acc[r] = 0.f;
+        for (int j = 0; j < PP; j++) {
+            const float xj = sx[j];
+            const float *col = T + (size_t)j * PP;
+#pragma unroll
+            for (int r = 0; r < NR; r++) {
+                const int i = lane + 32 * r;
+                if (i < PP) acc[r] = fmaf(col[i], xj, acc[r]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < NR; r++) {
+            const int i = lane + 32 * r;
+            if (i < PP) part[w * PP + i] = acc[r];
+        }
+    }
+    __syncthreads();
+    float *Mp = M + (size_t)c * PP;
+    for (int i = threadIdx.x; i < PP; i += 32 * MV_WARPS) {
+        float sum = 0.f;
+        for (int k = 0; k < nc; k++) sum += part[k * PP + i];
+        Mp[i] = sum;
+    }
+}
+
+template <int NR>
+__global__ void __launch_bounds__(32 * MV_WARPS) l2l_mv_k(int PP, int ls, int le, const int *__restrict__ parent,
+                                                         const int4 *__restrict__ xyz, const float *__restrict__ mat,
+                                                         float *__restrict__ L)
+{
+    extern __shared__ float sm_mv[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int c = ls + blockIdx.x * MV_WARPS + w;
+    if (c >= le) return;
+    float *sx = sm_mv + w * PP;
+    const float *T = mat + (size_t)child_octant(xyz[c]) * PP * PP;
+    const float *Lp = L + (size_t)parent[c] * PP;
+    for (int j = lane; j < PP; j += 32) sx[j] = Lp[j];
+    __syncwarp();
+    float acc[NR];
+#pragma unroll
+    for (int r = 0; r < NR; r++) acc[r] = 0.f;
+    for (int j = 0; j < PP; j++) {
+        const float xj = sx[j];
+        const float *col = T + (size_t)j * PP;
+#pragma unroll
+        for (int r = 0; r < NR; r++) {
+            const int i = lane + 32 * r;
+            if (i < PP) acc[r] = fmaf(col[i], xj, acc[r]);
+        }
+    }
+    float *Lc = L + (size_t)c * PP;
+#pragma unroll
+    for (int r = 0; r < NR; r++) {
+        const int i = lane + 32 * r;
+        if (i < PP) Lc[i] += acc[r];
+    }
+}
+
+static void m2m_mv(int PP, int ls, int le, const int *child, const int *nchild, const int4 *xyz, const float *mat,
+                   float *M, cudaStream_t s)
+{
+    const unsigned g = (unsigned)(le - ls);
+    const size_t sm = sizeof(float) * 2 * MV_WARPS * PP;
+    switch ((PP + 31) / 32) {
+#define FMM_MV_CASE(R) \
+    case R: m2m_mv_k<R><<<g, 32 * MV_WARPS, sm, s>>>(PP, ls, le, child, nchild, xyz, mat, M); break;
+        FMM_MV_CASE(1) FMM_MV_CASE(2) FMM_MV_CASE(3) FMM_MV_CASE(4) FMM_MV_CASE(5) FMM_MV_CASE(6) FMM_MV_CASE(7)
+        FMM_MV_CASE(8) FMM_MV_CASE(9) FMM_MV_CASE(10) FMM_MV_CASE(11) FMM_MV_CASE(12) FMM_MV_CASE(13)
+#undef FMM_MV_CASE
+    default: throw Error{FMM_EINVAL, "m2m: unsupported p"};
+    }
+}
+
+static void l2l_mv(int PP, int ls, int le, const int *parent, const int4 *xyz, const float *mat, float *L, cudaStream_t s)
+{
+    const unsigned g = nblk(le - ls, MV_WARPS);
+    const size_t sm = sizeof(float) * MV_WARPS * PP;
+    switch ((PP + 31) / 32) {
+#define FMM_MV_CASE(R) \
+    case R: l2l_mv_k<R><<<g, 32 * MV_WARPS, sm, s>>>(PP, ls, le, parent, xyz, mat, L); break;
+        FMM_MV_CASE(1) FMM_MV_CASE(2) FMM_MV_CASE(3) FMM_MV_CASE(4) FMM_MV_CASE(5) FMM_MV_CASE(6) FMM_MV_CASE(7)
+        FMM_MV_CASE(8) FMM_MV_CASE(9) FMM_MV_CASE(10) FMM_MV_CASE(11) FMM_MV_CASE(12) FMM_MV_CASE(13)
+#undef FMM_MV_CASE
+    default: throw Error{FMM_EINVAL, "l2l: unsupported p"};
+    }
+}
+
 // Column m (orders +m and -m) of I_n^m(u), n = m .. Q-1, written to full
 // complex storage sI[2 * (n*n + n +- m)]; computed in FP64 by one thread:
 // I_m^m = (2m-1)!! (x + iy)^m / r^(2m+1), then the three-term recurrence in n.
@@ -719,6 +835,106 @@ __global__ void __launch_bounds__(64) l2p_k(int p, const int *__restrict__ leave
     }
 }
 
+// geometric centre and inverse width of every cell (cell_geom), once per evaluation
+__global__ void cgeo_k(int nc, const int4 *__restrict__ xyz, const Box *__restrict__ box, double4_32a *__restrict__ g)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    double cen[3], w;
+    cell_geom(box, xyz[c], cen, w);
+    g[c] = make_double4_32a(cen[0], cen[1], cen[2], 1.0 / w);
+}
+
+// L2P with the order fixed at compile time: one thread per sorted particle,
+// the local expansion of its leaf read through the L1 cache (the particles of
+// a leaf are consecutive, so a warp reads one or two expansions). The same
+// sums as l2p_k: phi = Re sum L_n^m conj(R_n^m), d/dz from L_{n+1}^m and
+// (d_x - i d_y) from L_{n+1}^{m-1} and L_{n+1}^{m+1} (Sec. 2.1, L2P).
+template <int P, class P4>
+__global__ void __launch_bounds__(256) l2p_flat_k(int64_t n, const int *__restrict__ pcell,
+                                                  const double4_32a *__restrict__ cgeo, const P4 *__restrict__ xs,
+                                                  const float *__restrict__ L, double4_32a *__restrict__ far)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int c = pcell[j];
+    const double4_32a g = cgeo[c];
+    const double cen[3] = {g.x, g.y, g.z};
+    const double iw = g.w;
+    const double4_32a pt = rel_pt(xs, (int)j, cen);
+    const float x = (float)(pt.x * iw), y = (float)(pt.y * iw), z = (float)(pt.z * iw);
+    const float r2 = x * x + y * y + z * z;
+    const float *Lc = L + (size_t)c * (P * P);
+    auto ld = [&](int k) { return __ldg(Lc + k); };
+    float F = 0.f, Fz = 0.f, Gr = 0.f, Gi = 0.f;
+    float mre = 1.f, mim = 0.f;
+#pragma unroll
+    for (int m = 0; m < P; m++) {
+        if (m > 0) {
+            const float f = 1.f / (float)(2 * m);
+            const float a = (mre * x - mim * y) * f, b = (mre * y + mim * x) * f;
+            mre = a;
+            mim = b;
+        }
+        const float wm = m ? 2.f : 1.f;
+        float p2re = 0.f, p2im = 0.f, p1re = 0.f, p1im = 0.f;
+#pragma unroll
+        for (int nn = m; nn < P; nn++) {
+            float rre, rim;
+            if (nn == m) {
+                rre = mre;
+                rim = mim;
+            } else if (nn == m + 1) {
+                rre = z * mre;
+                rim = z * mim;
+            } else {
+                const float a = (float)(2 * nn - 1), b = 1.f / (float)((nn + m) * (nn - m));
+                rre = (a * z * p1re - r2 * p2re) * b;
+                rim = (a * z * p1im - r2 * p2im) * b;
+            }
+            p2re = p1re; p2im = p1im; p1re = rre; p1im = rim;
+            const float lr = ld(re_idx(nn, m)), li = m ? ld(im_idx(nn, m)) : 0.f;
+            F += wm * (lr * rre + li * rim);
+            if (nn + 1 < P) {
+                const float zr = ld(re_idx(nn + 1, m)), zi = m ? ld(im_idx(nn + 1, m)) : 0.f;
+                Fz += wm * (zr * rre + zi * rim);
+                float ar, ai;
+                if (m == 0) {
+                    ar = -ld(re_idx(nn + 1, 1));
+                    ai = ld(im_idx(nn + 1, 1));
+                } else {
+                    ar = ld(re_idx(nn + 1, m - 1));
+                    ai = (m - 1) ? ld(im_idx(nn + 1, m - 1)) : 0.f;
+                }
+                Gr -= ar * rre + ai * rim;
+                Gi -= ai * rre - ar * rim;
+                if (m >= 1) {
+                    const float br = ld(re_idx(nn + 1, m + 1)), bi = ld(im_idx(nn + 1, m + 1));
+                    Gr += br * rre + bi * rim;
+                    Gi -= bi * rre - br * rim;
+                }
+            }
+        }
+    }
+    const double iw2 = iw * iw;
+    far[j] = make_double4_32a((double)F * iw, (double)Gr * iw2, -(double)Gi * iw2, (double)Fz * iw2);
+}
+
+template <class P4>
+static bool l2p_flat_launch(int p, int64_t n, const int *pcell, const double4_32a *cgeo, const P4 *xs, const float *L,
+                            double4_32a *far, cudaStream_t s)
+{
+    const unsigned g = nblk(n, 256);
+    switch (p) {
+#define FMM_L2P_CASE(PV) \
+    case PV: l2p_flat_k<PV, P4><<<g, 256, 0, s>>>(n, pcell, cgeo, xs, L, far); return true;
+        FMM_L2P_CASE(2) FMM_L2P_CASE(3) FMM_L2P_CASE(4) FMM_L2P_CASE(5) FMM_L2P_CASE(6)
+        FMM_L2P_CASE(7) FMM_L2P_CASE(8) FMM_L2P_CASE(9) FMM_L2P_CASE(10)
+#undef FMM_L2P_CASE
+    default: return false;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // host: tables and orchestration
 // ---------------------------------------------------------------------------
@@ -811,6 +1027,79 @@ void operators_init(fmm_ctx *h)
     }
     std::vector<float> r32(r64.size());
     for (size_t i = 0; i < r64.size(); i++) r32[i] = (float)r64[i];
+
+    // M2M and L2L as real p^2 x p^2 maps of the packed expansions, one per child
+    // octant o (the same sums as m2m_k and l2l_k, in FP64, applied to each unit
+    // vector of the packed basis): column j = the map of e_j; stored [o][j][i].
+    std::vector<float> mm((size_t)8 * PP * PP), ll((size_t)8 * PP * PP);
+    std::vector<double> e(PP), out(PP);
+    auto get = [&](int n, int m, double &re, double &im) {  // complex coefficient (n, m) of the packed e
+        const int a = m < 0 ? -m : m;
+        re = e[re_idx(n, a)];
+        im = a ? e[im_idx(n, a)] : 0.0;
+        if (m < 0) {
+            im = -im;
+            if (a & 1) {
+                re = -re;
+                im = -im;
+            }
+        }
+    };
+    for (int o = 0; o < 8; o++) {
+        const double *R = r64.data() + (size_t)o * 2 * PP;
+        for (int j0 = 0; j0 < PP; j0++) {
+            std::fill(e.begin(), e.end(), 0.0);
+            e[j0] = 1.0;
+            // M2M: child (offset t_o from the parent centre, in parent widths) -> parent
+            std::fill(out.begin(), out.end(), 0.0);
+            for (int n = 0; n < p; n++)
+                for (int m = 0; m <= n; m++) {
+                    double sr = 0, si = 0;
+                    for (int k = 0; k <= n; k++) {
+                        const int j = n - k;
+                        const double sc = std::ldexp(1.0, -j);
+                        for (int l = -k; l <= k; l++) {
+                            const int mu = m - l;
+                            if (mu > j || mu < -j) continue;
+                            const double rr = R[2 * full(k, l)], ri = -R[2 * full(k, l) + 1];
+                            double mr, mi;
+                            get(j, mu, mr, mi);
+                            sr += sc * (rr * mr - ri * mi);
+                            si += sc * (rr * mi + ri * mr);
+                        }
+                    }
+                    out[re_idx(n, m)] = sr;
+                    if (m) out[im_idx(n, m)] = si;
+                }
+            for (int i = 0; i < PP; i++) mm[((size_t)o * PP + j0) * PP + i] = (float)out[i];
+            // L2L: parent -> child at offset t_o
+            std::fill(out.begin(), out.end(), 0.0);
+            for (int k = 0; k < p; k++)
+                for (int l = 0; l <= k; l++) {
+                    double sr = 0, si = 0;
+                    for (int n = k; n < p; n++) {
+                        const int d = n - k;
+                        for (int m = -n; m <= n; m++) {
+                            const int mu = m - l;
+                            if (mu > d || mu < -d) continue;
+                            double lr, li;
+                            get(n, m, lr, li);
+                            const double rr = R[2 * full(d, mu)], ri = -R[2 * full(d, mu) + 1];
+                            sr += lr * rr - li * ri;
+                            si += lr * ri + li * rr;
+                        }
+                    }
+                    const double sc = std::ldexp(1.0, -(k + 1));
+                    out[re_idx(k, l)] = sc * sr;
+                    if (l) out[im_idx(k, l)] = sc * si;
+                }
+            for (int i = 0; i < PP; i++) ll[((size_t)o * PP + j0) * PP + i] = (float)out[i];
+        }
+    }
+    h->m2m_mat.ensure(sizeof(float) * mm.size());
+    h->l2l_mat.ensure(sizeof(float) * ll.size());
+    FMM_CUDA_TRY(cudaMemcpy(h->m2m_mat.p, mm.data(), sizeof(float) * mm.size(), cudaMemcpyHostToDevice));
+    FMM_CUDA_TRY(cudaMemcpy(h->l2l_mat.p, ll.data(), sizeof(float) * ll.size(), cudaMemcpyHostToDevice));
     h->rtab64.ensure(sizeof(double) * r64.size());
     h->rtab32.ensure(sizeof(float) * r32.size());
     FMM_CUDA_TRY(cudaMemcpy(h->rtab64.p, r64.data(), sizeof(double) * r64.size(), cudaMemcpyHostToDevice));
@@ -856,8 +1145,12 @@ static void far_field_t(fmm_ctx *h, const P4 *xs, const T *rtab)
         const int ls = h->lvl_start[l], le = h->lvl_start[l + 1];
         const int64_t nt = (int64_t)(le - ls) * ntri;
         if (nt == 0) continue;
-        m2m_k<T><<<nblk(nt, 128), 128, 0, s>>>(p, ls, le, h->c_child.as<int>(), h->c_nchild.as<int>(), h->c_xyz.as<int4>(),
-                                               rtab, M);
+        if constexpr (std::is_same<T, float>::value)
+            m2m_mv(PP, ls, le, h->c_child.as<int>(), h->c_nchild.as<int>(), h->c_xyz.as<int4>(), h->m2m_mat.as<float>(),
+                   reinterpret_cast<float *>(M), s);
+        else
+            m2m_k<T><<<nblk(nt, 128), 128, 0, s>>>(p, ls, le, h->c_child.as<int>(), h->c_nchild.as<int>(),
+                                                   h->c_xyz.as<int4>(), rtab, M);
         count_launch(h);
     }
     check_launch("m2m");
@@ -903,15 +1196,31 @@ static void far_field_t(fmm_ctx *h, const P4 *xs, const T *rtab)
         const int ls = h->lvl_start[l + 1], le = h->lvl_start[l + 2];
         const int64_t nt = (int64_t)(le - ls) * ntri;
         if (nt == 0) continue;
-        l2l_k<T><<<nblk(nt, 128), 128, 0, s>>>(p, ls, le, h->c_parent.as<int>(), h->c_xyz.as<int4>(), rtab, L);
+        if constexpr (std::is_same<T, float>::value)
+            l2l_mv(PP, ls, le, h->c_parent.as<int>(), h->c_xyz.as<int4>(), h->l2l_mat.as<float>(),
+                   reinterpret_cast<float *>(L), s);
+        else
+            l2l_k<T><<<nblk(nt, 128), 128, 0, s>>>(p, ls, le, h->c_parent.as<int>(), h->c_xyz.as<int4>(), rtab, L);
         count_launch(h);
     }
     check_launch("l2l");
     // L2P
     FMM_CUDA_TRY(cudaEventRecord(ev[6], s));
     h->far.ensure(sizeof(double4_32a) * (size_t)h->n);
-    l2p_k<T, P4><<<h->nleaves, 64, sizeof(T) * PP, s>>>(p, h->leaves.as<int>(), h->c_begin.as<int>(), h->c_end.as<int>(),
-                                                        h->c_xyz.as<int4>(), box, xs, L, h->far.as<double4_32a>());
+    bool l2p_done = false;
+    if constexpr (std::is_same<T, float>::value) {
+        if (h->n > 0 && p >= 2 && p <= P2M_WARP_MAXP) {
+            h->cgeo.ensure(sizeof(double4_32a) * (size_t)nc);
+            cgeo_k<<<nblk(nc, 256), 256, 0, s>>>(nc, h->c_xyz.as<int4>(), box, h->cgeo.as<double4_32a>());
+            count_launch(h);
+            l2p_done = l2p_flat_launch<P4>(p, h->n, h->pcell.as<int>(), h->cgeo.as<double4_32a>(), xs,
+                                           reinterpret_cast<const float *>(L), h->far.as<double4_32a>(), s);
+        }
+    }
+    if (!l2p_done)
+        l2p_k<T, P4><<<h->nleaves, 64, sizeof(T) * PP, s>>>(p, h->leaves.as<int>(), h->c_begin.as<int>(),
+                                                            h->c_end.as<int>(), h->c_xyz.as<int4>(), box, xs, L,
+                                                            h->far.as<double4_32a>());
     count_launch(h);
     check_launch("l2p");
     FMM_CUDA_TRY(cudaEventRecord(ev[7], s));

@@ -152,6 +152,7 @@ struct fmm_ctx {
     fmm::DevBuf st_dev;         // int4 per entry
     int st_R = 0;               // offsets |v_k| <= st_R are in the stencil
     fmm::DevBuf rtab64, rtab32; // R_n^m(t_o), 8 child offsets, full complex storage of degree < p
+    fmm::DevBuf m2m_mat, l2l_mat; // FP32 p^2 x p^2 real maps of M2M and L2L per child octant, [o][in][out]
     fmm::DevBuf ttab;           // tensor-core M2L operators (split TF32 images), per vector
     size_t ttab_stride = 0;     // bytes per vector in ttab
     int ttab_nv = -1;           // stencil vectors the operator images were made for
@@ -161,6 +162,9 @@ struct fmm_ctx {
     fmm::DevBuf box;
     fmm::DevBuf x_in, q_in;             // staging of host inputs
     fmm::DevBuf keys, keys2, idx, idx2; // Morton keys and permutation (radix sort ping-pong)
+    fmm::DevBuf inv;                    // inverse permutation: sorted position of each input particle
+    fmm::DevBuf pcell;                  // leaf cell of each sorted particle
+    fmm::DevBuf cgeo;                   // per cell: geometric centre and 1 / width (double4)
     fmm::DevBuf hist, scan_tmp;
     fmm::DevBuf xs64, xs32, xs32lo;
     fmm::DevBuf c_level, c_anchor, c_begin, c_end, c_child, c_nchild, c_parent, c_xyz;

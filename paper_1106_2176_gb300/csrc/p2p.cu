@@ -522,12 +522,14 @@ void near_field(fmm_ctx *h, cudaStream_t s)
 // far + near, back to the caller's particle order and element type
 // ---------------------------------------------------------------------------
 template <class OT>
-__global__ void combine_k(const double4_32a *__restrict__ far, const double4_32a *__restrict__ near, const int *__restrict__ perm,
+__global__ void combine_k(const double4_32a *__restrict__ far, const double4_32a *__restrict__ near, const int *__restrict__ inv,
                           int64_t n, OT *__restrict__ phi, OT *__restrict__ grad)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int64_t j = perm[i];
+    // one thread per particle in the caller's order: its sorted position is
+    // read, the two 32-byte records gathered, and the outputs written in order
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int64_t i = inv[j];
     const double4_32a a = far[i], b = near[i];
     phi[j] = (OT)(a.x + b.x);
     if (grad) {
@@ -541,10 +543,10 @@ void combine_unsort(fmm_ctx *h, void *phi, void *grad)
 {
     if (h->dtype == FMM_F64)
         combine_k<double><<<nblk(h->n, 256), 256, 0, h->stream>>>(h->far.as<double4_32a>(), h->near.as<double4_32a>(),
-                                                                  h->idx.as<int>(), h->n, (double *)phi, (double *)grad);
+                                                                  h->inv.as<int>(), h->n, (double *)phi, (double *)grad);
     else
         combine_k<float><<<nblk(h->n, 256), 256, 0, h->stream>>>(h->far.as<double4_32a>(), h->near.as<double4_32a>(),
-                                                                 h->idx.as<int>(), h->n, (float *)phi, (float *)grad);
+                                                                 h->inv.as<int>(), h->n, (float *)phi, (float *)grad);
     count_launch(h);
     check_launch("combine");
 }

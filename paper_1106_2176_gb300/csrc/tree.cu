@@ -403,11 +403,13 @@ void morton_sort_into(const void *x, int64_t n64, int dt, uint64_t *keys, int *p
 
 template <class T>
 __global__ void gather_k(const T *__restrict__ x, const T *__restrict__ q, const int *__restrict__ idx, int64_t n,
-                         double4_32a *__restrict__ xs64, float4 *__restrict__ xs32, float4 *__restrict__ xs32lo)
+                         double4_32a *__restrict__ xs64, float4 *__restrict__ xs32, float4 *__restrict__ xs32lo,
+                         int *__restrict__ inv)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int j = idx[i];
+    inv[j] = (int)i;
     double a = (double)x[3 * (int64_t)j], b = (double)x[3 * (int64_t)j + 1], c = (double)x[3 * (int64_t)j + 2];
     double d = (double)q[j];
     if (xs64) xs64[i] = make_double4_32a(a, b, c, d);
@@ -628,7 +630,9 @@ __global__ void pair_rows_k(const uint64_t *__restrict__ keys, int64_t np, int b
     if (i >= np) return;
     uint64_t k = keys[i];
     src[i] = (int)(k & ((1ull << bs) - 1));
-    atomicAdd(&rowcnt[(int)(k >> bs)], 1u);
+    const int row = (int)(k >> bs);
+    const unsigned same = __match_any_sync(__activemask(), row);
+    if ((int)(threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(&rowcnt[row], (unsigned)__popc(same));
 }
 
 __global__ void interactions_k(const int *__restrict__ ptr, const int *__restrict__ src, const int *__restrict__ begin,
@@ -671,6 +675,64 @@ __global__ void p2p_runs_k(int nleaves, const int *__restrict__ leaves, const in
     nrun[A] = o - ptr[A];
 }
 
+// (target, source) pairs -> CSR rows without a global sort: rows are counted
+// and filled with warp-aggregated atomics, then each row is put in ascending
+// source order by exact ranks (sources of a row are distinct).
+__global__ void row_count_k(const int2 *__restrict__ pr, int64_t np, unsigned *__restrict__ cnt)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    const int a = pr[i].x;
+    const unsigned act = __activemask();
+    const unsigned same = __match_any_sync(act, a);
+    if ((int)(threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(&cnt[a], (unsigned)__popc(same));
+}
+
+__global__ void row_fill_k(const int2 *__restrict__ pr, int64_t np, const int *__restrict__ ptr, unsigned *__restrict__ cur,
+                           int *__restrict__ src)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    const int2 v = pr[i];
+    const unsigned act = __activemask();
+    const unsigned same = __match_any_sync(act, v.x);
+    const int lane = threadIdx.x & 31, leader = __ffs(same) - 1;
+    unsigned base = 0;
+    if (lane == leader) base = atomicAdd(&cur[v.x], (unsigned)__popc(same));
+    base = __shfl_sync(same, base, leader);
+    const unsigned rank = __popc(same & ((1u << lane) - 1));
+    src[ptr[v.x] + base + rank] = v.y;
+}
+
+__global__ void row_max_k(int nc, const unsigned *__restrict__ cnt, unsigned *__restrict__ mx)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned v = c < nc ? cnt[c] : 0u;
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0 && v) atomicMax(mx, v);
+}
+
+constexpr int ROW_SORT_WARPS = 8, ROW_SORT_CAP = 1024;
+
+__global__ void __launch_bounds__(32 * ROW_SORT_WARPS) row_sort_k(int nc, const int *__restrict__ ptr, int *__restrict__ src)
+{
+    __shared__ int sh[ROW_SORT_WARPS][ROW_SORT_CAP];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int r = blockIdx.x * ROW_SORT_WARPS + w;
+    if (r >= nc) return;
+    const int b = ptr[r], len = ptr[r + 1] - b;
+    if (len <= 1 || len > ROW_SORT_CAP) return;
+    int *row = sh[w];
+    for (int k = lane; k < len; k += 32) row[k] = src[b + k];
+    __syncwarp();
+    for (int k = lane; k < len; k += 32) {
+        const int e = row[k];
+        int rank = 0;
+        for (int t = 0; t < len; t++) rank += row[t] < e;
+        src[b + rank] = e;
+    }
+}
+
 static int bits_for(int64_t v)
 {
     int b = 1;
@@ -687,6 +749,28 @@ static void pairs_to_csr(fmm_ctx *h, const int2 *pairs, int64_t np, DevBuf &ptr,
     h->row_cnt.ensure(sizeof(unsigned) * (size_t)(nc + 1));
     FMM_CUDA_TRY(cudaMemsetAsync(h->row_cnt.p, 0, sizeof(unsigned) * (size_t)(nc + 1), s));
     if (np > 0) {
+        row_count_k<<<nblocks(np, 256), 256, 0, s>>>(pairs, np, h->row_cnt.as<unsigned>());
+        count_launch(h);
+        // longest row: rows that fit the per-warp sort are filled and ranked
+        // in place, otherwise the pairs go through a global sort
+        unsigned *dmax = reinterpret_cast<unsigned *>(h->counters.as<char>() + sizeof(TravCounters) + 32);
+        FMM_CUDA_TRY(cudaMemsetAsync(dmax, 0, sizeof(unsigned), s));
+        row_max_k<<<nblocks(nc, 256), 256, 0, s>>>(nc, h->row_cnt.as<unsigned>(), dmax);
+        count_launch(h);
+        unsigned *hp = h->hpin.as<unsigned>();
+        FMM_CUDA_TRY(cudaMemcpyAsync(hp, dmax, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+        FMM_CUDA_TRY(cudaStreamSynchronize(s));
+        if (*hp <= (unsigned)ROW_SORT_CAP) {
+            scan_exclusive_u32(h, h->row_cnt.as<unsigned>(), reinterpret_cast<unsigned *>(ptr.as<int>()), nc + 1, nullptr, s);
+            FMM_CUDA_TRY(cudaMemsetAsync(h->row_cnt.p, 0, sizeof(unsigned) * (size_t)(nc + 1), s));
+            row_fill_k<<<nblocks(np, 256), 256, 0, s>>>(pairs, np, ptr.as<int>(), h->row_cnt.as<unsigned>(), src.as<int>());
+            count_launch(h);
+            row_sort_k<<<nblocks(nc, ROW_SORT_WARPS), 32 * ROW_SORT_WARPS, 0, s>>>(nc, ptr.as<int>(), src.as<int>());
+            count_launch(h);
+            check_launch("pairs to csr");
+            return;
+        }
+        FMM_CUDA_TRY(cudaMemsetAsync(h->row_cnt.p, 0, sizeof(unsigned) * (size_t)(nc + 1), s));
         const int bs = bits_for(nc - 1);
         h->pair_keys.ensure(sizeof(uint64_t) * (size_t)np);
         h->pair_keys2.ensure(sizeof(uint64_t) * (size_t)np);
@@ -778,6 +862,16 @@ __global__ void leaves_write_k(int nc, const int *__restrict__ nchild, const uns
     if (c < nc && nchild[c] == 0) leaves[off[c]] = c;
 }
 
+// leaf cell of every sorted particle: one warp per cell, leaves write their range
+__global__ void pcell_k(int nc, const int *__restrict__ nchild, const int *__restrict__ begin,
+                        const int *__restrict__ end, int *__restrict__ pcell)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = (int)(t >> 5), lane = (int)(t & 31);
+    if (c >= nc || nchild[c] != 0) return;
+    for (int j = begin[c] + lane; j < end[c]; j += 32) pcell[j] = c;
+}
+
 // ---------------------------------------------------------------------------
 // host orchestration
 // ---------------------------------------------------------------------------
@@ -828,12 +922,13 @@ void tree_build(fmm_ctx *h, const void *x, const void *q, int64_t n, int dt)
         h->xs32lo.ensure(sizeof(float4) * n);
         xs32lo = h->xs32lo.as<float4>();
     }
+    h->inv.ensure(sizeof(int) * n);
     if (dt == FMM_F64)
         gather_k<double><<<nblocks(n, TB), TB, 0, s>>>((const double *)x, (const double *)q, h->idx.as<int>(), n, xs64, xs32,
-                                                       xs32lo);
+                                                       xs32lo, h->inv.as<int>());
     else
         gather_k<float><<<nblocks(n, TB), TB, 0, s>>>((const float *)x, (const float *)q, h->idx.as<int>(), n, xs64, xs32,
-                                                      xs32lo);
+                                                      xs32lo, h->inv.as<int>());
     count_launch(h);
     check_launch("gather");
 
@@ -914,6 +1009,10 @@ void tree_build(fmm_ctx *h, const void *x, const void *q, int64_t n, int dt)
         scan_exclusive_u32(h, h->split_cnt.as<unsigned>(), h->split_off.as<unsigned>(), ncells, tot, s);
         leaves_write_k<<<nblocks(ncells, TB), TB, 0, s>>>(ncells, h->c_nchild.as<int>(), h->split_off.as<unsigned>(),
                                                           h->leaves.as<int>());
+        count_launch(h);
+        h->pcell.ensure(sizeof(int) * (size_t)std::max<int64_t>(n, 1));
+        pcell_k<<<nblocks((int64_t)ncells * 32, TB), TB, 0, s>>>(ncells, h->c_nchild.as<int>(), h->c_begin.as<int>(),
+                                                               h->c_end.as<int>(), h->pcell.as<int>());
         count_launch(h);
         // lattice extent of the cells of every level: no same-level pair is
         // farther apart, which bounds the M2L stencil on deep adaptive trees
