@@ -516,6 +516,17 @@ __device__ __forceinline__ bool mac_accept(int4 a, int4 b, double c)
     return lhs < rhs;
 }
 
+// The same test for two cells of one level: with W_A = W_B = W both sides
+// carry the exact factor 4 W^2, so it reduces to 3 < fl(theta^2 |v|^2), v the
+// offset in cell units, and by monotone rounding to |v|^2 >= K0 with K0 the
+// first integer that passes (computed on the host with the same FP64 multiply).
+__device__ __forceinline__ bool mac_accept_same(int4 a, int4 b, long long K0)
+{
+    const int sh = FMM_MAXLEVEL - a.w;
+    const long long vx = (b.x - a.x) >> sh, vy = (b.y - a.y) >> sh, vz = (b.z - a.z) >> sh;
+    return vx * vx + vy * vy + vz * vz >= K0;
+}
+
 // warp-aggregated reservation of `cnt` slots in a global counter
 __device__ __forceinline__ unsigned long long warp_reserve(unsigned long long *ctr, unsigned cnt)
 {
@@ -564,6 +575,7 @@ __global__ void extent_k(int nc, const int4 *__restrict__ xyz, int *__restrict__
 // registers and written after one warp-aggregated reservation per list.
 __global__ void __launch_bounds__(256) expand_k(const int2 *__restrict__ F, unsigned nF, const int4 *__restrict__ xyz,
                                                 const int *__restrict__ child, const int *__restrict__ nchild, double cm,
+                                                long long K0,
                                                 int2 *__restrict__ p2p, unsigned long long cap_p2p,
                                                 int2 *__restrict__ m2lx, unsigned long long cap_m2lx,
                                                 int2 *__restrict__ next, unsigned long long cap_next,
@@ -593,7 +605,7 @@ __global__ void __launch_bounds__(256) expand_k(const int2 *__restrict__ F, unsi
         for (int k = 0; k < nb; k++) {
             const int b = b0 + k;
             const int4 xb = xyz[b];
-            if (mac_accept(xa, xb, cm)) {
+            if (xa.w == xb.w ? mac_accept_same(xa, xb, K0) : mac_accept(xa, xb, cm)) {
                 if (xa.w == xb.w) cI++;
                 else mX |= 1u << k;
             } else if (leafa && nchild[b] == 0) mP |= 1u << k;
@@ -1037,6 +1049,9 @@ void tree_build(fmm_ctx *h, const void *x, const void *q, int64_t n, int dt)
 
     // 5. dual traversal
     stencil_update(h);
+    long long K0 = (long long)std::ceil(3.0 / h->cmac);
+    while (K0 > 0 && 3.0 < h->cmac * (double)(K0 - 1)) K0--;
+    while (!(3.0 < h->cmac * (double)K0)) K0++;
     {
         // the near-field stencil size bounds the P2P list of a leaf in a uniform tree
         const size_t per = (size_t)h->p2p_cap_hint + 8;
@@ -1074,7 +1089,7 @@ void tree_build(fmm_ctx *h, const void *x, const void *q, int64_t n, int dt)
                 FMM_CUDA_TRY(cudaMemcpyAsync(dc, hp, sizeof(TravCounters), cudaMemcpyHostToDevice, s));
                 size_t cn = h->frontB.cap / sizeof(int2);
                 expand_k<<<nblocks(nF * 8, 256), 256, 0, s>>>(h->frontA.as<int2>(), (unsigned)nF, h->c_xyz.as<int4>(),
-                                                          h->c_child.as<int>(), h->c_nchild.as<int>(), h->cmac,
+                                                          h->c_child.as<int>(), h->c_nchild.as<int>(), h->cmac, K0,
                                                           h->p2p_pairs.as<int2>(), cap_p2p, h->m2lx_pairs.as<int2>(),
                                                           cap_m2lx, h->frontB.as<int2>(), cn, dc);
                 count_launch(h);
