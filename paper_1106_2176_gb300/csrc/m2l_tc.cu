@@ -16,18 +16,20 @@
 // the accumulator is drained into per-thread FP32 (hi, lo) TwoSum registers;
 // two TMEM buffers alternate so the drain overlaps the next MMAs.
 //
-// Per CTA (320 threads: 8 worker warps, 1 MMA warp, 1 operator warp), for
-// every unit (v, k-block) of 32 coefficients:
-//   - worker warp w copies, with cp.async, half of each of 32 target rows'
-//     raw FP32 multipole block (source found by a lattice lookup fetched QV
-//     vectors ahead into a shared ring; zero fill if the cell is absent) into
-//     a 128B-swizzled stage of the A ring;
+// Per CTA (320 threads: two groups of 4 worker warps, 1 MMA warp, 1 operator
+// warp), for every unit (v, k-block) of 32 coefficients, taken by the group
+// u % 2:
+//   - each thread of the group copies, with cp.async, its target row's raw
+//     FP32 multipole block (source found by a lattice lookup fetched ahead into
+//     the thread's ring; zero fill if the cell is absent) into a 128B-swizzled
+//     stage of the group's A ring;
 //   - the operator warp bulk-copies the pre-split, pre-swizzled [T_hi ; T_lo]
-//     operator block into a stage of the operator ring;
-//   - once its A stage is full, each worker splits its part into TF32 hi and
-//     lo (lo = a - hi) in a compute stage and refills the A stage;
-//   - one thread of the MMA warp issues the tcgen05.mma of the compute stage
-//     and the operator stage and commits to their "free" mbarriers.
+//     operator block into the unit's compute stage;
+//   - once its A stage is full, each thread splits its row into TF32 hi and lo
+//     (lo = a - hi), stores both in the compute stage's tensor-memory columns
+//     and refills its A stage;
+//   - one thread of the MMA warp issues the tcgen05.mma (A from tensor memory,
+//     the operator from shared memory) and commits to the stage's mbarrier.
 // Every wait is bounded; on a timeout the kernel records an error code and
 // leaves after its copies have landed and its TMEM is released.
 #include <algorithm>
@@ -39,6 +41,9 @@
 namespace fmm {
 
 static inline unsigned nblk(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+// source index of an absent cell, copied like a lattice-map entry
+__device__ int g_no_cell = -1;
 
 // ---------------------------------------------------------------------------
 // PTX wrappers
@@ -76,6 +81,30 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity)
         if (ok) return true;
     }
     return false;
+}
+
+// bounded wait for two (barrier, parity) pairs at once (bit k of `mask`
+// selects pair k); their tests overlap instead of running back to back, and a
+// waiting thread may be suspended instead of spinning on the issue slots
+__device__ __forceinline__ bool mbar_wait2(uint32_t mask, uint64_t *b0, uint32_t p0, uint64_t *b1, uint32_t p1)
+{
+    const uint32_t a0 = smem_u32(b0), a1 = smem_u32(b1);
+    for (int it = 0; it < (1 << 20) && mask; it++) {
+        uint32_t ok0 = 1, ok1 = 1;
+        if (mask & 1u)
+            asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                         : "=r"(ok0)
+                         : "r"(a0), "r"(p0)
+                         : "memory");
+        if (mask & 2u)
+            asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                         : "=r"(ok1)
+                         : "r"(a1), "r"(p1)
+                         : "memory");
+        if (ok0) mask &= ~1u;
+        if (ok1) mask &= ~2u;
+    }
+    return mask == 0;
 }
 
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t src_bytes)
@@ -129,6 +158,29 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, 
         "l"(a), "l"(b), "r"(idesc), "r"(acc)
         : "memory");
 }
+
+// the same with A in tensor memory (atmem: lane 0 and the first of its K columns)
+__device__ __forceinline__ void mma_tf32_ta(uint32_t tmem, uint32_t atmem, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(tmem),
+        "r"(atmem), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+// 16 consecutive TMEM columns of this warp's 32 lanes (one row per thread)
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float *v)
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
+        "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+        "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+        "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+        "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void mma_commit(uint64_t *bar)
 {
@@ -190,35 +242,46 @@ __device__ __forceinline__ void cp_async_arrive_noinc(uint64_t *bar)
 // ---------------------------------------------------------------------------
 // tile geometry
 // ---------------------------------------------------------------------------
-// Warp roles: warps 0-7 (256 threads: target row r = tid % 128 and half
-// h = tid / 128 of the coefficients) gather, split and drain; warp 8 issues
-// the MMAs; warp 9 copies the operator blocks. Three rings of stages:
-//   A raw (RS): the gathered FP32 multipoles of a unit, 128 B per row and
-//     k-block. A worker warp fills and reads only its own 32 rows x half, so it
-//     refills a stage right after its own split of it, with no MMA wait.
-//   operator (BS): the pre-split [T_hi ; T_lo] block of a unit, one bulk copy,
-//     read by the MMAs where it lands and freed by their commit.
-//   compute (CS): A_hi, A_lo after the split, freed by the MMA commit.
+// Warp roles: warps 0-7 form two groups of four (group g = warps 4g .. 4g+3,
+// thread row r = tid % 128, in its warp's TMEM lane quarter); group g takes
+// the units u with u % 2 == g, so the latency of one group's hand-offs is
+// hidden behind the other's. Warp 8 issues the MMAs; warp 9 copies the
+// operator blocks.
+//   A raw rings (RSG stages per group, shared memory): the gathered FP32
+//     multipoles of a unit, 128 B per row, 128B-swizzled. A thread copies and
+//     reads only its own row, so it refills a stage right after its split.
+//   compute stages (CS): A_hi, A_lo in tensor memory (written by the unit's
+//     group with tcgen05.st, read by the MMA as its A operand) and the operator
+//     block in shared memory (one bulk copy). One MMA commit frees both.
+// Tensor memory: AC accumulator buffers of 2 NP columns (main | correction)
+// followed by the CS A stages of 64 columns (hi 32 | lo 32). Thread (r, g)
+// drains output columns [g HN, (g + 1) HN) of row r.
 template <int NP, int KB>
 struct TcCfg {
     static constexpr int M = 128;                  // target rows per tile
     static constexpr int NW = 8;                   // worker warps
+    static constexpr int NG = 2;                   // worker groups
     static constexpr int MMA_WARP = NW, B_WARP = NW + 1;
     static constexpr int NT = NW * 32 + 64;        // threads (workers, MMA warp, operator warp)
     static constexpr int A_RAW = M * 128;          // raw A k-block (FP32, swizzled)
     static constexpr int B_RAW = 2 * NP * 128;     // [T_hi ; T_lo] k-block (TF32 pair, swizzled)
-    static constexpr int CMP = 2 * A_RAW;          // A_hi, A_lo
-    static constexpr int QV = 8;                   // lookahead of the source lookups (vectors)
-    static constexpr int RING = 2 * QV * M * 4;    // lookup ring
-    static constexpr int CS = 3;                   // compute stages
-    static constexpr int BUDGET = 220 * 1024 - RING - 512 - 1024 - CS * CMP;
-    static constexpr int BS = BUDGET >= 4 * B_RAW + 3 * A_RAW ? 4 : (BUDGET >= 3 * B_RAW + 2 * A_RAW ? 3 : 2);
-    static constexpr int RS = BUDGET >= BS * B_RAW + 3 * A_RAW ? 3 : 2;
-    static constexpr int SMEM = RS * A_RAW + BS * B_RAW + CS * CMP + RING + 512 + 1024;
-    static_assert(SMEM <= 227 * 1024, "shared memory of one CTA");
-    static constexpr int TCOLS = 4 * NP <= 32 ? 32 : (4 * NP <= 64 ? 64 : (4 * NP <= 128 ? 128 : (4 * NP <= 256 ? 256 : 512)));
+    static constexpr int ACOLS = 64;               // TMEM columns of one A stage (hi, lo)
+    static constexpr int AC = 4 * NP + 2 * ACOLS <= 512 ? 2 : 1;  // accumulator buffers
+    static constexpr int CS = AC == 2 ? (4 * NP + 4 * ACOLS <= 512 ? 4 : 2)
+                                      : ((512 - 2 * NP) / ACOLS >= 4 ? 4 : (512 - 2 * NP) / ACOLS);
+    static constexpr int ACC_COLS = AC * 2 * NP;
+    static constexpr int TCOLS = 512;
+    static constexpr int QU = 8;                   // lookahead of the source lookups (units of the group)
+    static constexpr int RINGU = 2 * QU;
+    static constexpr int RING = NG * RINGU * M * 4;
+    static constexpr int BUDGET = 220 * 1024 - RING - 512 - 1024 - CS * B_RAW;
+    static constexpr int RSG = BUDGET / (NG * A_RAW) >= 3 ? 3 : BUDGET / (NG * A_RAW);  // raw stages per group
+    static constexpr int SMEM = NG * RSG * A_RAW + CS * B_RAW + RING + 512 + 1024;
+    static_assert(RSG >= 2 && RSG <= 3 && CS >= 2 && QU >= RSG && ACC_COLS + CS * ACOLS <= TCOLS && SMEM <= 227 * 1024,
+                  "stage budget");
     static constexpr int GV = 8;                   // vectors per accumulator drain
-    static constexpr int HN = NP / 2;              // coefficients per thread
+    static constexpr int HN = NP / 2;              // output coefficients per thread
+    static constexpr int DRAIN_AT = AC == 2 ? 2 : 0;  // vectors into group gg + 1 at which group gg is drained
 };
 
 // Zero-padded copy of the scaled multipoles: out[c][KB * 32] (only when p^2 is
@@ -240,29 +303,27 @@ __global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
              int *__restrict__ err)
 {
     using C = TcCfg<NP, KB>;
-    constexpr int RS = C::RS, BS = C::BS, CS = C::CS, QV = C::QV, KP = KB * 32;
+    constexpr int RSG = C::RSG, CS = C::CS, AC = C::AC, NG = C::NG, QU = C::QU, RINGU = C::RINGU, KP = KB * 32;
     if ((int)blockIdx.x >= *ntiles) return;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-    unsigned char *araw = base;                        // RS x A_RAW
-    unsigned char *bops = araw + RS * C::A_RAW;        // BS x B_RAW
-    unsigned char *cmp = bops + BS * C::B_RAW;         // CS x (A_hi, A_lo)
-    int *ring = reinterpret_cast<int *>(cmp + CS * C::CMP);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(cmp + CS * C::CMP + C::RING);
-    uint64_t *a_full = bar;                   // RS: 256 cp.async arrivals
-    uint64_t *b_full = a_full + RS;           // BS: operator copy (transaction bytes)
-    uint64_t *b_free = b_full + BS;           // BS: MMA commits
-    uint64_t *cmp_full = b_free + BS;         // CS: 256 arrivals after the split
+    unsigned char *araw = base;                           // NG x RSG x A_RAW
+    unsigned char *bops = araw + NG * RSG * C::A_RAW;     // CS x B_RAW
+    int *ring = reinterpret_cast<int *>(bops + CS * C::B_RAW);  // NG x RINGU x M
+    uint64_t *bar = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(ring) + C::RING);
+    uint64_t *a_full = bar;                   // NG x RSG: cp.async arrivals of the group's 128 threads
+    uint64_t *b_full = a_full + NG * RSG;     // CS: operator copy (transaction bytes)
+    uint64_t *cmp_full = b_full + CS;         // CS: one arrival per warp of the unit's group
     uint64_t *cmp_free = cmp_full + CS;       // CS: MMA commits
-    uint64_t *acc_full = cmp_free + CS;       // 2: MMA commits at the end of a group
-    uint64_t *acc_empty = acc_full + 2;       // 2: 256 arrivals after a drain
-    uint64_t *fin = acc_full + 4;             // 1
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_full + 5);
+    uint64_t *acc_full = cmp_free + CS;       // AC: MMA commits at the end of a group of vectors
+    uint64_t *acc_empty = acc_full + AC;      // AC: one arrival per worker warp after a drain
+    uint64_t *fin = acc_empty + AC;           // 1
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(fin + 1);
     int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool worker = warp < C::NW;
-    const int row = tid & 127, half = (tid >> 7) & 1;  // worker: target row and coefficient half
+    const int row = tid & 127, grp = (tid >> 7) & 1;  // worker: target row and group
     const M2LTile td = tiles[blockIdx.x];
     const int PP = p * p;
     const int l = td.level, sh = FMM_MAXLEVEL - l;
@@ -281,18 +342,15 @@ __global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
     const int ngroups = (nv + C::GV - 1) / C::GV;
 
     if (tid == 0) {
-        for (int s = 0; s < RS; s++) mbar_init(&a_full[s], 32 * C::NW);
-        for (int s = 0; s < BS; s++) {
-            mbar_init(&b_full[s], 1);
-            mbar_init(&b_free[s], 1);
-        }
+        for (int s = 0; s < NG * RSG; s++) mbar_init(&a_full[s], 128);
         for (int s = 0; s < CS; s++) {
-            mbar_init(&cmp_full[s], 32 * C::NW);
+            mbar_init(&b_full[s], 1);
+            mbar_init(&cmp_full[s], C::NW / C::NG);
             mbar_init(&cmp_free[s], 1);
         }
-        for (int b = 0; b < 2; b++) {
+        for (int b = 0; b < AC; b++) {
             mbar_init(&acc_full[b], 1);
-            mbar_init(&acc_empty[b], 32 * C::NW);
+            mbar_init(&acc_empty[b], C::NW);
         }
         mbar_init(fin, 1);
         *abort_flag = 0;
@@ -315,30 +373,27 @@ __global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
             const uint32_t id_full = idesc_tf32(128, 2 * NP), id_half = idesc_tf32(128, NP);
             for (int u = 0; u < nunits; u++) {
                 if (*(volatile int *)abort_flag) break;
-                const int c = u % CS, bs = u % BS;
-                const int vi = u / KB, kb = u % KB, g = vi / C::GV, b = g & 1;
+                const int c = u % CS;
+                const int vi = u / KB, kb = u % KB, g = vi / C::GV, b = g % AC;
                 bool ok = mbar_wait(&cmp_full[c], (uint32_t)((u / CS) & 1));
-                if (ok) ok = mbar_wait(&b_full[bs], (uint32_t)((u / BS) & 1));
-                if (ok && kb == 0 && vi % C::GV == 0 && g >= 2) ok = mbar_wait(&acc_empty[b], (uint32_t)(((g - 2) >> 1) & 1));
+                if (ok && kb == 0 && vi % C::GV == 0 && g >= AC)
+                    ok = mbar_wait(&acc_empty[b], (uint32_t)(((g - AC) / AC) & 1));
                 if (!ok) {
                     atomicExch(abort_flag, 1);
                     break;
                 }
-                fence_proxy_async();
                 tc_fence_after();
-                unsigned char *cs = cmp + c * C::CMP;
-                const uint32_t ahi = smem_u32(cs), alo = smem_u32(cs + C::A_RAW);
-                const uint32_t bb = smem_u32(bops + bs * C::B_RAW);
+                const uint32_t ahi = tmem + (uint32_t)(C::ACC_COLS + c * C::ACOLS), alo = ahi + 32;
+                const uint32_t bb = smem_u32(bops + c * C::B_RAW);
                 const uint32_t dmain = tmem + (uint32_t)(b * 2 * NP), dcorr = dmain + NP;
                 const bool first = (vi % C::GV == 0) && kb == 0;
 #pragma unroll
                 for (int k = 0; k < 4; k++) {
                     // A_hi [T_hi ; T_lo] -> main | correction, then A_lo T_hi -> correction
-                    mma_tf32(dmain, sdesc(ahi + 32 * k), sdesc(bb + 32 * k), id_full, (first && k == 0) ? 0u : 1u);
-                    mma_tf32(dcorr, sdesc(alo + 32 * k), sdesc(bb + 32 * k), id_half, 1u);
+                    mma_tf32_ta(dmain, ahi + 8 * k, sdesc(bb + 32 * k), id_full, (first && k == 0) ? 0u : 1u);
+                    mma_tf32_ta(dcorr, alo + 8 * k, sdesc(bb + 32 * k), id_half, 1u);
                 }
                 mma_commit(&cmp_free[c]);
-                mma_commit(&b_free[bs]);
                 if ((kb == KB - 1) && ((vi % C::GV == C::GV - 1) || vi == nv - 1)) mma_commit(&acc_full[b]);
             }
             // every commit has arrived before the shared memory goes away
@@ -352,21 +407,21 @@ __global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
             int issued = 0;
             for (int u = 0; u < nunits; u++) {
                 if (*(volatile int *)abort_flag) break;
-                const int bs = u % BS;
-                if (u >= BS && !mbar_wait(&b_free[bs], (uint32_t)(((u - BS) / BS) & 1))) {
+                const int c = u % CS;
+                if (u >= CS && !mbar_wait(&cmp_free[c], (uint32_t)(((u - CS) / CS) & 1))) {
                     atomicExch(abort_flag, 1);
                     break;
                 }
                 const int4 v = st[e0 + u / KB];
-                mbar_arrive_tx(&b_full[bs], C::B_RAW);
-                bulk_g2s(smem_u32(bops + bs * C::B_RAW), ttab + ((size_t)v.w * KB + u % KB) * C::B_RAW, C::B_RAW,
-                         &b_full[bs]);
+                mbar_arrive_tx(&b_full[c], C::B_RAW);
+                bulk_g2s(smem_u32(bops + c * C::B_RAW), ttab + ((size_t)v.w * KB + u % KB) * C::B_RAW, C::B_RAW,
+                         &b_full[c]);
                 issued = u + 1;
             }
             // copies still in flight when the pipeline stopped early land
             // before the shared memory goes away (bounded waits)
             if (*(volatile int *)abort_flag)
-                for (int u = max(0, issued - BS); u < issued; u++) mbar_wait(&b_full[u % BS], (uint32_t)((u / BS) & 1));
+                for (int u = max(0, issued - CS); u < issued; u++) mbar_wait(&b_full[u % CS], (uint32_t)((u / CS) & 1));
         }
     } else {
         // ---------------------------------------------------------- worker warps
@@ -374,75 +429,64 @@ __global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
         float acc_hi[HN], acc_lo[HN];
 #pragma unroll
         for (int k = 0; k < HN; k++) acc_hi[k] = acc_lo[k] = 0.f;
+        const uint32_t tlane = (uint32_t)((warp & 3) * 32) << 16;  // this warp's TMEM lane quarter
+        const int g = grp;
+        const int nown = nunits > g ? (nunits - g + 1) / 2 : 0;  // units u = g, g + 2, ... of this group
+        int *myring = ring + g * RINGU * C::M;
+        const bool dense = LD.map_off >= 0;  // the level has a lattice map: lookups arrive by cp.async
 
-        // source cell of vector vi for row `row`, fetched QV vectors ahead into
-        // ring slot vi % (2 QV) by the row's half-0 thread (cp.async of the
-        // lattice-map entry when the level has a dense map, a search of the
-        // level's keys otherwise); it is visible to the half-1 thread through
-        // the raw-stage barrier of the unit whose loads issued it
-        auto fetch = [&](int vi) {
-            if (half) return;
-            const uint32_t slot = smem_u32(ring + (vi % (2 * QV)) * 128 + row);
+        // source cell of this row for the group's unit j, looked up QU units
+        // ahead into ring slot j % RINGU (cp.async of the lattice-map entry, or
+        // a search of the level's keys); only this thread reads the slot, after
+        // the raw-stage barrier that its own later copies arrive on
+        auto fetch = [&](int j) {
+            if (j >= nown) return;
+            const uint32_t slot = smem_u32(myring + (j % RINGU) * C::M + row);
             int r = -1;
-            if (cell >= 0 && vi < nv) {
-                const int4 v = st[e0 + vi];
+            if (cell >= 0) {
+                const int4 v = st[e0 + (2 * j + g) / KB];
                 const int x = px + v.x, y = py + v.y, z = pz + v.z, side = 1 << l;
                 if (x >= 0 && y >= 0 && z >= 0 && x < side && y < side && z < side) {
-                    if (LD.map_off >= 0) {
+                    if (dense) {
                         cp_async4(slot, map_pool + LD.map_off + (long long)morton3((uint32_t)x, (uint32_t)y, (uint32_t)z));
                         return;
                     }
                     r = level_lookup(LD, map_pool, anchor, l, x, y, z);
                 }
             }
-            ring[(vi % (2 * QV)) * 128 + row] = r;
+            if (dense) cp_async4(slot, &g_no_cell);
+            else myring[(j % RINGU) * C::M + row] = r;
         };
-        for (int i = 0; i < QV; i++) fetch(i);
-        cp_async_commit();
-        cp_async_wait_all();
-        named_barrier_sync(1, 32 * C::NW);  // the first ring entries, for every worker
-
-        int src = -1;
-        // copy unit u into raw stage u % RS: this warp's 32 rows and its half
-        // of each row (64 B)
-        auto load_unit = [&](int u) {
-            const int r = u % RS, vi = u / KB, kb = u % KB;
-            if (kb == 0) {
-                src = ring[(vi % (2 * QV)) * 128 + row];
-                fetch(vi + QV);
-            }
-            const uint32_t ar = smem_u32(araw + r * C::A_RAW);
-            const int ch = 4 * half + (lane & 3);
+        // copy the group's unit j into its raw stage j % RSG: this thread's row (128 B)
+        auto load_unit = [&](int j) {
+            const int u = 2 * j + g, kb = u % KB;
+            const int src = myring[(j % RINGU) * C::M + row];
+            fetch(j + QU);
+            const uint32_t ar = smem_u32(araw + (g * RSG + j % RSG) * C::A_RAW) + (uint32_t)row * 128u;
+            const float *gs = mrow + ((size_t)(src >= 0 ? src : 0) * KP + kb * 32);
 #pragma unroll
-            for (int i = 0; i < 4; i++) {
-                const int rr = 8 * i + (lane >> 2);  // row within the warp's 32
-                const int sr = __shfl_sync(0xffffffffu, src, rr);
-                const int ro = ((warp & 3) << 5) + rr;
-                const float *g = mrow + ((size_t)(sr >= 0 ? sr : 0) * KP + kb * 32) + ch * 4;
-                cp_async16(ar + (uint32_t)ro * 128u + ((((uint32_t)ch) ^ ((uint32_t)ro & 7u)) << 4), g,
-                           sr >= 0 ? 16u : 0u);
-            }
-            if (kb == 0) __threadfence_block();  // a ring entry stored directly by fetch() is ordered before the arrival
-            cp_async_arrive_noinc(&a_full[r]);
+            for (int ch = 0; ch < 8; ch++)
+                cp_async16(ar + ((((uint32_t)ch) ^ ((uint32_t)row & 7u)) << 4), gs + ch * 4, src >= 0 ? 16u : 0u);
+            cp_async_arrive_noinc(&a_full[g * RSG + j % RSG]);
         };
 
-        auto drain = [&](int g) {
-            const int b = g & 1;
+        auto drain = [&](int gg) {
+            const int b = gg % AC;
             __syncwarp();
-            const bool ok = __all_sync(0xffffffffu, mbar_wait(&acc_full[b], (uint32_t)((g >> 1) & 1)));
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(&acc_full[b], (uint32_t)((gg / AC) & 1)));
             if (!ok) {
                 atomicExch(abort_flag, 1);
                 return;
             }
             tc_fence_after();
-            const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(b * 2 * NP + half * HN);
+            const uint32_t taddr = tmem + tlane + (uint32_t)(b * 2 * NP + g * HN);
             float mv[16], cv[16];
 #pragma unroll
             for (int k0 = 0; k0 < HN; k0 += 16) {
                 if (k0 + 16 <= HN) {
                     tmem_ld16(taddr + k0, mv);
                     tmem_ld16(taddr + NP + k0, cv);
-                } else {  // HN = 8 (p <= 4): 8 columns
+                } else {  // 8 remaining columns
                     tmem_ld8(taddr + k0, mv);
                     tmem_ld8(taddr + NP + k0, cv);
                 }
@@ -451,46 +495,63 @@ __global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
                     if (k0 + k < HN) two_sum_acc(acc_hi[k0 + k], acc_lo[k0 + k], mv[k] + cv[k]);
             }
             tc_fence_before();
-            mbar_arrive(&acc_empty[b]);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[b]);
         };
 
-        for (int u = 0; u < RS && u < nunits; u++) load_unit(u);
+        for (int j = 0; j < QU; j++) fetch(j);
+        cp_async_commit();
+        cp_async_wait_all();
+        for (int j = 0; j < RSG && j < nown; j++) load_unit(j);
         int drained = 0;
-        for (int u = 0; u < nunits; u++) {
+        for (int j = 0; j < nown; j++) {
             if (*(volatile int *)abort_flag) break;
-            const int r = u % RS, c = u % CS;
-            bool ok = mbar_wait(&a_full[r], (uint32_t)((u / RS) & 1));
-            if (ok && u >= CS) ok = mbar_wait(&cmp_free[c], (uint32_t)(((u - CS) / CS) & 1));
+            const int u = 2 * j + g, c = u % CS, vi = u / KB;
+            // one accumulator buffer: group gg is drained before group gg + 1 starts
+            if (AC == 1 && vi / C::GV > drained) {
+                drain(drained);
+                drained++;
+                if (*(volatile int *)abort_flag) break;
+            }
+            const bool ok = mbar_wait2(u >= CS ? 3u : 1u, &a_full[g * RSG + j % RSG], (uint32_t)((j / RSG) & 1),
+                                       &cmp_free[c], (uint32_t)((max(u - CS, 0) / CS) & 1));
             if (!ok) {
                 atomicExch(abort_flag, 1);
                 break;
             }
-            // split raw FP32 into TF32 (hi, lo), this thread's half of its row:
-            // hi rounded to nearest, lo = a - hi (exact in FP32; the MMA reads
-            // its leading 11 bits, an error below 2^-21 of a)
-            unsigned char *rs = araw + r * C::A_RAW;
-            unsigned char *cs = cmp + c * C::CMP;
+            tc_fence_after();
+            // split this row's raw FP32 k-block into TF32 (hi, lo): hi rounded to
+            // nearest, lo = a - hi (exact in FP32; the MMA reads its leading 11
+            // bits, an error below 2^-21 of a); both go to the A stage in TMEM
+            const unsigned char *rs = araw + (g * RSG + j % RSG) * C::A_RAW + row * 128;
+            const uint32_t ta = tmem + tlane + (uint32_t)(C::ACC_COLS + c * C::ACOLS);
 #pragma unroll
-            for (int j = 0; j < 4; j++) {
-                const int ch = 4 * half + j;
-                const uint32_t o = (uint32_t)row * 128u + ((((uint32_t)ch) ^ ((uint32_t)row & 7u)) << 4);
-                const float4 a = *reinterpret_cast<const float4 *>(rs + o);
-                float4 hi, lo;
-                hi.x = tf32_rn(a.x); lo.x = a.x - hi.x;
-                hi.y = tf32_rn(a.y); lo.y = a.y - hi.y;
-                hi.z = tf32_rn(a.z); lo.z = a.z - hi.z;
-                hi.w = tf32_rn(a.w); lo.w = a.w - hi.w;
-                *reinterpret_cast<float4 *>(cs + o) = hi;
-                *reinterpret_cast<float4 *>(cs + C::A_RAW + o) = lo;
+            for (int h = 0; h < 2; h++) {
+                float hi[16], lo[16];
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const int ch = 4 * h + q;
+                    const float4 a = *reinterpret_cast<const float4 *>(rs + ((ch ^ (row & 7)) << 4));
+                    hi[4 * q + 0] = tf32_rn(a.x); lo[4 * q + 0] = a.x - hi[4 * q + 0];
+                    hi[4 * q + 1] = tf32_rn(a.y); lo[4 * q + 1] = a.y - hi[4 * q + 1];
+                    hi[4 * q + 2] = tf32_rn(a.z); lo[4 * q + 2] = a.z - hi[4 * q + 2];
+                    hi[4 * q + 3] = tf32_rn(a.w); lo[4 * q + 3] = a.w - hi[4 * q + 3];
+                }
+                tmem_st16(ta + 16 * h, hi);
+                tmem_st16(ta + 32 + 16 * h, lo);
             }
-            fence_proxy_async();
-            mbar_arrive(&cmp_full[c]);
-            // this warp has read its part of raw stage r: refill it with unit u + RS
+            tmem_wait_st();
+            tc_fence_before();
             __syncwarp();
-            if (u + RS < nunits) load_unit(u + RS);
-            // drain group g - 1 once group g is well under way
-            const int vi = u / KB;
-            if ((u % KB) == KB - 1 && vi % C::GV == 2 && vi / C::GV >= 1 && drained < vi / C::GV) {
+            if (lane == 0) {
+                // the group's first warp also waits for the operator block
+                if ((warp & 3) == 0 && !mbar_wait(&b_full[c], (uint32_t)((u / CS) & 1))) atomicExch(abort_flag, 1);
+                mbar_arrive(&cmp_full[c]);
+            }
+            // this thread has read its row of the raw stage: refill it
+            if (j + RSG < nown) load_unit(j + RSG);
+            // two accumulator buffers: drain group gg once group gg + 1 is well under way
+            if (AC == 2 && vi >= C::DRAIN_AT && (vi - C::DRAIN_AT) / C::GV > drained) {
                 drain(drained);
                 drained++;
             }
@@ -504,15 +565,15 @@ __global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
             }
         }
         if (cell >= 0 && !*(volatile int *)abort_flag) {
-            float *Lc = L + (size_t)cell * PP + half * HN;
+            float *Lc = L + (size_t)cell * PP + g * HN;
 #pragma unroll
             for (int k = 0; k < HN; k++)
-                if (half * HN + k < PP) Lc[k] += acc_hi[k] + acc_lo[k];
+                if (g * HN + k < PP) Lc[k] += acc_hi[k] + acc_lo[k];
         }
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == C::NW) {
+    if (warp == C::MMA_WARP) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TCOLS));
     }
     if (tid == 0 && *(volatile int *)abort_flag) atomicExch(err, 1);
