@@ -9,11 +9,14 @@
 // GPU mapping: one block of 128 threads per target leaf. Each thread owns two
 // targets (i and i + R, R = ceil(n_leaf / 2) rows) and one of S = 128 / R
 // slices of the source stream, so a leaf of ~38 particles keeps ~114 of 128
-// threads busy. Source leaves are concatenated into a shared-memory chunk;
-// threads of one slice read the same source (broadcast), FMA and rsqrt run on
-// the CUDA cores. In FP32 the sum over a slice is taken in blocks of 64
-// sources whose totals are added with TwoSum, and slices are combined in FP64
-// in a fixed order, so the result does not depend on scheduling.
+// threads busy. Warp 0 plans each chunk of the concatenated source leaves (its
+// pieces of runs); all threads copy it into shared memory as pair records
+// while the previous chunk is computed. Threads of one slice read the same
+// source pair (broadcast); the interaction runs on packed FP32 pairs (f32x2)
+// and rsqrt on the CUDA cores. Block sums of up to ~128 source pairs, and the
+// target leaf's own particles separately, are added with TwoSum into a
+// per-thread (hi, lo) state; slices are combined with TwoSum in a fixed
+// order, so the result does not depend on scheduling.
 #include <algorithm>
 #include <type_traits>
 
@@ -97,19 +100,21 @@ constexpr int P2P_T = FMM_P2P_T;  // threads per block (one target leaf)
 // chunk buffers (2: the next chunk is copied while the current one is
 // computed; 3: the next two)
 #ifndef FMM_P2P_CH
-#define FMM_P2P_CH 704
+#define FMM_P2P_CH 688
 #endif
+// source segments (pieces of runs) per chunk of the packed path
+constexpr int P2P_MAXSEG = 32;
 #ifndef FMM_P2P_NBUF
 #define FMM_P2P_NBUF 2
 #endif
-// source pairs per TwoSum block and the unroll of the pair loop
-#ifndef FMM_P2P_BLK
-#define FMM_P2P_BLK 64
+// source pairs summed in FP32 before they are folded into the TwoSum state,
+// and the source pairs of one fully unrolled step of the pair loop
+#ifndef FMM_P2P_FOLD
+#define FMM_P2P_FOLD 128
 #endif
-#ifndef FMM_P2P_UNROLL
-#define FMM_P2P_UNROLL 8
+#ifndef FMM_P2P_STEP
+#define FMM_P2P_STEP 8
 #endif
-constexpr int P2P_UNROLL = FMM_P2P_UNROLL;
 
 // One source against the TPT targets of a thread.
 template <bool CHECK, bool DS, int TPT, class T, class T4>
@@ -220,15 +225,14 @@ __device__ __forceinline__ void interact_pk(f2 sx, f2 sy, f2 sz, f2 sq, f2 tx, f
 }
 
 // Sources [j0, j1) of a pair-record chunk against the TPT targets of a
-// thread. An odd source at either end is taken alone; the pairs between run in
-// blocks of BLK pairs whose two halves are added and then summed with TwoSum
-// into the thread's (hi, lo) state, kept in shared memory (hl[c * P2P_T] and
-// hl[(4 TPT + c) * P2P_T]) since it is touched once per block only.
+// thread, added into the packed block sums acc (the two halves hold even and
+// odd sources). An odd source at either end is taken alone and added to the
+// low half; the pairs between run in fully unrolled steps and a tail.
+// `cnt` counts the pairs in acc since the last fold.
 template <bool CHECK, int TPT>
 __device__ __forceinline__ void p2p_range_pk(int j0, int j1, const float *shf, const f2 (&tx)[TPT], const f2 (&ty)[TPT],
-                                             const f2 (&tz)[TPT], float *hl)
+                                             const f2 (&tz)[TPT], f2 (&acc)[4 * TPT], int &cnt)
 {
-    auto add = [&](int c, float v) { acc2(hl[c * P2P_T], hl[(4 * TPT + c) * P2P_T], v); };
     auto single = [&](int j) {
         const float *r = shf + 8 * (j >> 1) + (j & 1);
         const float4 sj = make_float4(r[0], r[2], r[4], r[6]);
@@ -240,53 +244,51 @@ __device__ __forceinline__ void p2p_range_pk(int j0, int j1, const float *shf, c
             f2_unpack(tz[k], zi, u);
             float pp = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
             interact<CHECK>(make_float4(xi, yi, zi, 0.f), sj, pp, gx, gy, gz);
-            add(4 * k, pp);
-            add(4 * k + 1, gx);
-            add(4 * k + 2, gy);
-            add(4 * k + 3, gz);
+            // interact() and the packed sums both hold q (x_j - x_i) / r^3
+            acc[4 * k] = f2_add(acc[4 * k], f2_pack(pp, 0.f));
+            acc[4 * k + 1] = f2_add(acc[4 * k + 1], f2_pack(gx, 0.f));
+            acc[4 * k + 2] = f2_add(acc[4 * k + 2], f2_pack(gy, 0.f));
+            acc[4 * k + 3] = f2_add(acc[4 * k + 3], f2_pack(gz, 0.f));
         }
+        cnt++;
     };
     int a = j0, b = j1;
     if (a < b && (a & 1)) single(a++);
     if (a < b && (b & 1)) single(--b);
     const ulonglong2 *pr = reinterpret_cast<const ulonglong2 *>(shf);
-    auto fold = [&](const f2 (&acc)[4 * TPT]) {
-#pragma unroll
-        for (int c = 0; c < 4 * TPT; c++) {
-            float u, v;
-            f2_unpack(acc[c], u, v);
-            add(c, u + v);
-        }
-    };
     int k = a >> 1;
     const int k1 = b >> 1;
-    for (; k + FMM_P2P_BLK <= k1; k += FMM_P2P_BLK) {
-        f2 acc[4 * TPT];
+    cnt += k1 - k;
+    for (; k + FMM_P2P_STEP <= k1; k += FMM_P2P_STEP) {
 #pragma unroll
-        for (int c = 0; c < 4 * TPT; c++) acc[c] = 0ull;
-#pragma unroll P2P_UNROLL
-        for (int kk = 0; kk < FMM_P2P_BLK; kk++) {
+        for (int kk = 0; kk < FMM_P2P_STEP; kk++) {
             const ulonglong2 A = pr[2 * (k + kk)], B = pr[2 * (k + kk) + 1];
 #pragma unroll
             for (int t = 0; t < TPT; t++)
                 interact_pk<CHECK>(A.x, A.y, B.x, B.y, tx[t], ty[t], tz[t], acc[4 * t], acc[4 * t + 1], acc[4 * t + 2],
                                    acc[4 * t + 3]);
         }
-        fold(acc);
     }
-    if (k < k1) {
-        f2 acc[4 * TPT];
+    for (; k < k1; k++) {
+        const ulonglong2 A = pr[2 * k], B = pr[2 * k + 1];
 #pragma unroll
-        for (int c = 0; c < 4 * TPT; c++) acc[c] = 0ull;
-#pragma unroll 4
-        for (; k < k1; k++) {
-            const ulonglong2 A = pr[2 * k], B = pr[2 * k + 1];
+        for (int t = 0; t < TPT; t++)
+            interact_pk<CHECK>(A.x, A.y, B.x, B.y, tx[t], ty[t], tz[t], acc[4 * t], acc[4 * t + 1], acc[4 * t + 2],
+                               acc[4 * t + 3]);
+    }
+}
+
+// the packed block sums are added, half by half, into the thread's (hi, lo)
+// state with TwoSum (hl[c * P2P_T], hl[(4 TPT + c) * P2P_T] in shared memory)
+template <int TPT>
+__device__ __forceinline__ void p2p_fold_pk(f2 (&acc)[4 * TPT], float *hl)
+{
 #pragma unroll
-            for (int t = 0; t < TPT; t++)
-                interact_pk<CHECK>(A.x, A.y, B.x, B.y, tx[t], ty[t], tz[t], acc[4 * t], acc[4 * t + 1], acc[4 * t + 2],
-                                   acc[4 * t + 3]);
-        }
-        fold(acc);
+    for (int c = 0; c < 4 * TPT; c++) {
+        float u, v;
+        f2_unpack(acc[c], u, v);
+        acc2(hl[c * P2P_T], hl[(4 * TPT + c) * P2P_T], u + v);
+        acc[c] = 0ull;
     }
 }
 
@@ -315,7 +317,7 @@ struct RunCursor {
 // come as particle runs (adjacent source leaves merged); chunks of CH sources
 // are copied into shared memory with cp.async, the next chunk while the
 // current one is computed (two buffers). Only the target leaf's own particles
-// need the j == i / r == 0 test. Slices are reduced in FP64 in a fixed order.
+// need the j == i / r == 0 test. Slices are reduced in a fixed order.
 // DS: FP32 (hi, lo) coordinates for FP64 inputs.
 template <class T, bool DS, int TPT>
 __global__ void __launch_bounds__(P2P_T, sizeof(T) == 4 ? FMM_P2P_MINB : 1) p2p_k(const typename Vec4<T>::type *__restrict__ xs, const float4 *__restrict__ xlo,
@@ -329,9 +331,15 @@ __global__ void __launch_bounds__(P2P_T, sizeof(T) == 4 ? FMM_P2P_MINB : 1) p2p_
     constexpr int CH = DS ? 512 : (sizeof(T) == 8 ? 512 : FMM_P2P_CH);
     constexpr int NB = PK ? FMM_P2P_NBUF : 2;
     static_assert(NB == 2 || NB == 3, "two or three chunk buffers");
+    static_assert(!(PK && NB == 3), "the packed path plans one chunk ahead");
     __shared__ T4 sh[NB][CH];
     __shared__ float4 shlo[DS ? 2 : 1][DS ? CH : 1];
     __shared__ float hls[PK ? 8 * TPT * P2P_T : 1];  // packed path: per-thread TwoSum state, column-major
+    // packed path: per chunk, its source segments (first source, count,
+    // position in the chunk) and (segments, fill, own-leaf range), planned by
+    // warp 0; three tables rotate so none is rewritten while it is read
+    __shared__ int4 tseg[PK ? 3 : 1][PK ? P2P_MAXSEG : 1];
+    __shared__ int4 tinf[PK ? 3 : 1];
     static_assert(sizeof(T4) * NB * CH >= sizeof(double) * P2P_T * 4 * TPT, "slice sums reuse the source buffers");
     double *red = reinterpret_cast<double *>(&sh[0][0]);  // slice sums, after the last chunk
     const int A = leaves[blockIdx.x];
@@ -380,6 +388,77 @@ __global__ void __launch_bounds__(P2P_T, sizeof(T) == 4 ? FMM_P2P_MINB : 1) p2p_
         return fill;
     };
 
+    // warp 0: the next chunk's segments from the run cursor, 32 runs per step
+    // (a warp scan of their lengths gives their positions in the chunk)
+    auto plan = [&](RunCursor &cur, int tb_) {
+        const int lane = threadIdx.x & 31;
+        int fill = 0, nseg = 0;
+        if (lane == 0) tinf[tb_] = make_int4(0, 0, 0, 0);
+        __syncwarp();
+        while (cur.k < cur.k1 && fill < CH && nseg < P2P_MAXSEG) {
+            const int k = cur.k + lane;
+            int g0 = 0, len = 0;
+            if (k < cur.k1) {
+                const int2 rr = runs[k];
+                g0 = rr.x + (lane == 0 ? cur.off : 0);
+                len = rr.y - g0;
+            }
+            int incl = len;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const int start = fill + incl - len;
+            int take = max(0, min(len, CH - start));
+            if (nseg + lane >= P2P_MAXSEG) take = 0;
+            const int cnt = __popc(__ballot_sync(0xffffffffu, take > 0));
+            if (cnt == 0) break;
+            if (take > 0) {
+                tseg[tb_][nseg + lane] = make_int4(g0, take, start, 0);
+                const int a = max(g0, tb), b = min(g0 + take, te);
+                if (a < b) {
+                    tinf[tb_].z = start + a - g0;
+                    tinf[tb_].w = start + b - g0;
+                }
+            }
+            const int lt = __shfl_sync(0xffffffffu, take, cnt - 1), ll = __shfl_sync(0xffffffffu, len, cnt - 1),
+                      ls = __shfl_sync(0xffffffffu, start, cnt - 1);
+            fill = ls + lt;
+            nseg += cnt;
+            if (lt == ll) {
+                cur.k += cnt;
+                cur.off = 0;
+            } else {
+                cur.off = (cnt == 1 ? cur.off : 0) + lt;
+                cur.k += cnt - 1;
+            }
+        }
+        __syncwarp();
+        if (lane == 0) {
+            tinf[tb_].x = nseg;
+            tinf[tb_].y = fill;
+        }
+    };
+    // every thread: copy its sources of the planned chunk into buffer bf
+    auto stage_planned = [&](int tb_, int bf) {
+        const int ns = tinf[tb_].x;
+        float *base = reinterpret_cast<float *>(&sh[bf][0]);
+        for (int sgi = 0; sgi < ns; sgi++) {
+            const int4 e = tseg[tb_][sgi];
+            for (int j = threadIdx.x; j < e.y; j += P2P_T) {  // source c -> pair record c / 2, half c % 2
+                const int c = e.z + j;
+                float *d = base + 8 * (c >> 1) + (c & 1);
+                const float *g = reinterpret_cast<const float *>(xs + e.x + j);
+                cpa4(d, g);
+                cpa4(d + 2, g + 1);
+                cpa4(d + 4, g + 2);
+                cpa4(d + 6, g + 3);
+            }
+        }
+        cpa_commit();
+    };
+
     for (int t0 = tb; t0 < te; t0 += TPT * P2P_T) {
         const int nt = min(TPT * P2P_T, te - t0);
         const int R = (nt + TPT - 1) / TPT;
@@ -407,13 +486,28 @@ __global__ void __launch_bounds__(P2P_T, sizeof(T) == 4 ? FMM_P2P_MINB : 1) p2p_
         T h[4 * TPT], lo[4 * TPT];
 #pragma unroll
         for (int c = 0; c < 4 * TPT; c++) h[c] = lo[c] = T(0);
+        f2 pacc[4 * TPT];  // packed path: block sums of the current fold
+        int pcnt = 0;
+#pragma unroll
+        for (int c = 0; c < 4 * TPT; c++) pacc[c] = 0ull;
         if constexpr (PK) {
 #pragma unroll
             for (int c = 0; c < 8 * TPT; c++) hls[c * P2P_T + threadIdx.x] = 0.f;
         }
         RunCursor cur{r0, r1, 0};
         __syncthreads();  // buffers free (previous target block or slice sums)
-        int slo, shi, fill = stage(cur, 0, slo, shi);
+        int slo = 0, shi = 0, fill = 0, ti = 0;  // ti: table of the current chunk
+        if constexpr (PK) {
+            if (threadIdx.x < 32) plan(cur, 0);
+            __syncthreads();
+            const int4 inf = tinf[0];
+            fill = inf.y;
+            slo = inf.z;
+            shi = inf.w;
+            if (fill > 0) stage_planned(0, 0);
+        } else {
+            fill = stage(cur, 0, slo, shi);
+        }
         int bf = 0;
         // NB = 3: chunk i + 1 is staged ahead as well; chunk i + 2 goes into
         // the buffer of chunk i - 1 once every thread has passed the barrier
@@ -427,6 +521,20 @@ __global__ void __launch_bounds__(P2P_T, sizeof(T) == 4 ? FMM_P2P_MINB : 1) p2p_
                 else cpa_wait0();
                 __syncthreads();  // chunk bf complete; chunk bf - 1 consumed by every thread
                 if (cur.k < cur.k1) n2fill = stage(cur, bf == 0 ? 2 : bf - 1, n2lo, n2hi);
+            } else if constexpr (PK) {
+                // warp 0 plans chunk bf + 1; after the barrier chunk bf is
+                // complete, every thread has finished chunk bf - 1, and all copy
+                // chunk bf + 1 into its buffer while chunk bf is computed
+                cpa_wait0();
+                const int tn = ti == 2 ? 0 : ti + 1;
+                if (threadIdx.x < 32) plan(cur, tn);
+                __syncthreads();
+                const int4 inf = tinf[tn];
+                nfill = inf.y;
+                nslo = inf.z;
+                nshi = inf.w;
+                if (nfill > 0) stage_planned(tn, bf ^ 1);
+                ti = tn;
             } else {
                 // one barrier per chunk: after it, chunk bf is complete and
                 // every thread has finished chunk bf - 1, whose buffer then
@@ -443,10 +551,21 @@ __global__ void __launch_bounds__(P2P_T, sizeof(T) == 4 ? FMM_P2P_MINB : 1) p2p_
                     const int jlo = min(fill, 2 * ((np * sl) / S));
                     const int jhi = min(fill, 2 * ((np * (sl + 1)) / S));
                     const float *sb = reinterpret_cast<const float *>(&sh[bf][0]);
-                    float *hl = hls + threadIdx.x;
-                    p2p_range_pk<false, TPT>(jlo, min(jhi, slo), sb, tx, ty, tz, hl);
-                    p2p_range_pk<true, TPT>(max(jlo, slo), min(jhi, shi), sb, tx, ty, tz, hl);
-                    p2p_range_pk<false, TPT>(max(jlo, shi), jhi, sb, tx, ty, tz, hl);
+                    // the target leaf's own particles (the nearest, largest
+                    // terms) are summed and folded on their own
+                    const bool own = max(jlo, slo) < min(jhi, shi);
+                    p2p_range_pk<false, TPT>(jlo, min(jhi, slo), sb, tx, ty, tz, pacc, pcnt);
+                    if (own) {
+                        p2p_fold_pk<TPT>(pacc, hls + threadIdx.x);
+                        p2p_range_pk<true, TPT>(max(jlo, slo), min(jhi, shi), sb, tx, ty, tz, pacc, pcnt);
+                        p2p_fold_pk<TPT>(pacc, hls + threadIdx.x);
+                        pcnt = 0;
+                    }
+                    p2p_range_pk<false, TPT>(max(jlo, shi), jhi, sb, tx, ty, tz, pacc, pcnt);
+                    if (pcnt >= FMM_P2P_FOLD) {
+                        p2p_fold_pk<TPT>(pacc, hls + threadIdx.x);
+                        pcnt = 0;
+                    }
                 } else {
                     const int jlo = (int)(((long long)fill * sl) / S), jhi = (int)(((long long)fill * (sl + 1)) / S);
                     const T4 *sb = sh[bf];
@@ -474,23 +593,48 @@ __global__ void __launch_bounds__(P2P_T, sizeof(T) == 4 ? FMM_P2P_MINB : 1) p2p_
         __syncthreads();  // the last chunk consumed before the slice sums reuse it
         if (act) {
             if constexpr (PK) {
+                p2p_fold_pk<TPT>(pacc, hls + threadIdx.x);
 #pragma unroll
                 for (int c = 0; c < 4 * TPT; c++) {
                     h[c] = hls[c * P2P_T + threadIdx.x];
                     lo[c] = hls[(4 * TPT + c) * P2P_T + threadIdx.x];
                 }
             }
+            if constexpr (sizeof(T) == 4) {
+                float2 *red2 = reinterpret_cast<float2 *>(red);
 #pragma unroll
-            for (int c = 0; c < 4 * TPT; c++) red[(sl * R + row) * 4 * TPT + c] = (double)h[c] + (double)lo[c];
+                for (int c = 0; c < 4 * TPT; c++) red2[(sl * R + row) * 4 * TPT + c] = make_float2(h[c], lo[c]);
+            } else {
+#pragma unroll
+                for (int c = 0; c < 4 * TPT; c++) red[(sl * R + row) * 4 * TPT + c] = (double)h[c] + (double)lo[c];
+            }
         }
         __syncthreads();
         if ((int)threadIdx.x < R) {
             double o[4 * TPT];
+            if constexpr (sizeof(T) == 4) {
+                // slices in fixed order, compensated in FP32 (TwoSum of the
+                // leading parts, the trailing parts added), one conversion each
+                const float2 *red2 = reinterpret_cast<const float2 *>(red);
+                float oh[4 * TPT], ol[4 * TPT];
 #pragma unroll
-            for (int c = 0; c < 4 * TPT; c++) o[c] = 0.0;
-            for (int s2 = 0; s2 < S; s2++)
+                for (int c = 0; c < 4 * TPT; c++) oh[c] = ol[c] = 0.f;
+                for (int s2 = 0; s2 < S; s2++)
 #pragma unroll
-                for (int c = 0; c < 4 * TPT; c++) o[c] += red[(s2 * R + threadIdx.x) * 4 * TPT + c];
+                    for (int c = 0; c < 4 * TPT; c++) {
+                        const float2 v = red2[(s2 * R + threadIdx.x) * 4 * TPT + c];
+                        acc2(oh[c], ol[c], v.x);
+                        ol[c] += v.y;
+                    }
+#pragma unroll
+                for (int c = 0; c < 4 * TPT; c++) o[c] = (double)oh[c] + (double)ol[c];
+            } else {
+#pragma unroll
+                for (int c = 0; c < 4 * TPT; c++) o[c] = 0.0;
+                for (int s2 = 0; s2 < S; s2++)
+#pragma unroll
+                    for (int c = 0; c < 4 * TPT; c++) o[c] += red[(s2 * R + threadIdx.x) * 4 * TPT + c];
+            }
 #pragma unroll
             for (int kk = 0; kk < TPT; kk++)
                 if ((int)threadIdx.x + kk * R < nt)
