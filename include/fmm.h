@@ -149,6 +149,39 @@ FMM_API int fmm_build(fmm_handle h, const void *x, const void *q, int64_t n, int
  */
 FMM_API int fmm_evaluate(fmm_handle h, void *phi, void *grad);
 
+/* Weighted energy and its adjoint (differentiation of the evaluation).
+ *
+ * The paper evaluates potentials and forces (Sec. 2); these calls add the
+ * derivatives of the weighted energy E = 1/2 sum_i w_i q_i phi_i. The Laplace
+ * kernel is symmetric, so with psi the potential of the charges w_j q_j at the
+ * same positions:
+ *   dE/dq_k = 1/2 (w_k phi_k + psi_k),
+ *   dE/dx_k = 1/2 q_k (w_k grad phi_k + grad psi_k),
+ *   dE/dw_k = 1/2 q_k phi_k.
+ * psi comes from one more evaluation on the same tree: fmm_update_charges(h,
+ * q, w) then fmm_evaluate. */
+
+/* Replace the charges of the built tree by q (times w if w is not NULL), in
+ * the caller's order, same dtype and memory kind as at build; the positions and
+ * the tree stay. The next fmm_evaluate uses them. Returns FMM_ESTATE before a
+ * build, FMM_EINVAL for NULL h or q. */
+FMM_API int fmm_update_charges(fmm_handle h, const void *q, const void *w);
+
+/* *out = 1/2 sum_i w_i q_i phi_i over the built n particles, summed in FP64 in
+ * a fixed order. w, q, phi: device arrays of the build's dtype, caller's order.
+ * Returns FMM_ESTATE before a build, FMM_EINVAL on NULL arguments or a
+ * host-memory build. Synchronises the stream. */
+FMM_API int fmm_energy(fmm_handle h, const void *w, const void *q, const void *phi, double *out);
+
+/* Adjoint of fmm_energy scaled by gE: dq = gE dE/dq, dx = gE dE/dx (n x 3),
+ * dw = gE dE/dw, from phi, grad (the evaluation with charges q) and psi, gpsi
+ * (the evaluation with charges w q). Device arrays of the build's dtype,
+ * caller's order; any of dq, dx, dw may be NULL (dx needs grad and gpsi).
+ * Returns FMM_ESTATE before a build, FMM_EINVAL on NULL inputs or a
+ * host-memory build. */
+FMM_API int fmm_energy_adjoint(fmm_handle h, double gE, const void *w, const void *q, const void *phi,
+                               const void *grad, const void *psi, const void *gpsi, void *dq, void *dx, void *dw);
+
 /* Counters and phase timings of the last build and evaluate; synchronises
  * the handle's stream. */
 FMM_API int fmm_get_stats(fmm_handle h, fmm_stats *out);

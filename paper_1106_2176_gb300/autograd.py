@@ -1,0 +1,44 @@
+"""Differentiable weighted energy of the FMM potential.
+
+E(x, q, w) = 1/2 sum_i w_i q_i phi_i, phi_i = sum_{j != i} q_j / |x_i - x_j|,
+evaluated by the FMM. The backward pass is the library's adjoint: the kernel
+is symmetric, so dE/dq and dE/dx need one more FMM evaluation on the same tree
+with charges w q (psi), and nothing of the forward pass is kept but phi and
+grad phi; the expansions are recomputed rather than stored.
+
+    E = fmm_energy(x, q, w, p=8, theta=0.5, ncrit=64, precision="mixed")
+    E.backward()   # x.grad, q.grad, w.grad
+"""
+import torch
+
+from .fmm import FMM
+
+
+class FMMEnergy(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, x, q, w, p, theta, ncrit, precision):
+        f = FMM(x.shape[0], p=p, theta=theta, ncrit=ncrit, precision=precision)
+        x, q, w = x.contiguous(), q.contiguous(), w.contiguous()
+        f.build(x, q)
+        phi, grad = f.evaluate()
+        e = f.energy(w, q, phi)
+        ctx.f = f
+        ctx.save_for_backward(q, w, phi, grad)
+        return torch.tensor(e, dtype=torch.float64, device=x.device)
+
+    @staticmethod
+    def backward(ctx, gE):
+        q, w, phi, grad = ctx.saved_tensors
+        f = ctx.f
+        f.update_charges(q, w)
+        psi, gpsi = f.evaluate()
+        dq, dx, dw = f.energy_adjoint(float(gE), w, q, phi, grad, psi, gpsi, dq=ctx.needs_input_grad[1],
+                                      dx=ctx.needs_input_grad[0], dw=ctx.needs_input_grad[2])
+        ctx.f = None
+        f.close()
+        return dx, dq, dw, None, None, None, None
+
+
+def fmm_energy(x, q, w, p=8, theta=0.5, ncrit=64, precision="mixed"):
+    """1/2 sum w q phi with gradients for x (n, 3), q (n,) and w (n,); CUDA tensors, float32 or float64."""
+    return FMMEnergy.apply(x, q, w, p, theta, ncrit, precision)

@@ -78,7 +78,7 @@ void PinnedBuf::release()
 
 fmm_ctx::~fmm_ctx()
 {
-    fmm::DevBuf *bufs[] = {&st_dev, &rtab64, &rtab32, &m2m_mat, &l2l_mat, &ttab, &box, &x_in, &q_in, &keys, &keys2, &idx, &inv, &pcell, &cgeo,
+    fmm::DevBuf *bufs[] = {&st_dev, &rtab64, &rtab32, &m2m_mat, &l2l_mat, &ttab, &box, &x_in, &q_in, &w_in, &keys, &keys2, &idx, &inv, &pcell, &cgeo, &energy_buf,
                            &idx2, &hist, &scan_tmp, &xs64, &xs32, &xs32lo, &c_level, &c_anchor, &c_begin, &c_end, &c_child,
                            &c_nchild, &c_parent, &c_xyz, &split_cnt, &split_off, &split_bnd, &leaves, &frontA,
                            &frontB, &p2p_pairs, &m2lx_pairs, &pair_keys, &pair_keys2, &pair_vals, &pair_vals2,
@@ -326,6 +326,56 @@ int fmm_evaluate(fmm_handle h, void *phi, void *grad)
     FMM_CUDA_TRY(cudaEventRecord(ev[12], s));
     if (h->host_mem) FMM_CUDA_TRY(cudaStreamSynchronize(s));
     h->evaluated = true;
+    return FMM_OK;
+    API_END
+}
+
+int fmm_update_charges(fmm_handle h, const void *q, const void *w)
+{
+    if (!h) return fail(FMM_EINVAL, "fmm_update_charges: NULL handle");
+    if (!h->built) return fail(FMM_ESTATE, "fmm_update_charges: no successful fmm_build");
+    if (!q) return fail(FMM_EINVAL, "fmm_update_charges: NULL q");
+    API_BEGIN
+    const void *qd = q, *wd = w;
+    if (h->host_mem) {
+        const size_t es = h->dtype == FMM_F64 ? 8 : 4;
+        h->q_in.ensure(es * (size_t)h->n);
+        FMM_CUDA_TRY(cudaMemcpyAsync(h->q_in.p, q, es * (size_t)h->n, cudaMemcpyHostToDevice, h->stream));
+        qd = h->q_in.p;
+        if (w) {
+            h->w_in.ensure(es * (size_t)h->n);
+            FMM_CUDA_TRY(cudaMemcpyAsync(h->w_in.p, w, es * (size_t)h->n, cudaMemcpyHostToDevice, h->stream));
+            wd = h->w_in.p;
+        }
+    }
+    fmm::update_charges(h, qd, wd);
+    h->evaluated = false;
+    return FMM_OK;
+    API_END
+}
+
+int fmm_energy(fmm_handle h, const void *w, const void *q, const void *phi, double *out)
+{
+    if (!h) return fail(FMM_EINVAL, "fmm_energy: NULL handle");
+    if (!h->built) return fail(FMM_ESTATE, "fmm_energy: no successful fmm_build");
+    if (!w || !q || !phi || !out) return fail(FMM_EINVAL, "fmm_energy: NULL argument");
+    if (h->host_mem) return fail(FMM_EINVAL, "fmm_energy: device arrays only");
+    API_BEGIN
+    *out = fmm::energy(h, w, q, phi);
+    return FMM_OK;
+    API_END
+}
+
+int fmm_energy_adjoint(fmm_handle h, double gE, const void *w, const void *q, const void *phi, const void *grad,
+                       const void *psi, const void *gpsi, void *dq, void *dx, void *dw)
+{
+    if (!h) return fail(FMM_EINVAL, "fmm_energy_adjoint: NULL handle");
+    if (!h->built) return fail(FMM_ESTATE, "fmm_energy_adjoint: no successful fmm_build");
+    if (!w || !q || !phi || !psi) return fail(FMM_EINVAL, "fmm_energy_adjoint: NULL input");
+    if (dx && (!grad || !gpsi)) return fail(FMM_EINVAL, "fmm_energy_adjoint: dx needs grad and gpsi");
+    if (h->host_mem) return fail(FMM_EINVAL, "fmm_energy_adjoint: device arrays only");
+    API_BEGIN
+    fmm::energy_adjoint(h, gE, w, q, phi, grad, psi, gpsi, dq, dx, dw);
     return FMM_OK;
     API_END
 }

@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstring>
 #include <cstdio>
 #include <string>
 #include <vector>
@@ -160,11 +161,12 @@ struct fmm_ctx {
 
     // workspaces
     fmm::DevBuf box;
-    fmm::DevBuf x_in, q_in;             // staging of host inputs
+    fmm::DevBuf x_in, q_in, w_in;       // staging of host inputs
     fmm::DevBuf keys, keys2, idx, idx2; // Morton keys and permutation (radix sort ping-pong)
     fmm::DevBuf inv;                    // inverse permutation: sorted position of each input particle
     fmm::DevBuf pcell;                  // leaf cell of each sorted particle
     fmm::DevBuf cgeo;                   // per cell: geometric centre and 1 / width (double4)
+    fmm::DevBuf energy_buf;             // block sums of the weighted energy
     fmm::DevBuf hist, scan_tmp;
     fmm::DevBuf xs64, xs32, xs32lo;
     fmm::DevBuf c_level, c_anchor, c_begin, c_end, c_child, c_nchild, c_parent, c_xyz;
@@ -218,6 +220,10 @@ void m2l_tensor(fmm_ctx *h, float *L, const float *M);
 // p2p.cu
 void near_field(fmm_ctx *h, cudaStream_t s);  // P2P into h->near
 void combine_unsort(fmm_ctx *h, void *phi, void *grad);
+void update_charges(fmm_ctx *h, const void *q, const void *w);
+double energy(fmm_ctx *h, const void *w, const void *q, const void *phi);
+void energy_adjoint(fmm_ctx *h, double gE, const void *w, const void *q, const void *phi, const void *grad,
+                    const void *psi, const void *gpsi, void *dq, void *dx, void *dw);
 void direct_sum(fmm_ctx *h, const double *x, const double *q, int64_t n, const int64_t *tidx, int64_t nt,
                 double *phi, double *grad);
 

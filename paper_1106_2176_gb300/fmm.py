@@ -85,6 +85,9 @@ def lib():
     L.fmm_export_expansions.argtypes = [_vp, _vp, _vp]
     L.fmm_direct.argtypes = [_vp, _vp, _vp, i64, _vp, i64, _vp, _vp]
     L.fmm_morton_sort_noalloc.argtypes = [_vp, i64, i32, _vp, _vp, _vp]
+    L.fmm_update_charges.argtypes = [_vp, _vp, _vp]
+    L.fmm_energy.argtypes = [_vp, _vp, _vp, _vp, ctypes.POINTER(d)]
+    L.fmm_energy_adjoint.argtypes = [_vp, d, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
     L.fmm_destroy.argtypes = [_vp]
     L.fmm_last_error.argtypes = [_vp]
     L.fmm_last_error.restype = ctypes.c_char_p
@@ -190,6 +193,39 @@ class FMM:
         _check(lib().fmm_set_stream(self._h, _stream_ptr()), self._h)
         _check(lib().fmm_evaluate(self._h, _vp(phi.data_ptr()), _vp(grad.data_ptr())), self._h)
         return phi, grad
+
+    # -- weighted energy and its adjoint ---------------------------------------
+    def update_charges(self, q, w=None):
+        """New charges q (times w if given) on the built tree; same kind and dtype as at build."""
+        if self._host:
+            _check(lib().fmm_update_charges(self._h, _vp(q.ctypes.data), _vp(w.ctypes.data) if w is not None else None),
+                   self._h)
+            return
+        _check(lib().fmm_set_stream(self._h, _stream_ptr()), self._h)
+        _check(lib().fmm_update_charges(self._h, _vp(q.data_ptr()), _vp(w.data_ptr()) if w is not None else None),
+               self._h)
+
+    def energy(self, w, q, phi):
+        """1/2 sum w q phi (FP64), device tensors of the build's dtype."""
+        out = ctypes.c_double()
+        _check(lib().fmm_set_stream(self._h, _stream_ptr()), self._h)
+        _check(lib().fmm_energy(self._h, _vp(w.data_ptr()), _vp(q.data_ptr()), _vp(phi.data_ptr()), ctypes.byref(out)),
+               self._h)
+        return out.value
+
+    def energy_adjoint(self, gE, w, q, phi, grad, psi, gpsi, dq=True, dx=True, dw=True):
+        """(gE dE/dq, gE dE/dx, gE dE/dw) from the two evaluations (charges q, then w q)."""
+        import torch
+        n = self._n
+        mk = lambda shape: torch.empty(shape, dtype=self._torch_dtype, device=self._device)
+        oq = mk(n) if dq else None
+        ox = mk((n, 3)) if dx else None
+        ow = mk(n) if dw else None
+        ptr = lambda t: _vp(t.data_ptr()) if t is not None else None
+        _check(lib().fmm_set_stream(self._h, _stream_ptr()), self._h)
+        _check(lib().fmm_energy_adjoint(self._h, float(gE), ptr(w), ptr(q), ptr(phi), ptr(grad), ptr(psi), ptr(gpsi),
+                                        ptr(oq), ptr(ox), ptr(ow)), self._h)
+        return oq, ox, ow
 
     # -- introspection ---------------------------------------------------------
     def stats(self):
