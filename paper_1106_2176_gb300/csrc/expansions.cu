@@ -22,6 +22,8 @@
 //   L2P  phi = Re sum L~ conj(R(x^)) / w, grad from d_z R_n^m = R_{n-1}^m and
 //        (d_x + i d_y) R_n^m = -R_{n-1}^{m+1}, divided by w^2.
 #include <algorithm>
+#include <climits>
+#include <array>
 #include <type_traits>
 #include <cmath>
 #include <map>
@@ -591,7 +593,8 @@ __global__ void __launch_bounds__(M2L_CC_T) m2l_cc_k(int p, const M2LTile *__res
         blk[r] = T(0);
         tot[r] = A(0);
     }
-    const int e0 = st_off[td.octant], e1 = st_off[td.octant + 1];
+    // the octant's entries are sorted by reach: only a prefix can hit a cell
+    const int e0 = st_off[td.octant], e1 = e0 + st_off[9 + td.octant * (FMM_MAXLEVEL + 1) + l];
     int since = 0;
     for (int e = e0; e < e1; e++) {
         const int4 v = st[e];
@@ -662,71 +665,104 @@ __global__ void __launch_bounds__(M2L_CC_T) m2l_cc_k(int p, const M2LTile *__res
 }
 
 // ---------------------------------------------------------------------------
-// M2L between cells of different levels (explicit list, one block per target)
+// M2L between cells of different levels (explicit list).
+//
+// With s = max(w_A, w_B) and u = (c_A - c_B) / s, the scaled expansions
+// (M~_j = M_j / w_B^j, L~_n = L_n w_A^(n+1)) give
+//   L~_n^m += (w_A/s)^(n+1) (-1)^n sum_{j,k} (w_B/s)^j M~_j^k I_{j+n}^{k+m}(u).
+// Both ratios are powers of two no larger than 1 and |u| stays above the
+// acceptance distance, so nothing overflows in FP32 whatever the level gap
+// (terms of a cell many levels smaller than its partner underflow to zero,
+// their true size).  One block of four warps per target cell; warp w takes
+// the cell's pairs w, w + 4, ...: lanes 0..Q-1 build one column m of I(u)
+// each, the warp gathers the source's M~, then lane o owns outputs o and
+// o + 32 of the triangle.  The four warp sums are added in warp order.
 // ---------------------------------------------------------------------------
+constexpr int M2LX_W = 4;
+
+// Column m of I_n^m(u), n = m .. Q-1, computed in C and written as T to
+// full complex storage: I_m^m = (2m-1)!! (x + iy)^m / r^(2m+1), then the
+// three-term recurrence in n; orders -m from I_n^-m = (-1)^m conj(I_n^m).
+template <class C, class T>
+__device__ void irregular_col(int Q, int m, C x, C y, C z, T *sI)
+{
+    const C r2 = x * x + y * y + z * z, ir2 = C(1) / r2;
+    const C sg = (m & 1) ? C(-1) : C(1);
+    auto put = [&](int n, C cr, C ci) {
+        sI[2 * (n * n + n + m)] = (T)cr;
+        sI[2 * (n * n + n + m) + 1] = (T)ci;
+        if (m) {
+            sI[2 * (n * n + n - m)] = (T)(sg * cr);
+            sI[2 * (n * n + n - m) + 1] = (T)(-sg * ci);
+        }
+    };
+    C pr = sqrt(ir2), pi = C(0);
+    for (int k = 1; k <= m; k++) {
+        const C f = C(2 * k - 1) * ir2;
+        const C a = (pr * x - pi * y) * f, b = (pr * y + pi * x) * f;
+        pr = a;
+        pi = b;
+    }
+    put(m, pr, pi);
+    if (m + 1 >= Q) return;
+    const C f1 = C(2 * m + 1) * z * ir2;
+    C p2r = pr, p2i = pi, p1r = pr * f1, p1i = pi * f1;
+    put(m + 1, p1r, p1i);
+    for (int n = m + 2; n < Q; n++) {
+        const C a = C(2 * n - 1) * z, b = C((n + m - 1) * (n - m - 1));
+        const C cr = (a * p1r - b * p2r) * ir2, ci = (a * p1i - b * p2i) * ir2;
+        put(n, cr, ci);
+        p2r = p1r;
+        p2i = p1i;
+        p1r = cr;
+        p1i = ci;
+    }
+}
+
 template <class T>
-__global__ void __launch_bounds__(64) m2lx_k(int p, int nc, const int *__restrict__ ptr, const int *__restrict__ src,
-                                             const int4 *__restrict__ xyz, const T *__restrict__ M, T *__restrict__ L)
+__global__ void __launch_bounds__(32 * M2LX_W) m2lx_k(int p, int nc, const int *__restrict__ ptr,
+                                                      const int *__restrict__ src, const int4 *__restrict__ xyz,
+                                                      const T *__restrict__ M, T *__restrict__ L)
 {
     const int c = blockIdx.x;
     if (c >= nc) return;
     const int k0 = ptr[c], k1 = ptr[c + 1];
     if (k0 == k1) return;
     const int PP = p * p, Q = 2 * p - 1, ntri = p * (p + 1) / 2;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double *tre = reinterpret_cast<double *>(smem_raw);      // Q(Q+1)/2
-    double *tim = tre + Q * (Q + 1) / 2;
-    T *sI = reinterpret_cast<T *>(tim + Q * (Q + 1) / 2);   // Q*Q complex
-    T *sM = sI + 2 * Q * Q;                                  // PP complex
+    // per warp: its running sums (2 ntri FP64), I(u) (Q*Q complex), M~ (PP complex)
+    double *sA = reinterpret_cast<double *>(smem_raw) + (size_t)warp * 2 * ntri;
+    T *sI = reinterpret_cast<T *>(smem_raw + sizeof(double) * M2LX_W * 2 * ntri) + (size_t)warp * 2 * (Q * Q + PP);
+    T *sM = sI + 2 * Q * Q;
+    for (int o = lane; o < 2 * ntri; o += 32) sA[o] = 0.0;
     const int4 a = xyz[c];
     const long long WA = 1LL << (FMM_MAXLEVEL - a.w);
-    double accr[4] = {0, 0, 0, 0}, acci[4] = {0, 0, 0, 0};
-    for (int k = k0; k < k1; k++) {
+    for (int k = k0 + warp; k < k1; k += M2LX_W) {
         const int B = src[k];
         const int4 b = xyz[B];
         const long long WB = 1LL << (FMM_MAXLEVEL - b.w);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            // u = (c_A - c_B) / w_A in half-grid units; exact in FP64
-            const double sc = 1.0 / (double)(2 * WA);
-            const double ux = (double)(2LL * (a.x - b.x) + (WA - WB)) * sc;
-            const double uy = (double)(2LL * (a.y - b.y) + (WA - WB)) * sc;
-            const double uz = (double)(2LL * (a.z - b.z) + (WA - WB)) * sc;
-            irregular_tri<double>(Q, ux, uy, uz, tre, tim);
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i < Q * Q; i += blockDim.x) {
-            int n = (int)sqrtf((float)i);
-            while (n * n > i) n--;
-            while ((n + 1) * (n + 1) <= i) n++;
-            const int m = i - n * n - n, am = m < 0 ? -m : m;
-            double re = tre[tri(n, am)], im = tim[tri(n, am)];
-            if (m < 0) {
-                im = -im;
-                if (am & 1) {
-                    re = -re;
-                    im = -im;
-                }
-            }
-            sI[2 * i] = (T)re;
-            sI[2 * i + 1] = (T)im;
-        }
-        const double rho = (double)WB / (double)WA;
-        for (int i = threadIdx.x; i < PP; i += blockDim.x) {
+        const int dl = a.w - b.w;  // > 0: the target is the smaller cell
+        // u = (c_A - c_B) / max(w_A, w_B) from half-grid units; exact in FP64
+        const double sc = 1.0 / (double)(2 * (WA > WB ? WA : WB));
+        const double ux = (double)(2LL * (a.x - b.x) + (WA - WB)) * sc;
+        const double uy = (double)(2LL * (a.y - b.y) + (WA - WB)) * sc;
+        const double uz = (double)(2LL * (a.z - b.z) + (WA - WB)) * sc;
+        __syncwarp();
+        for (int m = lane; m < Q; m += 32) irregular_col<T, T>(Q, m, (T)ux, (T)uy, (T)uz, sI);
+        for (int i = lane; i < PP; i += 32) {
             int j = (int)sqrtf((float)i);
             while (j * j > i) j--;
             while ((j + 1) * (j + 1) <= i) j++;
             const int kk = i - j * j - j;
             T re, im;
             cget(M + (size_t)B * PP, j, kk, re, im);
-            const T s = (T)pow(rho, (double)j);
-            sM[2 * i] = re * s;
-            sM[2 * i + 1] = im * s;
+            const T f = dl < 0 ? (T)ldexp(1.0, dl * j) : T(1);  // (w_B / s)^j
+            sM[2 * i] = re * f;
+            sM[2 * i + 1] = im * f;
         }
-        __syncthreads();
-        for (int r = 0; r < 4; r++) {
-            const int o = threadIdx.x + r * blockDim.x;
-            if (o >= ntri) break;
+        __syncwarp();
+        for (int o = lane; o < ntri; o += 32) {
             int n, m;
             tri_inv(o, n, m);
             T sr = 0, si = 0;
@@ -734,25 +770,30 @@ __global__ void __launch_bounds__(64) m2lx_k(int p, int nc, const int *__restric
                 for (int kk = -j; kk <= j; kk++) {
                     const T mr = sM[2 * full(j, kk)], mi = sM[2 * full(j, kk) + 1];
                     const int fi = full(j + n, kk + m);
-                    sr += mr * sI[2 * fi] - mi * sI[2 * fi + 1];
-                    si += mr * sI[2 * fi + 1] + mi * sI[2 * fi];
+                    const T ir = sI[2 * fi], ii = sI[2 * fi + 1];
+                    sr += mr * ir - mi * ii;
+                    si += mr * ii + mi * ir;
                 }
-            if (n & 1) {
-                sr = -sr;
-                si = -si;
-            }
-            accr[r] += (double)sr;
-            acci[r] += (double)si;
+            double f = dl > 0 ? ldexp(1.0, -dl * (n + 1)) : 1.0;  // (w_A / s)^(n+1)
+            if (n & 1) f = -f;
+            sA[2 * o] += f * (double)sr;
+            sA[2 * o + 1] += f * (double)si;
         }
     }
+    __syncthreads();
+    if (warp) return;
+    const double *sA0 = reinterpret_cast<const double *>(smem_raw);
     T *Lc = L + (size_t)c * PP;
-    for (int r = 0; r < 4; r++) {
-        const int o = threadIdx.x + r * blockDim.x;
-        if (o >= ntri) break;
+    for (int o = lane; o < ntri; o += 32) {
         int n, m;
         tri_inv(o, n, m);
-        Lc[re_idx(n, m)] += (T)accr[r];
-        if (m) Lc[im_idx(n, m)] += (T)acci[r];
+        double sr = 0, si = 0;
+        for (int w = 0; w < M2LX_W; w++) {
+            sr += sA0[(size_t)w * 2 * ntri + 2 * o];
+            si += sA0[(size_t)w * 2 * ntri + 2 * o + 1];
+        }
+        Lc[re_idx(n, m)] += (T)sr;
+        if (m) Lc[im_idx(n, m)] += (T)si;
     }
 }
 
@@ -955,6 +996,11 @@ int m2l_tile_size(fmm_ctx *h)
 // rejected). Offsets are bounded by the largest coordinate difference of two
 // existing cells of one level, so a tiny theta stays small on shallow trees
 // and on deep chains of a few cells alike. Rebuilt only when the bound grows.
+static int stencil_reach(const std::array<int, 4> &v)
+{
+    return std::max(std::abs(v[0]), std::max(std::abs(v[1]), std::abs(v[2])));
+}
+
 void stencil_update(fmm_ctx *h)
 {
     const double c = h->cmac;
@@ -981,12 +1027,26 @@ void stencil_update(fmm_ctx *h)
                     h->st_host.insert(h->st_host.end(), {vx, vy, vz, id});
                 }
         h->st_off[o + 1] = (int)(h->st_host.size() / 4);
+        // shortest offsets first (stable; the vector ids keep their numbering):
+        // a level whose cells span at most E lattice steps reaches only the
+        // entries with max(|vx|, |vy|, |vz|) <= E, a prefix of the octant
+        std::vector<std::array<int, 4>> eo((size_t)(h->st_off[o + 1] - h->st_off[o]));
+        for (size_t i = 0; i < eo.size(); i++)
+            for (int k = 0; k < 4; k++) eo[i][k] = h->st_host[4 * ((size_t)h->st_off[o] + i) + k];
+        std::stable_sort(eo.begin(), eo.end(), [](const std::array<int, 4> &a, const std::array<int, 4> &b) {
+            return stencil_reach(a) < stencil_reach(b);
+        });
+        for (size_t i = 0; i < eo.size(); i++)
+            for (int k = 0; k < 4; k++) h->st_host[4 * ((size_t)h->st_off[o] + i) + k] = eo[i][k];
     }
     h->nV = nv;
     const int ne = h->st_off[8];
-    std::vector<int> buf(4 * (size_t)ne + 9);
+    std::vector<int> buf(4 * (size_t)ne + 9 + 8 * (FMM_MAXLEVEL + 1));
     std::copy(h->st_host.begin(), h->st_host.end(), buf.begin());
     for (int o = 0; o < 9; o++) buf[4 * (size_t)ne + o] = h->st_off[o];
+    for (int o = 0; o < 8; o++)
+        for (int l = 0; l <= FMM_MAXLEVEL; l++)
+            buf[4 * (size_t)ne + 9 + o * (FMM_MAXLEVEL + 1) + l] = h->st_off[o + 1] - h->st_off[o];
     h->st_dev.ensure(sizeof(int) * buf.size());
     FMM_CUDA_TRY(cudaMemcpy(h->st_dev.p, buf.data(), sizeof(int) * buf.size(), cudaMemcpyHostToDevice));
     h->st_R = R;
@@ -997,6 +1057,26 @@ void stencil_update(fmm_ctx *h)
             for (int vz = -R; vz <= R; vz++)
                 if (!(3.0 < c * ((double)vx * vx + (double)vy * vy + (double)vz * vz))) near++;
     h->p2p_cap_hint = near;
+}
+
+void stencil_levels(fmm_ctx *h, cudaStream_t s)
+{
+    const int ne = h->st_off[8];
+    std::vector<int> cnt(8 * (FMM_MAXLEVEL + 1));
+    for (int o = 0; o < 8; o++)
+        for (int l = 0; l <= FMM_MAXLEVEL; l++) {
+            // no extent known: every entry; an empty level (-1): none
+            const int E = l < (int)h->lvl_ext.size() ? h->lvl_ext[l] : INT_MAX;
+            int e = h->st_off[o];
+            while (e < h->st_off[o + 1]) {
+                const int *v = &h->st_host[4 * (size_t)e];
+                if (std::max(std::abs(v[0]), std::max(std::abs(v[1]), std::abs(v[2]))) > E) break;
+                e++;
+            }
+            cnt[o * (FMM_MAXLEVEL + 1) + l] = e - h->st_off[o];
+        }
+    int *dst = reinterpret_cast<int *>(h->st_dev.as<char>() + sizeof(int) * (4 * (size_t)ne + 9));
+    FMM_CUDA_TRY(cudaMemcpyAsync(dst, cnt.data(), sizeof(int) * cnt.size(), cudaMemcpyHostToDevice, s));
 }
 
 // R_n^m(t_o) for the 8 child offsets t_o = (c_child - c_parent) / w_parent
@@ -1179,14 +1259,14 @@ static void far_field_t(fmm_ctx *h, const P4 *xs, const T *rtab)
         }
     }
     if (h->n_m2lx > 0) {
-        size_t smem = sizeof(double) * (size_t)Q * (Q + 1) + sizeof(T) * 2 * ((size_t)Q * Q + PP);
+        size_t smem = sizeof(T) * M2LX_W * 2 * ((size_t)Q * Q + PP) + sizeof(double) * M2LX_W * 2 * ntri;
         static size_t set_x[2] = {0, 0};
         size_t &ss = set_x[sizeof(T) == 8];
         if (smem > ss) {
             FMM_CUDA_TRY(cudaFuncSetAttribute(m2lx_k<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             ss = smem;
         }
-        m2lx_k<T><<<nc, 64, smem, s>>>(p, nc, h->m2lx_ptr.as<int>(), h->m2lx_src.as<int>(), h->c_xyz.as<int4>(), M, L);
+        m2lx_k<T><<<nc, 32 * M2LX_W, smem, s>>>(p, nc, h->m2lx_ptr.as<int>(), h->m2lx_src.as<int>(), h->c_xyz.as<int4>(), M, L);
         count_launch(h);
         check_launch("m2l irregular");
     }

@@ -139,6 +139,7 @@ struct fmm_ctx {
     int engine_used = 0;
     int overlap = 1;  // far and near field on concurrent streams
     int lattice_extent = 0;  // largest same-level coordinate difference of existing cells
+    std::vector<int> lvl_ext;  // per level: the same, -1 for an empty level
     int ncells = 0, depth = 0, nleaves = 0;
     std::vector<int> lvl_start;  // cells of level l are [lvl_start[l], lvl_start[l+1])
     int64_t n_p2p = 0, n_m2lx = 0, n_m2l_implicit = 0, n_interactions = 0;
@@ -210,6 +211,9 @@ void scan_exclusive_u32(fmm_ctx *h, const unsigned *in, unsigned *out, int64_t c
 // expansions.cu
 void operators_init(fmm_ctx *h);  // R tables of M2M / L2L
 void stencil_update(fmm_ctx *h);  // same-level M2L stencil for the current tree depth
+// per (octant, level): how many of the octant's entries (shortest first) can
+// reach a cell of that level in the current tree; written after the offsets
+void stencil_levels(fmm_ctx *h, cudaStream_t s);
 void far_field(fmm_ctx *h);       // P2M, M2M, M2L, L2L, L2P into h->far
 
 // m2l_tc.cu

@@ -35,6 +35,10 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <tuple>
 
 #include "fmm_internal.cuh"
 
@@ -336,8 +340,8 @@ __global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
         pz = a.z >> sh;
     }
     const LevelDesc LD = ld[l];
-    const int e0 = st_off[td.octant], e1 = st_off[td.octant + 1];
-    const int nv = e1 - e0;
+    // the octant's entries are sorted by reach: only a prefix can hit a cell
+    const int e0 = st_off[td.octant], nv = st_off[9 + td.octant * (FMM_MAXLEVEL + 1) + l];
     const int nunits = nv * KB;
     const int ngroups = (nv + C::GV - 1) / C::GV;
 
@@ -658,11 +662,29 @@ static void build_irregular_full(int Q, double x, double y, double z, std::vecto
     }
 }
 
+// The operator image depends only on p and the stencil, which the MAC
+// constant and the stencil bound fix (vectors are numbered in a fixed order):
+// handles with the same three share one host image, built once per process.
+static std::mutex g_img_mu;
+static std::map<std::tuple<int, double, int>, std::shared_ptr<const std::vector<unsigned char>>> g_img_cache;
+
 void tensor_tables_update(fmm_ctx *h)
 {
     const TcShape sh = tc_shape(h->p);
     if (!sh.NP) return;
     if (h->ttab_nv == h->nV && h->ttab.p) return;
+    const auto key = std::make_tuple(h->p, h->cmac, h->st_R);
+    {
+        std::lock_guard<std::mutex> lk(g_img_mu);
+        auto it = g_img_cache.find(key);
+        if (it != g_img_cache.end()) {
+            h->ttab.ensure(it->second->size());
+            FMM_CUDA_TRY(cudaMemcpy(h->ttab.p, it->second->data(), it->second->size(), cudaMemcpyHostToDevice));
+            h->ttab_stride = (size_t)tc_shape(h->p).KB * 2 * tc_shape(h->p).NP * 128;
+            h->ttab_nv = h->nV;
+            return;
+        }
+    }
     const int p = h->p, PP = p * p, Q = 2 * p - 1, NP = sh.NP, KB = sh.KB;
     const size_t bbytes = (size_t)2 * NP * 128;  // one k-block of [T_hi ; T_lo]
     const size_t per_v = (size_t)KB * bbytes;
@@ -731,6 +753,8 @@ void tensor_tables_update(fmm_ctx *h)
     FMM_CUDA_TRY(cudaMemcpy(h->ttab.p, img.data(), img.size(), cudaMemcpyHostToDevice));
     h->ttab_stride = per_v;
     h->ttab_nv = h->nV;
+    std::lock_guard<std::mutex> lk(g_img_mu);
+    g_img_cache[key] = std::make_shared<const std::vector<unsigned char>>(std::move(img));
 }
 
 template <int NP, int KB>

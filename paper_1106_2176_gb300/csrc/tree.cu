@@ -1041,14 +1041,18 @@ void tree_build(fmm_ctx *h, const void *x, const void *q, int64_t n, int dt)
         FMM_CUDA_TRY(cudaStreamSynchronize(s));
         h->nleaves = (int)*hp;
         int E = 0;
+        h->lvl_ext.assign(FMM_MAXLEVEL + 1, -1);
         for (int l = 0; l <= depth; l++)
             for (int d = 0; d < 3; d++)
-                if (hext[NE + 3 * l + d] >= hext[3 * l + d]) E = std::max(E, hext[NE + 3 * l + d] - hext[3 * l + d]);
+                if (hext[NE + 3 * l + d] >= hext[3 * l + d])
+                    h->lvl_ext[l] = std::max(h->lvl_ext[l], hext[NE + 3 * l + d] - hext[3 * l + d]);
+        for (int l = 0; l <= depth; l++) E = std::max(E, h->lvl_ext[l]);
         h->lattice_extent = E;
     }
 
     // 5. dual traversal
     stencil_update(h);
+    stencil_levels(h, s);
     long long K0 = (long long)std::ceil(3.0 / h->cmac);
     while (K0 > 0 && 3.0 < h->cmac * (double)(K0 - 1)) K0--;
     while (!(3.0 < h->cmac * (double)K0)) K0++;
