@@ -574,16 +574,20 @@ __global__ void __launch_bounds__(M2L_CC_T) m2l_cc_k(int p, const M2LTile *__res
     T *sI = reinterpret_cast<T *>(smem_raw);                 // QQ complex
     T *sM = sI + 2 * QQ;                                     // tile_max * PP complex
     int *ssrc = reinterpret_cast<int *>(sM + 2 * (size_t)tile_max * PP);
-    int *spos = ssrc + tile_max;                             // 3 per target
+    int *spos = ssrc + tile_max;                             // 5 per target
 
-    const int l = td.level, sh = FMM_MAXLEVEL - l;
+    const int l = td.level;
+    // per target: lattice position, level and octant (a pooled tile mixes them)
     if ((int)threadIdx.x < td.count) {
         const int4 a = xyz[tgt[td.start + threadIdx.x]];
-        spos[3 * threadIdx.x + 0] = a.x >> sh;
-        spos[3 * threadIdx.x + 1] = a.y >> sh;
-        spos[3 * threadIdx.x + 2] = a.z >> sh;
+        const int sh = FMM_MAXLEVEL - a.w;
+        int *sp = spos + 5 * threadIdx.x;
+        sp[0] = a.x >> sh;
+        sp[1] = a.y >> sh;
+        sp[2] = a.z >> sh;
+        sp[3] = a.w;
+        sp[4] = (sp[0] & 1) | ((sp[1] & 1) << 1) | ((sp[2] & 1) << 2);
     }
-    const LevelDesc LD = ld[l];
     const int nout = td.count * ntri;
     using A = typename Acc<T>::type;
     T blk[2 * M2L_CC_ACC];
@@ -593,15 +597,18 @@ __global__ void __launch_bounds__(M2L_CC_T) m2l_cc_k(int p, const M2LTile *__res
         blk[r] = T(0);
         tot[r] = A(0);
     }
-    // the octant's entries are sorted by reach: only a prefix can hit a cell
-    const int e0 = st_off[td.octant], e1 = e0 + st_off[9 + td.octant * (FMM_MAXLEVEL + 1) + l];
+    // the set's entries are sorted by reach: only a prefix can hit a cell
+    const int e0 = st_off[td.octant], e1 = e0 + st_off[10 + td.octant * (FMM_MAXLEVEL + 1) + l];
     int since = 0;
     for (int e = e0; e < e1; e++) {
         const int4 v = st[e];
         __syncthreads();
-        if ((int)threadIdx.x < td.count)
-            ssrc[threadIdx.x] = level_lookup(LD, map_pool, anchor, l, spos[3 * threadIdx.x] + v.x,
-                                             spos[3 * threadIdx.x + 1] + v.y, spos[3 * threadIdx.x + 2] + v.z);
+        if ((int)threadIdx.x < td.count) {
+            const int *sp = spos + 5 * threadIdx.x;
+            ssrc[threadIdx.x] = ((v.w >> (16 + sp[4])) & 1)
+                                    ? level_lookup(ld[sp[3]], map_pool, anchor, sp[3], sp[0] + v.x, sp[1] + v.y, sp[2] + v.z)
+                                    : -1;
+        }
         if ((int)threadIdx.x < Q) irregular_column(Q, (int)threadIdx.x, -(double)v.x, -(double)v.y, -(double)v.z, sI);
         __syncthreads();
         for (int i = threadIdx.x; i < td.count * PP; i += blockDim.x) {
@@ -794,6 +801,171 @@ __global__ void __launch_bounds__(32 * M2LX_W) m2lx_k(int p, int nc, const int *
         }
         Lc[re_idx(n, m)] += (T)sr;
         if (m) Lc[im_idx(n, m)] += (T)si;
+    }
+}
+
+// FP32 form of the same for p = 2 .. 10, p fixed at compile time.  Eight warps
+// per target cell; each warp loads the source ids and cells of 32 of its pairs
+// at once (lane i: pair i), prefetches the next source's M~ while it computes
+// the current pair, and keeps its running sums as FP32 (hi, lo) pairs.
+constexpr int M2LX_FW = 8;
+
+__device__ __forceinline__ void m2lx_two_sum(float &hi, float &lo, float b)
+{
+    const float s = hi + b;
+    const float bb = s - hi;
+    lo += (hi - (s - bb)) + (b - bb);
+    hi = s;
+}
+
+template <int P>
+__global__ void __launch_bounds__(32 * M2LX_FW, 2) m2lx_f_k(int nc, const int *__restrict__ ptr,
+                                                         const int *__restrict__ src, const int4 *__restrict__ xyz,
+                                                         const float *__restrict__ M, float *__restrict__ L)
+{
+    constexpr int PP = P * P, Q = 2 * P - 1, NT = P * (P + 1) / 2, NO = (NT + 31) / 32, NM = (PP + 31) / 32;
+    __shared__ float2 sIa[M2LX_FW][Q * Q];
+    __shared__ float2 sMa[M2LX_FW][PP];
+    __shared__ double red[M2LX_FW][2 * NT];
+    const int c = blockIdx.x;
+    if (c >= nc) return;
+    const int k0 = ptr[c], k1 = ptr[c + 1];
+    if (k0 == k1) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float2 *sI = sIa[warp], *sM = sMa[warp];
+    const int4 a = xyz[c];
+    // this lane's entries of M~ in full complex storage: i = lane + 32 r = j^2 + j + k
+    int mre[NM], mim[NM], mj[NM];
+    float msr[NM], msi[NM];
+#pragma unroll
+    for (int r = 0; r < NM; r++) {
+        const int i = lane + 32 * r;
+        int j = 0;
+        while ((j + 1) * (j + 1) <= i) j++;
+        const int k = i - j * j - j, ak = k < 0 ? -k : k;
+        mj[r] = j;
+        mre[r] = i < PP ? j * j + (ak ? 2 * ak - 1 : 0) : 0;
+        mim[r] = i < PP && ak ? j * j + 2 * ak : -1;
+        // X_j^-k = (-1)^k conj(X_j^k)
+        const float sg = (k < 0 && (ak & 1)) ? -1.f : 1.f;
+        msr[r] = sg;
+        msi[r] = k < 0 ? -sg : sg;
+    }
+    // this lane's outputs o = lane + 32 r of the (n, m) triangle
+    int on[NO], om[NO];
+#pragma unroll
+    for (int r = 0; r < NO; r++) {
+        const int o = lane + 32 * r;
+        int n = 0;
+        while ((n + 1) * (n + 2) / 2 <= o) n++;
+        on[r] = o < NT ? n : -1;
+        om[r] = o - n * (n + 1) / 2;
+    }
+    float ahr[NO], alr[NO], ahi[NO], ali[NO];
+#pragma unroll
+    for (int r = 0; r < NO; r++) ahr[r] = alr[r] = ahi[r] = ali[r] = 0.f;
+
+    const int npair = k1 - k0 > warp ? (k1 - k0 - warp + M2LX_FW - 1) / M2LX_FW : 0;
+    for (int t0 = 0; t0 < npair; t0 += 32) {
+        const int nb = min(32, npair - t0);
+        int Bl = 0;
+        int4 bl = make_int4(0, 0, 0, 0);
+        if (lane < nb) {
+            Bl = src[k0 + warp + M2LX_FW * (t0 + lane)];
+            bl = xyz[Bl];
+        }
+        float pre[NM], pim[NM];
+        auto fetch = [&](int B) {
+#pragma unroll
+            for (int r = 0; r < NM; r++) {
+                pre[r] = lane + 32 * r < PP ? M[(size_t)B * PP + mre[r]] : 0.f;
+                pim[r] = lane + 32 * r < PP && mim[r] >= 0 ? M[(size_t)B * PP + mim[r]] : 0.f;
+            }
+        };
+        fetch(__shfl_sync(0xffffffffu, Bl, 0));
+        for (int t = 0; t < nb; t++) {
+            const int bw = __shfl_sync(0xffffffffu, bl.w, t);
+            const int bx = __shfl_sync(0xffffffffu, bl.x, t), by = __shfl_sync(0xffffffffu, bl.y, t),
+                      bz = __shfl_sync(0xffffffffu, bl.z, t);
+            const int dl = a.w - bw;  // > 0: the target is the smaller cell
+            const int lmin = a.w < bw ? a.w : bw;
+            const long long WA = 1LL << (FMM_MAXLEVEL - a.w), WB = 1LL << (FMM_MAXLEVEL - bw);
+            // u = (c_A - c_B) / max(w_A, w_B): integers below 2^24 times a power of two, exact in FP32
+            const float sc = ldexpf(1.f, -(FMM_MAXLEVEL + 1 - lmin));
+            const float ux = (float)(2LL * (a.x - bx) + (WA - WB)) * sc;
+            const float uy = (float)(2LL * (a.y - by) + (WA - WB)) * sc;
+            const float uz = (float)(2LL * (a.z - bz) + (WA - WB)) * sc;
+            __syncwarp();
+            if (lane < Q) irregular_col<float, float>(Q, lane, ux, uy, uz, reinterpret_cast<float *>(sI));
+#pragma unroll
+            for (int r = 0; r < NM; r++)
+                if (lane + 32 * r < PP) {
+                    const float f = dl < 0 ? ldexpf(1.f, dl * mj[r]) : 1.f;  // (w_B / s)^j
+                    sM[lane + 32 * r] = make_float2(pre[r] * msr[r] * f, pim[r] * msi[r] * f);
+                }
+            const int tn = t + 1 < nb ? t + 1 : t;
+            const int Bn = __shfl_sync(0xffffffffu, Bl, tn);
+            if (t + 1 < nb) fetch(Bn);
+            __syncwarp();
+#pragma unroll 1
+            for (int r = 0; r < NO; r++) {
+                if (on[r] < 0) continue;
+                const int n = on[r], m = om[r];
+                float sr = 0.f, si = 0.f;
+#pragma unroll
+                for (int j = 0; j < P; j++) {
+                    const float2 *Ij = sI + (j + n) * (j + n) + (j + n) + m;
+#pragma unroll
+                    for (int k = -j; k <= j; k++) {
+                        const float2 mv = sM[j * j + j + k];
+                        const float2 iv = Ij[k];
+                        sr = fmaf(mv.x, iv.x, sr);
+                        sr = fmaf(-mv.y, iv.y, sr);
+                        si = fmaf(mv.x, iv.y, si);
+                        si = fmaf(mv.y, iv.x, si);
+                    }
+                }
+                float f = dl > 0 ? ldexpf(1.f, -dl * (n + 1)) : 1.f;  // (w_A / s)^(n+1)
+                if (n & 1) f = -f;
+                m2lx_two_sum(ahr[r], alr[r], f * sr);
+                m2lx_two_sum(ahi[r], ali[r], f * si);
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < NO; r++)
+        if (on[r] >= 0) {
+            const int o = lane + 32 * r;
+            red[warp][2 * o] = (double)ahr[r] + (double)alr[r];
+            red[warp][2 * o + 1] = (double)ahi[r] + (double)ali[r];
+        }
+    __syncthreads();
+    if (warp) return;
+    float *Lc = L + (size_t)c * PP;
+#pragma unroll
+    for (int r = 0; r < NO; r++) {
+        if (on[r] < 0) continue;
+        const int o = lane + 32 * r;
+        double sr = 0, si = 0;
+        for (int w = 0; w < M2LX_FW; w++) {
+            sr += red[w][2 * o];
+            si += red[w][2 * o + 1];
+        }
+        Lc[re_idx(on[r], om[r])] += (float)sr;
+        if (om[r]) Lc[im_idx(on[r], om[r])] += (float)si;
+    }
+}
+
+static bool m2lx_f_launch(int p, int nc, const int *ptr, const int *src, const int4 *xyz, const float *M, float *L,
+                          cudaStream_t s)
+{
+    switch (p) {
+#define FMM_M2LX_CASE(PV) \
+    case PV: m2lx_f_k<PV><<<nc, 32 * M2LX_FW, 0, s>>>(nc, ptr, src, xyz, M, L); return true;
+        FMM_M2LX_CASE(2) FMM_M2LX_CASE(3) FMM_M2LX_CASE(4) FMM_M2LX_CASE(5) FMM_M2LX_CASE(6)
+        FMM_M2LX_CASE(7) FMM_M2LX_CASE(8) FMM_M2LX_CASE(9) FMM_M2LX_CASE(10)
+#undef FMM_M2LX_CASE
+    default: return false;
     }
 }
 
@@ -1009,7 +1181,7 @@ void stencil_update(fmm_ctx *h)
     if (R <= h->st_R && h->st_dev.p) return;
     std::map<std::tuple<int, int, int>, int> vid;
     int nv = 0;
-    h->st_off.assign(9, 0);
+    h->st_off.assign(10, 0);
     h->st_host.clear();
     for (int o = 0; o < 8; o++) {
         const int ox = o & 1, oy = (o >> 1) & 1, oz = (o >> 2) & 1;
@@ -1039,14 +1211,34 @@ void stencil_update(fmm_ctx *h)
         for (size_t i = 0; i < eo.size(); i++)
             for (int k = 0; k < 4; k++) h->st_host[4 * ((size_t)h->st_off[o] + i) + k] = eo[i][k];
     }
+    if (nv > 0xffff) throw Error{FMM_EINVAL, "M2L stencil: more than 65535 distinct vectors"};
     h->nV = nv;
-    const int ne = h->st_off[8];
-    std::vector<int> buf(4 * (size_t)ne + 9 + 8 * (FMM_MAXLEVEL + 1));
+    // the union of the 8 stencils (each vector once, shortest first) for
+    // tiles that pool cells of every octant; bits 16 + o of the fourth int
+    // say whether octant o's stencil holds the vector (all 8 bits for the
+    // entries of the per-octant lists)
+    const int ne8 = h->st_off[8];
+    std::vector<std::array<int, 4>> un((size_t)nv);
+    for (int e = 0; e < ne8; e++) {
+        int *v = &h->st_host[4 * (size_t)e];
+        const int o = (int)(std::upper_bound(h->st_off.begin(), h->st_off.begin() + 9, e) - h->st_off.begin()) - 1;
+        std::array<int, 4> &u = un[(size_t)v[3]];
+        if (!(u[3] >> 16)) u = {v[0], v[1], v[2], v[3]};
+        u[3] |= 1 << (16 + o);
+        v[3] |= 0xff << 16;
+    }
+    std::stable_sort(un.begin(), un.end(), [](const std::array<int, 4> &a, const std::array<int, 4> &b) {
+        return stencil_reach(a) < stencil_reach(b);
+    });
+    for (const auto &u : un) h->st_host.insert(h->st_host.end(), {u[0], u[1], u[2], u[3]});
+    h->st_off[9] = (int)(h->st_host.size() / 4);
+    const int ne = h->st_off[9];
+    std::vector<int> buf(4 * (size_t)ne + 10 + 9 * (FMM_MAXLEVEL + 1));
     std::copy(h->st_host.begin(), h->st_host.end(), buf.begin());
-    for (int o = 0; o < 9; o++) buf[4 * (size_t)ne + o] = h->st_off[o];
-    for (int o = 0; o < 8; o++)
+    for (int o = 0; o < 10; o++) buf[4 * (size_t)ne + o] = h->st_off[o];
+    for (int o = 0; o < 9; o++)
         for (int l = 0; l <= FMM_MAXLEVEL; l++)
-            buf[4 * (size_t)ne + 9 + o * (FMM_MAXLEVEL + 1) + l] = h->st_off[o + 1] - h->st_off[o];
+            buf[4 * (size_t)ne + 10 + o * (FMM_MAXLEVEL + 1) + l] = h->st_off[o + 1] - h->st_off[o];
     h->st_dev.ensure(sizeof(int) * buf.size());
     FMM_CUDA_TRY(cudaMemcpy(h->st_dev.p, buf.data(), sizeof(int) * buf.size(), cudaMemcpyHostToDevice));
     h->st_R = R;
@@ -1061,22 +1253,31 @@ void stencil_update(fmm_ctx *h)
 
 void stencil_levels(fmm_ctx *h, cudaStream_t s)
 {
-    const int ne = h->st_off[8];
-    std::vector<int> cnt(8 * (FMM_MAXLEVEL + 1));
-    for (int o = 0; o < 8; o++)
-        for (int l = 0; l <= FMM_MAXLEVEL; l++) {
-            // no extent known: every entry; an empty level (-1): none
-            const int E = l < (int)h->lvl_ext.size() ? h->lvl_ext[l] : INT_MAX;
+    const int ne = h->st_off[9];
+    std::vector<int> cnt(9 * (FMM_MAXLEVEL + 1));
+    int ecum = -1;
+    for (int l = 0; l <= FMM_MAXLEVEL; l++) {
+        // no extent known: every entry; an empty level (-1): none
+        const int E = l < (int)h->lvl_ext.size() ? h->lvl_ext[l] : INT_MAX;
+        ecum = std::max(ecum, E);  // pooled tiles hold cells of this level and above it
+        for (int o = 0; o < 9; o++) {
+            const int Eo = o < 8 ? E : ecum;
             int e = h->st_off[o];
             while (e < h->st_off[o + 1]) {
                 const int *v = &h->st_host[4 * (size_t)e];
-                if (std::max(std::abs(v[0]), std::max(std::abs(v[1]), std::abs(v[2]))) > E) break;
+                if (std::max(std::abs(v[0]), std::max(std::abs(v[1]), std::abs(v[2]))) > Eo) break;
                 e++;
             }
             cnt[o * (FMM_MAXLEVEL + 1) + l] = e - h->st_off[o];
         }
-    int *dst = reinterpret_cast<int *>(h->st_dev.as<char>() + sizeof(int) * (4 * (size_t)ne + 9));
+    }
+    int *dst = const_cast<int *>(stencil_offsets(h)) + 10;
     FMM_CUDA_TRY(cudaMemcpyAsync(dst, cnt.data(), sizeof(int) * cnt.size(), cudaMemcpyHostToDevice, s));
+}
+
+const int *stencil_offsets(fmm_ctx *h)
+{
+    return reinterpret_cast<const int *>(h->st_dev.as<char>() + sizeof(int4) * h->st_off[9]);
 }
 
 // R_n^m(t_o) for the 8 child offsets t_o = (c_child - c_parent) / w_parent
@@ -1237,13 +1438,13 @@ static void far_field_t(fmm_ctx *h, const P4 *xs, const T *rtab)
     // M2L
     FMM_CUDA_TRY(cudaEventRecord(ev[4], s));
     FMM_CUDA_TRY(cudaMemsetAsync(L, 0, sizeof(T) * (size_t)nc * PP, s));
-    const int *st_off = reinterpret_cast<const int *>(h->st_dev.as<char>() + sizeof(int4) * h->st_off[8]);
+    const int *st_off = stencil_offsets(h);
     if (h->depth >= 2) {
         if (std::is_same<T, float>::value && h->engine_used == FMM_M2L_TENSOR) {
             m2l_tensor(h, reinterpret_cast<float *>(L), reinterpret_cast<const float *>(M));
         } else {
             const int tile = m2l_tile_size(h);
-            size_t smem = sizeof(T) * 2 * ((size_t)Q * Q + (size_t)tile * PP) + sizeof(int) * 4 * tile;
+            size_t smem = sizeof(T) * 2 * ((size_t)Q * Q + (size_t)tile * PP) + sizeof(int) * 6 * tile;
             static size_t set_smem[2] = {0, 0};
             size_t &ss = set_smem[sizeof(T) == 8];
             if (smem > ss) {
@@ -1258,7 +1459,17 @@ static void far_field_t(fmm_ctx *h, const P4 *xs, const T *rtab)
             check_launch("m2l");
         }
     }
+    bool m2lx_done = false;
     if (h->n_m2lx > 0) {
+        if constexpr (std::is_same<T, float>::value)
+            m2lx_done = m2lx_f_launch(p, nc, h->m2lx_ptr.as<int>(), h->m2lx_src.as<int>(), h->c_xyz.as<int4>(),
+                                      reinterpret_cast<const float *>(M), reinterpret_cast<float *>(L), s);
+        if (m2lx_done) {
+            count_launch(h);
+            check_launch("m2l irregular");
+        }
+    }
+    if (h->n_m2lx > 0 && !m2lx_done) {
         size_t smem = sizeof(T) * M2LX_W * 2 * ((size_t)Q * Q + PP) + sizeof(double) * M2LX_W * 2 * ntri;
         static size_t set_x[2] = {0, 0};
         size_t &ss = set_x[sizeof(T) == 8];

@@ -91,7 +91,8 @@ struct LevelDesc {
     long long map_off;   // offset of a dense map (8^l int32) in the map pool, or -1
 };
 
-// M2L tile: up to TILE target cells of one level and one octant
+// M2L tile: up to TILE target cells of one level and one octant, or (octant
+// 8) cells of the sparse levels of every octant, level their largest level
 struct M2LTile {
     int start;   // first entry in the target list
     int count;
@@ -149,8 +150,8 @@ struct fmm_ctx {
 
     // stencil of same-level M2L (host copy and device copy)
     int nV = 0;                 // distinct translation vectors over all octants
-    std::vector<int> st_off;    // st_off[o] .. st_off[o+1]: entries of octant o
-    std::vector<int> st_host;   // 4 ints per entry: vx, vy, vz (source - target), vector id
+    std::vector<int> st_off;    // st_off[o] .. st_off[o+1]: entries of octant o; [8] .. [9]: their union
+    std::vector<int> st_host;   // 4 ints per entry: vx, vy, vz (source - target), id | octant mask << 16
     fmm::DevBuf st_dev;         // int4 per entry
     int st_R = 0;               // offsets |v_k| <= st_R are in the stencil
     fmm::DevBuf rtab64, rtab32; // R_n^m(t_o), 8 child offsets, full complex storage of degree < p
@@ -214,6 +215,9 @@ void stencil_update(fmm_ctx *h);  // same-level M2L stencil for the current tree
 // per (octant, level): how many of the octant's entries (shortest first) can
 // reach a cell of that level in the current tree; written after the offsets
 void stencil_levels(fmm_ctx *h, cudaStream_t s);
+// device copy of the stencil: entries (int4), then 10 offsets, then per set
+// (octants 0..7, union 8) and level the number of entries that can reach
+const int *stencil_offsets(fmm_ctx *h);
 void far_field(fmm_ctx *h);       // P2M, M2M, M2L, L2L, L2P into h->far
 
 // m2l_tc.cu

@@ -330,18 +330,23 @@ __global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
     const int row = tid & 127, grp = (tid >> 7) & 1;  // worker: target row and group
     const M2LTile td = tiles[blockIdx.x];
     const int PP = p * p;
-    const int l = td.level, sh = FMM_MAXLEVEL - l;
-    int px = 0, py = 0, pz = 0, cell = -1;
+    const int l = td.level;
+    // this row's cell, its level, lattice position and octant (a pooled tile
+    // mixes levels and octants)
+    int px = 0, py = 0, pz = 0, cell = -1, rl = l, ro = 0;
     if (worker && row < td.count) {
         cell = tgt[td.start + row];
         const int4 a = xyz[cell];
+        rl = a.w;
+        const int sh = FMM_MAXLEVEL - rl;
         px = a.x >> sh;
         py = a.y >> sh;
         pz = a.z >> sh;
+        ro = (px & 1) | ((py & 1) << 1) | ((pz & 1) << 2);
     }
-    const LevelDesc LD = ld[l];
-    // the octant's entries are sorted by reach: only a prefix can hit a cell
-    const int e0 = st_off[td.octant], nv = st_off[9 + td.octant * (FMM_MAXLEVEL + 1) + l];
+    const LevelDesc LD = ld[rl];
+    // the set's entries are sorted by reach: only a prefix can hit a cell
+    const int e0 = st_off[td.octant], nv = st_off[10 + td.octant * (FMM_MAXLEVEL + 1) + l];
     const int nunits = nv * KB;
     const int ngroups = (nv + C::GV - 1) / C::GV;
 
@@ -418,7 +423,7 @@ __global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
                 }
                 const int4 v = st[e0 + u / KB];
                 mbar_arrive_tx(&b_full[c], C::B_RAW);
-                bulk_g2s(smem_u32(bops + c * C::B_RAW), ttab + ((size_t)v.w * KB + u % KB) * C::B_RAW, C::B_RAW,
+                bulk_g2s(smem_u32(bops + c * C::B_RAW), ttab + ((size_t)(v.w & 0xffff) * KB + u % KB) * C::B_RAW, C::B_RAW,
                          &b_full[c]);
                 issued = u + 1;
             }
@@ -449,13 +454,13 @@ __global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
             int r = -1;
             if (cell >= 0) {
                 const int4 v = st[e0 + (2 * j + g) / KB];
-                const int x = px + v.x, y = py + v.y, z = pz + v.z, side = 1 << l;
-                if (x >= 0 && y >= 0 && z >= 0 && x < side && y < side && z < side) {
+                const int x = px + v.x, y = py + v.y, z = pz + v.z, side = 1 << rl;
+                if (((v.w >> (16 + ro)) & 1) && x >= 0 && y >= 0 && z >= 0 && x < side && y < side && z < side) {
                     if (dense) {
                         cp_async4(slot, map_pool + LD.map_off + (long long)morton3((uint32_t)x, (uint32_t)y, (uint32_t)z));
                         return;
                     }
-                    r = level_lookup(LD, map_pool, anchor, l, x, y, z);
+                    r = level_lookup(LD, map_pool, anchor, rl, x, y, z);
                 }
             }
             if (dense) cp_async4(slot, &g_no_cell);
@@ -695,7 +700,7 @@ void tensor_tables_update(fmm_ctx *h)
     auto im_i = [](int n, int m) { return n * n + 2 * m; };
     const int ne = h->st_off[8];
     for (int e = 0; e < ne; e++) {
-        const int vx = h->st_host[4 * e], vy = h->st_host[4 * e + 1], vz = h->st_host[4 * e + 2], id = h->st_host[4 * e + 3];
+        const int vx = h->st_host[4 * e], vy = h->st_host[4 * e + 1], vz = h->st_host[4 * e + 2], id = h->st_host[4 * e + 3] & 0xffff;
         if (seen[id]) continue;
         seen[id] = 1;
         build_irregular_full(Q, -(double)vx, -(double)vy, -(double)vz, Ire, Iim);
@@ -776,7 +781,7 @@ static void launch_tc(fmm_ctx *h, float *L, const float *M)
         FMM_CUDA_TRY(cudaFuncSetAttribute(m2l_tc_k<NP, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
         attr = true;
     }
-    const int *st_off = reinterpret_cast<const int *>(h->st_dev.as<char>() + sizeof(int4) * h->st_off[8]);
+    const int *st_off = stencil_offsets(h);
     const int *ntiles = reinterpret_cast<const int *>(h->m2l_misc.as<unsigned>() + 24 * (FMM_MAXLEVEL + 1));
     int *err = reinterpret_cast<int *>(h->m2l_misc.as<unsigned>() + 24 * (FMM_MAXLEVEL + 1) + 4);
     FMM_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));

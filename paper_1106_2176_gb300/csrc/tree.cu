@@ -818,16 +818,50 @@ __global__ void oct_count_k(int c0, int nc, const int *__restrict__ level, const
     atomicAdd(&grp[l * 8 + o], 1u);
 }
 
-// One thread: group offsets and tile descriptors, levels 2..depth. Within a
-// level the tiles of the 8 octant groups are interleaved (tile k of octant 0,
-// tile k of octant 1, ...): each group is in Morton order, so tiles that run
-// at the same time cover one compact region and share sources in L2.
-__global__ void tiles_k(int depth, int tile, const unsigned *__restrict__ grp, unsigned *__restrict__ goff,
-                        M2LTile *__restrict__ tiles, int *__restrict__ ntiles)
+// One thread: group offsets and tile descriptors, levels 2..depth.
+// Levels with at most pool_max cells would leave the tiles of their octant
+// groups mostly empty: their cells (every octant) are pooled, level by level,
+// at the front of the target list and cut into tiles of octant 8, whose
+// level is the largest level among their cells. Within a denser level the
+// tiles of the 8 octant groups are interleaved (tile k of octant 0, tile k of
+// octant 1, ...), so that tiles running at the same time cover one compact
+// region and share sources in L2.
+__global__ void tiles_k(int depth, int tile, int pool_max, const unsigned *__restrict__ grp,
+                        unsigned *__restrict__ goff, M2LTile *__restrict__ tiles, int *__restrict__ ntiles)
 {
     unsigned run = 0;
     int nt = 0;
+    auto level_cells = [&](int l) {
+        unsigned c = 0;
+        for (int o = 0; o < 8; o++) c += grp[l * 8 + o];
+        return c;
+    };
     for (int l = 2; l <= depth; l++) {
+        if (level_cells(l) > (unsigned)pool_max) continue;
+        for (int o = 0; o < 8; o++) {
+            goff[l * 8 + o] = run;
+            run += grp[l * 8 + o];
+        }
+    }
+    const unsigned pool = run;
+    int lv = 2;
+    for (unsigned t = 0; t < pool; t += tile) {
+        const unsigned cnt = min((unsigned)tile, pool - t), last = t + cnt - 1;
+        // level of the tile's last cell: the pooled levels are in ascending order
+        while (lv < depth) {
+            const unsigned c = level_cells(lv);
+            if (c <= (unsigned)pool_max && c > 0 && last < goff[lv * 8] + c) break;
+            lv++;
+        }
+        M2LTile d;
+        d.start = (int)t;
+        d.count = (int)cnt;
+        d.level = lv;
+        d.octant = 8;
+        tiles[nt++] = d;
+    }
+    for (int l = 2; l <= depth; l++) {
+        if (level_cells(l) <= (unsigned)pool_max) continue;
         unsigned kmax = 0;
         for (int o = 0; o < 8; o++) {
             const unsigned c = grp[l * 8 + o];
@@ -1205,7 +1239,7 @@ void tree_build(fmm_ctx *h, const void *x, const void *q, int64_t n, int dt)
             oct_count_k<<<nblocks(nt, TB), TB, 0, s>>>(c0, ncells, h->c_level.as<int>(), h->c_anchor.as<uint64_t>(), grp);
             count_launch(h);
         }
-        tiles_k<<<1, 1, 0, s>>>(depth, tile, grp, goff, h->m2l_tiles.as<M2LTile>(), ntiles);
+        tiles_k<<<1, 1, 0, s>>>(depth, tile, 4 * tile, grp, goff, h->m2l_tiles.as<M2LTile>(), ntiles);
         count_launch(h);
         if (nt > 0) {
             oct_scatter_k<<<nblocks(nt, TB), TB, 0, s>>>(c0, ncells, h->c_level.as<int>(), h->c_anchor.as<uint64_t>(),
@@ -1292,7 +1326,7 @@ void tree_export(fmm_ctx *h, uint64_t *keys, int32_t *perm, int32_t *level, uint
         if (m > 0) {
             cnt.ensure(sizeof(unsigned) * (m + 1));
             off.ensure(sizeof(unsigned) * (m + 1));
-            int *st_off = reinterpret_cast<int *>(h->st_dev.as<char>() + sizeof(int4) * h->st_off[8]);
+            const int *st_off = stencil_offsets(h);
             stencil_pairs_k<<<nblocks(m, 128), 128, 0, s>>>(c0, nc, h->c_level.as<int>(), h->c_xyz.as<int4>(),
                                                             h->c_anchor.as<uint64_t>(), h->lvl_desc.as<LevelDesc>(),
                                                             h->map_pool.as<int>(), h->st_dev.as<int4>(), st_off,
@@ -1308,7 +1342,7 @@ void tree_export(fmm_ctx *h, uint64_t *keys, int32_t *perm, int32_t *level, uint
         const int64_t ntot = nimp + h->n_m2lx;
         pairs.ensure(sizeof(int2) * (size_t)std::max<int64_t>(ntot, 1));
         if (m > 0 && nimp > 0) {
-            int *st_off = reinterpret_cast<int *>(h->st_dev.as<char>() + sizeof(int4) * h->st_off[8]);
+            const int *st_off = stencil_offsets(h);
             stencil_pairs_k<<<nblocks(m, 128), 128, 0, s>>>(c0, nc, h->c_level.as<int>(), h->c_xyz.as<int4>(),
                                                             h->c_anchor.as<uint64_t>(), h->lvl_desc.as<LevelDesc>(),
                                                             h->map_pool.as<int>(), h->st_dev.as<int4>(), st_off,
