@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=100_000)
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg (profiling runs)")
+    ap.add_argument("--batch", type=int, default=512, help="systems in the batched-evaluation leg (0 = skip)")
+    ap.add_argument("--diff-n", type=int, default=1_000_000, help="particles in the differentiation leg (0 = skip)")
     ap.add_argument("--overlap", type=int, default=0, choices=[0, 1],
                     help="0 (default): far and near field in turn on one stream, so the P2P events time the kernel "
                          "alone; 1: on concurrent streams")
@@ -238,6 +240,123 @@ def run_e2e(a, x, q, N, ncrit, world, dist, dev):
     return e2e
 
 
+def run_batch(a, dev):
+    """Many small systems in one CUDA-graph launch against one launch sequence
+    per system: sizes log-uniform in [1e3, 1e5], even systems a uniform cube,
+    odd ones a Plummer sphere, charges U[-1,1], FP32, p = 6, theta = 0.5, mixed
+    precision, ncrit tuned per size bucket. Error of each system: relative L2
+    on 32 sampled targets against the library's FP64 direct sum."""
+    import numpy as np
+    import torch
+    from paper_1106_2176_gb300 import inputs
+    from paper_1106_2176_gb300.batch import FMMBatch
+
+    rng = np.random.default_rng(5)
+    systems = []
+    for k in range(a.batch):
+        n = int(10 ** rng.uniform(3, 5))
+        x = inputs.uniform_cube(n, 1000 + k)[0] if k % 2 == 0 else inputs.plummer(n, 1000 + k)[0]
+        q = rng.uniform(-1, 1, n)
+        systems.append((torch.tensor(x.astype(np.float32), device=dev), torch.tensor(q.astype(np.float32), device=dev)))
+    b = FMMBatch(systems, p=6, theta=0.5, ncrit="auto", precision="mixed", streams=8)
+
+    def timed(fn, reps):
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return sum(ts) / len(ts)
+
+    for _ in range(max(a.warmup, 3)):
+        b.evaluate_each()
+    k0 = sum(f.stats()["kernel_launches"] for f in b.handles)
+    t_each = timed(b.evaluate_each, max(a.steps, 3))
+    launches = (sum(f.stats()["kernel_launches"] for f in b.handles) - k0) // max(a.steps, 3)
+    b.capture()
+    for _ in range(max(a.warmup, 3)):
+        b.replay()
+    t_graph = timed(b.replay, max(a.steps, 3))
+    e_phi = e_grad = 0.0
+    for (x, q), f, (phi, grad) in zip(systems, b.handles, b.out):
+        n = x.shape[0]
+        t = torch.as_tensor(inputs.sample_targets(n, 32, seed=n), device=dev)
+        pd, gd = f.direct(x, q, t)
+        e_phi = max(e_phi, float(torch.linalg.norm(phi[t].double() - pd) / torch.linalg.norm(pd)))
+        e_grad = max(e_grad, float(torch.linalg.norm(grad[t].double() - gd) / torch.linalg.norm(gd)))
+    out = {"workload": "%d systems, n log-uniform in [1e3, 1e5], half uniform cube, half Plummer, q U[-1,1], FP32, "
+                       "p=6, theta=0.5, mixed precision" % a.batch,
+           "systems": a.batch, "particles": b.particles, "graph_ms": t_graph, "per_system_launches_ms": t_each,
+           "speedup": t_each / t_graph, "particles_per_s": b.particles / (t_graph / 1000.0),
+           "max_rel_l2_phi": e_phi, "max_rel_l2_grad": e_grad, "error_targets_per_system": 32,
+           "ncrit_by_half_decade": {str(k / 2): v for k, v in (b.ncrit_by_bucket or {}).items()},
+           "streams": b.nstreams, "kernel_launches_per_replay": launches}
+    b.close()
+    return out
+
+
+def run_diff(a, dev):
+    """Weighted energy E = 1/2 sum w q phi and its gradients through the
+    autograd Function: N Plummer sphere, q U[0,1]/N, w N(0,1), FP32, p = 8,
+    theta = 0.5, mixed precision. One step = forward (build, evaluate, energy)
+    + backward (new charges w q, evaluate, adjoint). Error: relative L2 of
+    dE/dx, dE/dq on 1,024 sampled particles against the library's FP64 direct
+    sums of phi and psi."""
+    import numpy as np
+    import torch
+    from paper_1106_2176_gb300 import FMM, inputs
+    from paper_1106_2176_gb300.autograd import fmm_energy
+
+    n = a.diff_n
+    x, _ = inputs.plummer(n, 7)
+    rng = np.random.default_rng(107)
+    q = rng.uniform(0, 1, n) / n
+    w = rng.standard_normal(n)
+    xt = torch.tensor(x.astype(np.float32), device=dev, requires_grad=True)
+    qt = torch.tensor(q.astype(np.float32), device=dev, requires_grad=True)
+    wt = torch.tensor(w.astype(np.float32), device=dev, requires_grad=True)
+
+    def step():
+        xt.grad = qt.grad = wt.grad = None
+        E = fmm_energy(xt, qt, wt, p=8, theta=0.5, ncrit=64, precision="mixed")
+        E.backward()
+        return E
+
+    for _ in range(max(a.warmup, 3)):
+        step()
+    ts = []
+    for _ in range(max(a.steps, 3)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        step()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = sum(ts) / len(ts)
+    t = torch.as_tensor(inputs.sample_targets(n, 1024, seed=8), device=dev)
+    x64, q64, w64 = xt.detach().double(), qt.detach().double(), wt.detach().double()
+    g = FMM(n, p=8, theta=0.5, ncrit=64, precision="fp64")
+    phi, gphi = g.direct(x64, q64, t)
+    psi, gpsi = g.direct(x64, w64 * q64, t)
+    g.close()
+    dq = 0.5 * (w64[t] * phi + psi)
+    dx = 0.5 * q64[t, None] * (w64[t, None] * gphi + gpsi)
+
+    def rel(u, v):
+        return float(torch.linalg.norm(u.double() - v) / torch.linalg.norm(v))
+
+    return {"workload": "weighted energy and its gradients, Plummer sphere N=%d, q U[0,1]/N, w N(0,1), FP32, p=8, "
+                        "theta=0.5, ncrit=64, mixed precision" % n,
+            "N": n, "ms_per_step": ms, "particles_per_s": n / (ms / 1000.0),
+            "step": "forward (build, evaluate, energy) + backward (charges w q, evaluate, adjoint)",
+            "rel_l2_dE_dx": rel(xt.grad[t], dx), "rel_l2_dE_dq": rel(qt.grad[t], dq), "error_targets": 1024}
+
+
 def main():
     a = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -400,8 +519,15 @@ def main():
                                                                              "m2l_engine")},
                "roofline": roofline, "phase_rooflines": phases_roof, "cpu_baseline": cpu, "e2e": e2e,
                "gpu_launches": launches, "clocks": ck}
-        print(json.dumps(out), flush=True)
     f.close()
+    if rank == 0:
+        if world == 1 and (a.batch > 0 or a.diff_n > 0):
+            del xt, qt, phi, grad
+            torch.cuda.empty_cache()
+            out["batch"] = run_batch(a, dev)
+        if world == 1 and a.diff_n > 0:
+            out["differentiation"] = run_diff(a, dev)
+        print(json.dumps(out), flush=True)
     if dist:
         dist.barrier()
         dist.destroy_process_group()

@@ -9,15 +9,50 @@ grad phi; the expansions are recomputed rather than stored.
     E = fmm_energy(x, q, w, p=8, theta=0.5, ncrit=64, precision="mixed")
     E.backward()   # x.grad, q.grad, w.grad
 """
+import threading
+
 import torch
 
 from .fmm import FMM
+
+# Handles (and their device workspaces) are reused across calls with the same
+# size and parameters: a forward pass takes one, its backward pass returns it.
+_pool = {}
+_pool_lock = threading.Lock()
+POOL_MAX = 4  # idle handles kept per key
+
+
+def _take(n, p, theta, ncrit, precision, device):
+    key = (int(n), int(p), float(theta), int(ncrit), precision, device)
+    with _pool_lock:
+        free = _pool.get(key)
+        if free:
+            return key, free.pop()
+    return key, FMM(n, p=p, theta=theta, ncrit=ncrit, precision=precision)
+
+
+def _give(key, f):
+    with _pool_lock:
+        free = _pool.setdefault(key, [])
+        if len(free) < POOL_MAX:
+            free.append(f)
+            return
+    f.close()
+
+
+def clear_pool():
+    """Close every idle pooled handle."""
+    with _pool_lock:
+        hs = [f for free in _pool.values() for f in free]
+        _pool.clear()
+    for f in hs:
+        f.close()
 
 
 class FMMEnergy(torch.autograd.Function):
     @staticmethod
     def forward(ctx, x, q, w, p, theta, ncrit, precision):
-        f = FMM(x.shape[0], p=p, theta=theta, ncrit=ncrit, precision=precision)
+        ctx.key, f = _take(x.shape[0], p, theta, ncrit, precision, str(x.device))
         x, q, w = x.contiguous(), q.contiguous(), w.contiguous()
         f.build(x, q)
         phi, grad = f.evaluate()
@@ -35,7 +70,7 @@ class FMMEnergy(torch.autograd.Function):
         dq, dx, dw = f.energy_adjoint(float(gE), w, q, phi, grad, psi, gpsi, dq=ctx.needs_input_grad[1],
                                       dx=ctx.needs_input_grad[0], dw=ctx.needs_input_grad[2])
         ctx.f = None
-        f.close()
+        _give(ctx.key, f)
         return dx, dq, dw, None, None, None, None
 
 

@@ -2,7 +2,8 @@
 replay gives bitwise the results of one launch sequence per system, and each
 system stays within the error budget against the FP64 direct sum. Batching
 workload in small: sizes log-uniform in [10^3, 2 10^4], half uniform cube and
-half Plummer, charges U[-1,1], p = 6, theta = 0.5, mixed precision."""
+half Plummer, charges U[-1,1], p = 6, theta = 0.5, mixed precision; one leaf
+size for all, or one per size bucket from the tuner."""
 import numpy as np
 import pytest
 
@@ -14,7 +15,8 @@ from gpu_common import ensure_built, rel, torch_cuda
 pytestmark = pytest.mark.gpu
 
 
-def test_graph_batch_matches_per_system_launches_and_direct_sum():
+@pytest.mark.parametrize("ncrit", [64, "auto"])
+def test_graph_batch_matches_per_system_launches_and_direct_sum(ncrit):
     torch = torch_cuda()
     ensure_built()
     from paper_1106_2176_gb300.batch import FMMBatch
@@ -27,7 +29,9 @@ def test_graph_batch_matches_per_system_launches_and_direct_sum():
         x32, q32 = x.astype(np.float32), q.astype(np.float32)
         host.append((x32, q32))
         systems.append((torch.tensor(x32, device="cuda"), torch.tensor(q32, device="cuda")))
-    b = FMMBatch(systems, p=6, theta=0.5, ncrit=64, precision="mixed", streams=8)
+    b = FMMBatch(systems, p=6, theta=0.5, ncrit=ncrit, precision="mixed", streams=8)
+    if ncrit == "auto":
+        assert b.ncrit_by_bucket and set(b.ncrit_by_bucket.values()) <= {32, 64, 128, 256}
     ref = [(p.clone(), g.clone()) for p, g in b.evaluate_each()]
     torch.cuda.synchronize()
     for p, g in b.out:
