@@ -467,6 +467,19 @@ def main():
         f64.close()
         del p64, g64
 
+    # the same build through the dual traversal (fast path off), for the
+    # comparison of the two ways of making the lists
+    uni = {"used": bool(st1["uniform_path"]), "build_ms": phase["ms_build"]}
+    if st1["uniform_path"]:
+        f.set_uniform_path(False)
+        bt = []
+        for _ in range(3):
+            f.build(xt, qt)
+            bt.append(f.stats()["ms_build"])
+        f.set_uniform_path(True)
+        f.build(xt, qt)
+        uni["build_ms_traversal"] = min(bt)
+
     # end to end through the C ABI with pinned host buffers
     e2e = None
     if not a.no_e2e:
@@ -518,7 +531,7 @@ def main():
                                                                              "n_m2l_irregular", "n_interactions",
                                                                              "m2l_engine")},
                "roofline": roofline, "phase_rooflines": phases_roof, "cpu_baseline": cpu, "e2e": e2e,
-               "gpu_launches": launches, "clocks": ck}
+               "gpu_launches": launches, "clocks": ck, "uniform_path": uni}
     f.close()
     if rank == 0:
         if world == 1 and (a.batch > 0 or a.diff_n > 0):

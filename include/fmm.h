@@ -90,6 +90,8 @@ typedef struct {
     double ms_build, ms_evaluate;
     double ms_p2m, ms_m2m, ms_m2l, ms_l2l, ms_l2p, ms_p2p, ms_combine;
     int64_t kernel_launches; /* kernels this handle launched since creation */
+    int32_t uniform_path;    /* 1 if the last build took the full-octree fast path */
+    int32_t reserved;
 } fmm_stats;
 
 /* Sizes of the arrays fmm_export_tree writes. */
@@ -123,6 +125,20 @@ FMM_API int fmm_set_m2l_engine(fmm_handle h, int engine);
  * in turn on one device; this is an addition. Returns FMM_EINVAL for a NULL
  * handle or on not 0/1. */
 FMM_API int fmm_set_overlap(fmm_handle h, int on);
+
+/* Uniform-tree fast path (Sec. 5: for uniform distributions the cells of a
+ * level and the interaction lists follow from the Morton index alone).
+ * on = 1 (default): when the cell build yields a full octree (every leaf on
+ * the deepest level L and every level full), fmm_build skips the dual
+ * traversal: the P2P rows of the leaves come from the near-field lattice
+ * stencil of level L (the offsets the MAC rejects, cut at the lattice
+ * boundary, ancestors checked as the traversal does), there are no pairs
+ * across levels, and the implicit same-level M2L pairs are counted in closed
+ * form. The lists, and so the results, are identical to the traversal's.
+ * on = 0: always traverse. Takes effect at the next build; fmm_stats
+ * .uniform_path says which path the last build took. Returns FMM_EINVAL for a
+ * NULL handle or on not 0/1. */
+FMM_API int fmm_set_uniform_path(fmm_handle h, int on);
 
 /* Use the given cudaStream_t (NULL = legacy default stream) for all work. */
 FMM_API int fmm_set_stream(fmm_handle h, void *stream);

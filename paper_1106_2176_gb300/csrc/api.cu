@@ -81,7 +81,7 @@ fmm_ctx::~fmm_ctx()
     fmm::DevBuf *bufs[] = {&st_dev, &rtab64, &rtab32, &m2m_mat, &l2l_mat, &ttab, &box, &x_in, &q_in, &w_in, &keys, &keys2, &idx, &inv, &pcell, &cgeo, &energy_buf,
                            &idx2, &hist, &scan_tmp, &xs64, &xs32, &xs32lo, &c_level, &c_anchor, &c_begin, &c_end, &c_child,
                            &c_nchild, &c_parent, &c_xyz, &split_cnt, &split_off, &split_bnd, &leaves, &frontA,
-                           &frontB, &p2p_pairs, &m2lx_pairs, &pair_keys, &pair_keys2, &pair_vals, &pair_vals2,
+                           &frontB, &p2p_pairs, &m2lx_pairs, &near_dev, &pair_keys, &pair_keys2, &pair_vals, &pair_vals2,
                            &p2p_ptr, &p2p_src, &p2p_runs, &p2p_nrun, &m2lx_ptr, &m2lx_src, &row_cnt, &counters, &lvl_desc, &map_pool,
                            &m2l_tgt, &m2l_tiles, &m2l_misc, &msplit, &Mexp, &Lexp, &far, &near, &out_phi, &out_grad,
                            &direct_part};
@@ -229,6 +229,14 @@ int fmm_set_overlap(fmm_handle h, int on)
     if (!h) return fail(FMM_EINVAL, "fmm_set_overlap: NULL handle");
     if (on != 0 && on != 1) return fail(FMM_EINVAL, "fmm_set_overlap: on must be 0 or 1");
     h->overlap = on;
+    return FMM_OK;
+}
+
+int fmm_set_uniform_path(fmm_handle h, int on)
+{
+    if (!h) return fail(FMM_EINVAL, "fmm_set_uniform_path: NULL handle");
+    if (on != 0 && on != 1) return fail(FMM_EINVAL, "fmm_set_uniform_path: on must be 0 or 1");
+    h->uniform_req = on != 0;
     return FMM_OK;
 }
 
@@ -406,6 +414,7 @@ int fmm_get_stats(fmm_handle h, fmm_stats *out)
         out->async_error = e;
     }
     out->kernel_launches = h->launches;
+    out->uniform_path = h->uniform_used ? 1 : 0;
     cudaEvent_t *ev = h->tm.ev;
     if (h->built) out->ms_build = ev_ms(ev[0], ev[1]);
     if (h->evaluated) {

@@ -146,6 +146,8 @@ struct fmm_ctx {
     int64_t n_p2p = 0, n_m2lx = 0, n_m2l_implicit = 0, n_interactions = 0;
     int ntiles_max = 0;
     int p2p_cap_hint = 0;       // near-field stencil size (P2P sources of a leaf in a uniform tree)
+    bool uniform_req = true;    // full octrees take the lattice-stencil lists (fmm_set_uniform_path)
+    bool uniform_used = false;  // the last build did
     double ms_build = 0;
 
     // stencil of same-level M2L (host copy and device copy)
@@ -176,6 +178,7 @@ struct fmm_ctx {
     fmm::DevBuf leaves;
     fmm::DevBuf frontA, frontB;
     fmm::DevBuf p2p_pairs, m2lx_pairs;
+    fmm::DevBuf near_dev;       // near-field stencil of the uniform fast path (int4)
     fmm::DevBuf pair_keys, pair_keys2, pair_vals, pair_vals2;
     fmm::DevBuf p2p_ptr, p2p_src, m2lx_ptr, m2lx_src, row_cnt;
     fmm::DevBuf p2p_runs, p2p_nrun;     // P2P sources merged into particle runs per target leaf

@@ -14,6 +14,7 @@
 // target's octant (the MAC accepts them and rejects their parents), so the M2L
 // kernels enumerate them through a per-level lattice lookup.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 
 #include "fmm_internal.cuh"
@@ -726,6 +727,40 @@ __global__ void row_max_k(int nc, const unsigned *__restrict__ cnt, unsigned *__
 
 constexpr int ROW_SORT_WARPS = 8, ROW_SORT_CAP = 1024;
 
+// Ascending bitonic sort of 256 keys held by one warp, lane l holding keys
+// 8 l .. 8 l + 7: partners 8 or more apart are exchanged with shuffles, the
+// others inside the lane's registers.
+__device__ __forceinline__ void warp_bitonic256(int (&v)[8], int lane)
+{
+#pragma unroll
+    for (int k = 2; k <= 256; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= 8) {
+#pragma unroll
+                for (int r = 0; r < 8; r++) {
+                    const int i = lane * 8 + r;
+                    const int y = __shfl_xor_sync(0xffffffffu, v[r], j >> 3);
+                    const bool up = (i & k) == 0, low = (i & j) == 0;
+                    v[r] = low == up ? min(v[r], y) : max(v[r], y);
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < 8; r++) {
+                    if (r & j) continue;
+                    const bool up = ((lane * 8 + r) & k) == 0;
+                    const int a = v[r], b = v[r | j];
+                    v[r] = up ? min(a, b) : max(a, b);
+                    v[r | j] = up ? max(a, b) : min(a, b);
+                }
+            }
+        }
+    }
+}
+
+// Each CSR row in ascending order, one warp per row: rows of up to 256
+// entries by a bitonic sort in registers, longer ones (up to ROW_SORT_CAP)
+// by exact ranks in shared memory.
 __global__ void __launch_bounds__(32 * ROW_SORT_WARPS) row_sort_k(int nc, const int *__restrict__ ptr, int *__restrict__ src)
 {
     __shared__ int sh[ROW_SORT_WARPS][ROW_SORT_CAP];
@@ -734,6 +769,16 @@ __global__ void __launch_bounds__(32 * ROW_SORT_WARPS) row_sort_k(int nc, const 
     if (r >= nc) return;
     const int b = ptr[r], len = ptr[r + 1] - b;
     if (len <= 1 || len > ROW_SORT_CAP) return;
+    if (len <= 256) {
+        int v[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) v[k] = lane * 8 + k < len ? src[b + lane * 8 + k] : INT_MAX;
+        warp_bitonic256(v, lane);
+#pragma unroll
+        for (int k = 0; k < 8; k++)
+            if (lane * 8 + k < len) src[b + lane * 8 + k] = v[k];
+        return;
+    }
     int *row = sh[w];
     for (int k = lane; k < len; k += 32) row[k] = src[b + k];
     __syncwarp();
@@ -743,6 +788,45 @@ __global__ void __launch_bounds__(32 * ROW_SORT_WARPS) row_sort_k(int nc, const 
         for (int t = 0; t < len; t++) rank += row[t] < e;
         src[b + rank] = e;
     }
+}
+
+// ---------------------------------------------------------------------------
+// uniform-tree fast path: on a full octree (every leaf on level L, every level
+// full) the traversal's P2P lists are the near-field lattice stencil of level
+// L, cut at the lattice boundary; cell id = first cell of level L + Morton
+// index of the lattice position.  A candidate pair is kept only if no pair of
+// ancestors is accepted, as in the traversal.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool near_pair_kept(int L, int px, int py, int pz, int qx, int qy, int qz, long long K0)
+{
+    for (int l = L - 1; l >= 1; l--) {
+        const int sh = L - l;
+        const long long ux = (qx >> sh) - (px >> sh), uy = (qy >> sh) - (py >> sh), uz = (qz >> sh) - (pz >> sh);
+        if (ux * ux + uy * uy + uz * uz >= K0) return false;
+    }
+    return true;
+}
+
+// write = false: row counts into cnt[c]; write = true: the rows at ptr[c]
+__global__ void near_rows_k(int ls, int le, int L, const int4 *__restrict__ xyz, const int4 *__restrict__ near,
+                            int nnear, long long K0, unsigned *__restrict__ cnt, const int *__restrict__ ptr,
+                            int *__restrict__ src, bool write)
+{
+    const int c = ls + blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= le) return;
+    const int sh = FMM_MAXLEVEL - L, side = 1 << L;
+    const int4 a = xyz[c];
+    const int px = a.x >> sh, py = a.y >> sh, pz = a.z >> sh;
+    int k = 0, base = write ? ptr[c] : 0;
+    for (int e = 0; e < nnear; e++) {
+        const int4 v = near[e];
+        const int qx = px + v.x, qy = py + v.y, qz = pz + v.z;
+        if (qx < 0 || qy < 0 || qz < 0 || qx >= side || qy >= side || qz >= side) continue;
+        if (!near_pair_kept(L, px, py, pz, qx, qy, qz, K0)) continue;
+        if (write) src[base + k] = ls + (int)morton3((uint32_t)qx, (uint32_t)qy, (uint32_t)qz);
+        k++;
+    }
+    if (!write) cnt[c] = (unsigned)k;
 }
 
 static int bits_for(int64_t v)
@@ -921,6 +1005,69 @@ __global__ void pcell_k(int nc, const int *__restrict__ nchild, const int *__res
 // ---------------------------------------------------------------------------
 // host orchestration
 // ---------------------------------------------------------------------------
+// number of x in [0, S) of parity par with 0 <= x + v < S
+static int64_t lattice_count(int64_t S, int par, int v)
+{
+    const int64_t lo = std::max<int64_t>(0, -v), hi = std::min<int64_t>(S, S - v);
+    if (hi <= lo) return 0;
+    return (hi + 1 - par) / 2 - (lo + 1 - par) / 2;
+}
+
+// Fast path of a full octree of depth L: P2P rows from the near-field stencil,
+// no pairs across levels, and the implicit same-level M2L pairs counted in
+// closed form (per level, octant and stencil vector, the cells of that octant
+// whose partner lies inside the lattice). Returns false (nothing done) when
+// the near stencil is longer than the row sort handles.
+static bool uniform_lists(fmm_ctx *h, long long K0, cudaStream_t s)
+{
+    const int L = h->depth, nc = h->ncells;
+    const int ls = h->lvl_start[L], le = h->lvl_start[L + 1];
+    const double c = h->cmac;
+    // offsets beyond the lattice side never land inside it
+    const int R = (int)std::min<long long>((long long)std::ceil(std::sqrt((double)K0)) + 1, (1LL << L) - 1);
+    std::vector<int> nv;
+    for (int vx = -R; vx <= R; vx++)
+        for (int vy = -R; vy <= R; vy++)
+            for (int vz = -R; vz <= R; vz++) {
+                const double d2 = (double)vx * vx + (double)vy * vy + (double)vz * vz;
+                if (3.0 < c * d2) continue;
+                if ((int)(nv.size() / 4) == ROW_SORT_CAP) return false;  // rows too long for the row sort
+                nv.insert(nv.end(), {vx, vy, vz, 0});
+            }
+    const int nn = (int)(nv.size() / 4);
+    h->near_dev.ensure(sizeof(int) * nv.size());
+    FMM_CUDA_TRY(cudaMemcpyAsync(h->near_dev.p, nv.data(), sizeof(int) * nv.size(), cudaMemcpyHostToDevice, s));
+    h->p2p_ptr.ensure(sizeof(int) * (size_t)(nc + 1));
+    h->row_cnt.ensure(sizeof(unsigned) * (size_t)(nc + 1));
+    FMM_CUDA_TRY(cudaMemsetAsync(h->row_cnt.p, 0, sizeof(unsigned) * (size_t)(nc + 1), s));
+    near_rows_k<<<nblocks(le - ls, 128), 128, 0, s>>>(ls, le, L, h->c_xyz.as<int4>(), h->near_dev.as<int4>(), nn, K0,
+                                                      h->row_cnt.as<unsigned>(), nullptr, nullptr, false);
+    count_launch(h);
+    scan_exclusive_u32(h, h->row_cnt.as<unsigned>(), reinterpret_cast<unsigned *>(h->p2p_ptr.as<int>()), nc + 1, nullptr, s);
+    unsigned *hp = h->hpin.as<unsigned>();
+    FMM_CUDA_TRY(cudaMemcpyAsync(hp, h->p2p_ptr.as<int>() + nc, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    FMM_CUDA_TRY(cudaStreamSynchronize(s));
+    h->n_p2p = (int64_t)*hp;
+    h->p2p_src.ensure(sizeof(int) * (size_t)std::max<int64_t>(h->n_p2p, 1));
+    near_rows_k<<<nblocks(le - ls, 128), 128, 0, s>>>(ls, le, L, h->c_xyz.as<int4>(), h->near_dev.as<int4>(), nn, K0,
+                                                      nullptr, h->p2p_ptr.as<int>(), h->p2p_src.as<int>(), true);
+    count_launch(h);
+    row_sort_k<<<nblocks(nc, ROW_SORT_WARPS), 32 * ROW_SORT_WARPS, 0, s>>>(nc, h->p2p_ptr.as<int>(), h->p2p_src.as<int>());
+    count_launch(h);
+    check_launch("uniform lists");
+    int64_t m2l = 0;
+    for (int l = 1; l <= L; l++)
+        for (int o = 0; o < 8; o++)
+            for (int e = h->st_off[o]; e < h->st_off[o + 1]; e++) {
+                const int *v = &h->st_host[4 * (size_t)e];
+                m2l += lattice_count(1LL << l, o & 1, v[0]) * lattice_count(1LL << l, (o >> 1) & 1, v[1]) *
+                       lattice_count(1LL << l, (o >> 2) & 1, v[2]);
+            }
+    h->n_m2l_implicit = m2l;
+    h->n_m2lx = 0;
+    return true;
+}
+
 void tree_build(fmm_ctx *h, const void *x, const void *q, int64_t n, int dt)
 {
     cudaStream_t s = h->stream;
@@ -1090,7 +1237,13 @@ void tree_build(fmm_ctx *h, const void *x, const void *q, int64_t n, int dt)
     long long K0 = (long long)std::ceil(3.0 / h->cmac);
     while (K0 > 0 && 3.0 < h->cmac * (double)(K0 - 1)) K0--;
     while (!(3.0 < h->cmac * (double)K0)) K0++;
-    {
+    // a full octree (all leaves on the deepest level, every level full) takes
+    // the lattice stencils instead of the traversal
+    bool full = h->uniform_req && depth >= 1 && depth <= 9 && h->nleaves == (1 << (3 * depth)) &&
+                (int64_t)ncells == (((int64_t)1 << (3 * (depth + 1))) - 1) / 7;
+    if (full) full = uniform_lists(h, K0, s);
+    h->uniform_used = full;
+    if (!full) {
         // the near-field stencil size bounds the P2P list of a leaf in a uniform tree
         const size_t per = (size_t)h->p2p_cap_hint + 8;
         size_t cap_p2p = std::max<size_t>(1024, std::min((size_t)h->nleaves * per, (size_t)h->nleaves * h->nleaves));
@@ -1169,7 +1322,7 @@ void tree_build(fmm_ctx *h, const void *x, const void *q, int64_t n, int dt)
     }
 
     // 6. CSR lists
-    pairs_to_csr(h, h->p2p_pairs.as<int2>(), h->n_p2p, h->p2p_ptr, h->p2p_src, s);
+    if (!full) pairs_to_csr(h, h->p2p_pairs.as<int2>(), h->n_p2p, h->p2p_ptr, h->p2p_src, s);
     pairs_to_csr(h, h->m2lx_pairs.as<int2>(), h->n_m2lx, h->m2lx_ptr, h->m2lx_src, s);
     h->p2p_runs.ensure(sizeof(int2) * (size_t)std::max<int64_t>(h->n_p2p, 1));
     h->p2p_nrun.ensure(sizeof(int) * (size_t)ncells);

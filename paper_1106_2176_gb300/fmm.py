@@ -45,7 +45,8 @@ class fmm_stats(ctypes.Structure):
                 ("ms_build", ctypes.c_double), ("ms_evaluate", ctypes.c_double),
                 ("ms_p2m", ctypes.c_double), ("ms_m2m", ctypes.c_double), ("ms_m2l", ctypes.c_double),
                 ("ms_l2l", ctypes.c_double), ("ms_l2p", ctypes.c_double), ("ms_p2p", ctypes.c_double),
-                ("ms_combine", ctypes.c_double), ("kernel_launches", ctypes.c_int64)]
+                ("ms_combine", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
+                ("uniform_path", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class fmm_tree_sizes(ctypes.Structure):
@@ -77,6 +78,7 @@ def lib():
     L.fmm_set_m2l_engine.argtypes = [_vp, i32]
     L.fmm_set_overlap.argtypes = [_vp, i32]
     L.fmm_set_stream.argtypes = [_vp, _vp]
+    L.fmm_set_uniform_path.argtypes = [_vp, ctypes.c_int]
     L.fmm_build.argtypes = [_vp, _vp, _vp, i64, i32]
     L.fmm_evaluate.argtypes = [_vp, _vp, _vp]
     L.fmm_get_stats.argtypes = [_vp, ctypes.POINTER(fmm_stats)]
@@ -115,13 +117,15 @@ def _stream_ptr():
 class FMM:
     """Handle of one FMM configuration (N, p, theta, ncrit) on the current GPU."""
 
-    def __init__(self, N, p=8, theta=0.5, ncrit=64, precision="fp64", m2l_engine="auto", overlap=True):
+    def __init__(self, N, p=8, theta=0.5, ncrit=64, precision="fp64", m2l_engine="auto", overlap=True,
+                 uniform_path=True):
         self._h = _vp()
         _check(lib().fmm_create(int(N), int(p), float(theta), int(ncrit), ctypes.byref(self._h)))
         self.N, self.p, self.theta, self.ncrit = int(N), int(p), float(theta), int(ncrit)
         self.set_precision(precision)
         self.set_m2l_engine(m2l_engine)
         self.set_overlap(overlap)
+        self.set_uniform_path(uniform_path)
         self._n = 0
         self._dtype = None
         self._host = False
@@ -140,6 +144,11 @@ class FMM:
         """True: far and near field run concurrently; False: in turn (per-phase times)."""
         _check(lib().fmm_set_overlap(self._h, 1 if on else 0), self._h)
         self.overlap = bool(on)
+
+    def set_uniform_path(self, on):
+        """True: full octrees skip the traversal (lattice-stencil lists); False: always traverse."""
+        _check(lib().fmm_set_uniform_path(self._h, 1 if on else 0), self._h)
+        self.uniform_path = bool(on)
 
     # -- the two calls of the method ------------------------------------------
     def build(self, x, q):

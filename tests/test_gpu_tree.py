@@ -11,17 +11,17 @@ from gpu_common import ensure_built, torch_cuda
 pytestmark = pytest.mark.gpu
 
 
-def gpu_tree(x, q, ncrit, theta, dtype=np.float64, precision="fp64"):
+def gpu_tree(x, q, ncrit, theta, dtype=np.float64, precision="fp64", uniform_path=True):
     torch = torch_cuda()
     ensure_built()
     from paper_1106_2176_gb300 import FMM
-    f = FMM(len(q), p=4, theta=theta, ncrit=ncrit, precision=precision)
+    f = FMM(len(q), p=4, theta=theta, ncrit=ncrit, precision=precision, uniform_path=uniform_path)
     f.build(torch.tensor(np.asarray(x, dtype), device="cuda"), torch.tensor(np.asarray(q, dtype), device="cuda"))
     return f.export_tree(), f
 
 
-def compare(x, q, ncrit, theta, dtype=np.float64):
-    g, f = gpu_tree(x, q, ncrit, theta, dtype)
+def compare(x, q, ncrit, theta, dtype=np.float64, uniform_path=True):
+    g, f = gpu_tree(x, q, ncrit, theta, dtype, uniform_path=uniform_path)
     # the oracle sees exactly the values the GPU saw
     xo = np.asarray(x, dtype).astype(np.float64)
     T = oracle.Tree(xo, ncrit, theta)
@@ -40,6 +40,10 @@ def compare(x, q, ncrit, theta, dtype=np.float64):
     s = f.stats()
     assert s["n_p2p_pairs"] == T.n_p2p and s["n_m2l_pairs"] == T.n_m2l
     assert s["n_interactions"] == T.interactions and s["depth"] == T.depth
+    # the full-octree fast path is taken exactly when every leaf sits on the
+    # deepest level and every level is full
+    full = T.nleaves == 8 ** T.depth and T.ncells == (8 ** (T.depth + 1) - 1) // 7 and T.depth >= 1
+    assert s["uniform_path"] == int(uniform_path and full)
     return T
 
 
@@ -48,6 +52,16 @@ def compare(x, q, ncrit, theta, dtype=np.float64):
 def test_uniform_tree_bit_exact(n, ncrit, theta, seed):
     x, q = inputs.uniform_cube(n, seed)
     compare(x, q, ncrit, theta)
+
+
+@pytest.mark.parametrize("uniform_path", [True, False])
+@pytest.mark.parametrize("n,ncrit,theta,seed", [(16384, 64, 0.5, 1), (50000, 32, 0.4, 5), (4096, 100, 0.3, 7)])
+def test_full_octree_lists_with_and_without_fast_path(n, ncrit, theta, seed, uniform_path):
+    # uniform cubes whose trees come out full: the lattice-stencil lists and
+    # the traversal's both equal the oracle's
+    x, q = inputs.uniform_cube(n, seed)
+    T = compare(x, q, ncrit, theta, uniform_path=uniform_path)
+    assert T.nleaves == 8 ** T.depth
 
 
 @pytest.mark.parametrize("n,ncrit", [(20000, 16), (3000, 1)])
