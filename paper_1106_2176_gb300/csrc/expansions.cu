@@ -805,9 +805,12 @@ __global__ void __launch_bounds__(32 * M2LX_W) m2lx_k(int p, int nc, const int *
 }
 
 // FP32 form of the same for p = 2 .. 10, p fixed at compile time.  Eight warps
-// per target cell; each warp loads the source ids and cells of 32 of its pairs
-// at once (lane i: pair i), prefetches the next source's M~ while it computes
-// the current pair, and keeps its running sums as FP32 (hi, lo) pairs.
+// per target cell, each half-warp on its own pair: the cell's pair q goes to
+// half-warp q % 16 (its 16 lanes own outputs o, o + 16, ... of the triangle and
+// build columns m, m + 16 of I(u)).  A warp loads the source ids and cells of
+// 32 of its pairs at once (lane i: pair i), prefetches each half's next M~
+// while the current pair is computed, and keeps running sums as FP32 (hi, lo)
+// pairs; the 16 partial sums are added in half-warp order.
 constexpr int M2LX_FW = 8;
 
 __device__ __forceinline__ void m2lx_two_sum(float &hi, float &lo, float b)
@@ -819,27 +822,36 @@ __device__ __forceinline__ void m2lx_two_sum(float &hi, float &lo, float b)
 }
 
 template <int P>
-__global__ void __launch_bounds__(32 * M2LX_FW, 2) m2lx_f_k(int nc, const int *__restrict__ ptr,
-                                                         const int *__restrict__ src, const int4 *__restrict__ xyz,
-                                                         const float *__restrict__ M, float *__restrict__ L)
+constexpr size_t m2lx_f_smem()
 {
-    constexpr int PP = P * P, Q = 2 * P - 1, NT = P * (P + 1) / 2, NO = (NT + 31) / 32, NM = (PP + 31) / 32;
-    __shared__ float2 sIa[M2LX_FW][Q * Q];
-    __shared__ float2 sMa[M2LX_FW][PP];
-    __shared__ double red[M2LX_FW][2 * NT];
+    return sizeof(float2) * 2 * M2LX_FW * (size_t)((2 * P - 1) * (2 * P - 1) + P * P) +
+           sizeof(double) * 2 * M2LX_FW * (size_t)(P * (P + 1));
+}
+
+template <int P>
+__global__ void __launch_bounds__(32 * M2LX_FW, 2) m2lx_f_k(int nc, const int *__restrict__ ptr,
+                                                            const int *__restrict__ src, const int4 *__restrict__ xyz,
+                                                            const float *__restrict__ M, float *__restrict__ L)
+{
+    constexpr int PP = P * P, Q = 2 * P - 1, NT = P * (P + 1) / 2, NO = (NT + 15) / 16, NM = (PP + 15) / 16;
+    constexpr int NH = 2 * M2LX_FW;  // half-warps
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int c = blockIdx.x;
     if (c >= nc) return;
-    const int k0 = ptr[c], k1 = ptr[c + 1];
-    if (k0 == k1) return;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float2 *sI = sIa[warp], *sM = sMa[warp];
+    const int k0 = ptr[c], npair = ptr[c + 1] - k0;
+    if (npair == 0) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15;
+    const int hw = 2 * warp + half;
+    float2 *sI = reinterpret_cast<float2 *>(smem_raw) + (size_t)hw * (Q * Q + PP);
+    float2 *sM = sI + Q * Q;
+    double *red = reinterpret_cast<double *>(reinterpret_cast<float2 *>(smem_raw) + (size_t)NH * (Q * Q + PP));
     const int4 a = xyz[c];
-    // this lane's entries of M~ in full complex storage: i = lane + 32 r = j^2 + j + k
+    // this lane's entries of M~ in full complex storage: i = hl + 16 r = j^2 + j + k
     int mre[NM], mim[NM], mj[NM];
     float msr[NM], msi[NM];
 #pragma unroll
     for (int r = 0; r < NM; r++) {
-        const int i = lane + 32 * r;
+        const int i = hl + 16 * r;
         int j = 0;
         while ((j + 1) * (j + 1) <= i) j++;
         const int k = i - j * j - j, ak = k < 0 ? -k : k;
@@ -851,11 +863,11 @@ __global__ void __launch_bounds__(32 * M2LX_FW, 2) m2lx_f_k(int nc, const int *_
         msr[r] = sg;
         msi[r] = k < 0 ? -sg : sg;
     }
-    // this lane's outputs o = lane + 32 r of the (n, m) triangle
+    // this lane's outputs o = hl + 16 r of the (n, m) triangle
     int on[NO], om[NO];
 #pragma unroll
     for (int r = 0; r < NO; r++) {
-        const int o = lane + 32 * r;
+        const int o = hl + 16 * r;
         int n = 0;
         while ((n + 1) * (n + 2) / 2 <= o) n++;
         on[r] = o < NT ? n : -1;
@@ -865,28 +877,38 @@ __global__ void __launch_bounds__(32 * M2LX_FW, 2) m2lx_f_k(int nc, const int *_
 #pragma unroll
     for (int r = 0; r < NO; r++) ahr[r] = alr[r] = ahi[r] = ali[r] = 0.f;
 
-    const int npair = k1 - k0 > warp ? (k1 - k0 - warp + M2LX_FW - 1) / M2LX_FW : 0;
-    for (int t0 = 0; t0 < npair; t0 += 32) {
-        const int nb = min(32, npair - t0);
+    // step t of this warp: half h takes pair q = NH t + 2 warp + h
+    const int nstep = npair > 2 * warp ? (npair - 2 * warp + NH - 1) / NH : 0;
+    float pre[NM], pim[NM];
+    auto fetch = [&](int B) {
+#pragma unroll
+        for (int r = 0; r < NM; r++) {
+            pre[r] = hl + 16 * r < PP ? M[(size_t)B * PP + mre[r]] : 0.f;
+            pim[r] = hl + 16 * r < PP && mim[r] >= 0 ? M[(size_t)B * PP + mim[r]] : 0.f;
+        }
+    };
+    for (int t0 = 0; t0 < nstep; t0 += 16) {
+        const int nb = min(16, nstep - t0);
         int Bl = 0;
         int4 bl = make_int4(0, 0, 0, 0);
-        if (lane < nb) {
-            Bl = src[k0 + warp + M2LX_FW * (t0 + lane)];
-            bl = xyz[Bl];
-        }
-        float pre[NM], pim[NM];
-        auto fetch = [&](int B) {
-#pragma unroll
-            for (int r = 0; r < NM; r++) {
-                pre[r] = lane + 32 * r < PP ? M[(size_t)B * PP + mre[r]] : 0.f;
-                pim[r] = lane + 32 * r < PP && mim[r] >= 0 ? M[(size_t)B * PP + mim[r]] : 0.f;
+        {
+            const int q = NH * (t0 + (lane >> 1)) + 2 * warp + (lane & 1);
+            if ((lane >> 1) < nb && q < npair) {
+                Bl = src[k0 + q];
+                bl = xyz[Bl];
             }
-        };
-        fetch(__shfl_sync(0xffffffffu, Bl, 0));
+        }
+        {
+            const int B0 = __shfl_sync(0xffffffffu, Bl, half);
+            if (NH * t0 + 2 * warp + half < npair) fetch(B0);
+        }
         for (int t = 0; t < nb; t++) {
-            const int bw = __shfl_sync(0xffffffffu, bl.w, t);
-            const int bx = __shfl_sync(0xffffffffu, bl.x, t), by = __shfl_sync(0xffffffffu, bl.y, t),
-                      bz = __shfl_sync(0xffffffffu, bl.z, t);
+            const int li = 2 * t + half;  // lane holding this half's pair
+            const bool valid = NH * (t0 + t) + 2 * warp + half < npair;
+            const int bw = __shfl_sync(0xffffffffu, bl.w, li);
+            const int bx = __shfl_sync(0xffffffffu, bl.x, li), by = __shfl_sync(0xffffffffu, bl.y, li),
+                      bz = __shfl_sync(0xffffffffu, bl.z, li);
+            const int Bn = __shfl_sync(0xffffffffu, Bl, min(li + 2, 31));
             const int dl = a.w - bw;  // > 0: the target is the smaller cell
             const int lmin = a.w < bw ? a.w : bw;
             const long long WA = 1LL << (FMM_MAXLEVEL - a.w), WB = 1LL << (FMM_MAXLEVEL - bw);
@@ -896,35 +918,40 @@ __global__ void __launch_bounds__(32 * M2LX_FW, 2) m2lx_f_k(int nc, const int *_
             const float uy = (float)(2LL * (a.y - by) + (WA - WB)) * sc;
             const float uz = (float)(2LL * (a.z - bz) + (WA - WB)) * sc;
             __syncwarp();
-            if (lane < Q) irregular_col<float, float>(Q, lane, ux, uy, uz, reinterpret_cast<float *>(sI));
+            if (valid) {
+                for (int m = hl; m < Q; m += 16) irregular_col<float, float>(Q, m, ux, uy, uz, reinterpret_cast<float *>(sI));
 #pragma unroll
-            for (int r = 0; r < NM; r++)
-                if (lane + 32 * r < PP) {
-                    const float f = dl < 0 ? ldexpf(1.f, dl * mj[r]) : 1.f;  // (w_B / s)^j
-                    sM[lane + 32 * r] = make_float2(pre[r] * msr[r] * f, pim[r] * msi[r] * f);
-                }
-            const int tn = t + 1 < nb ? t + 1 : t;
-            const int Bn = __shfl_sync(0xffffffffu, Bl, tn);
-            if (t + 1 < nb) fetch(Bn);
+                for (int r = 0; r < NM; r++)
+                    if (hl + 16 * r < PP) {
+                        const float f = dl < 0 ? ldexpf(1.f, dl * mj[r]) : 1.f;  // (w_B / s)^j
+                        sM[hl + 16 * r] = make_float2(pre[r] * msr[r] * f, pim[r] * msi[r] * f);
+                    }
+            }
+            if (t + 1 < nb && NH * (t0 + t + 1) + 2 * warp + half < npair) fetch(Bn);
             __syncwarp();
+            if (!valid) continue;
 #pragma unroll 1
             for (int r = 0; r < NO; r++) {
                 if (on[r] < 0) continue;
                 const int n = on[r], m = om[r];
-                float sr = 0.f, si = 0.f;
+                // eight independent partial sums (term parity x four products)
+                // keep the FMA chains short
+                float a0[2] = {0.f, 0.f}, a1[2] = {0.f, 0.f}, a2[2] = {0.f, 0.f}, a3[2] = {0.f, 0.f};
 #pragma unroll
                 for (int j = 0; j < P; j++) {
                     const float2 *Ij = sI + (j + n) * (j + n) + (j + n) + m;
 #pragma unroll
                     for (int k = -j; k <= j; k++) {
+                        const int t = (j * j + j + k) & 1;
                         const float2 mv = sM[j * j + j + k];
                         const float2 iv = Ij[k];
-                        sr = fmaf(mv.x, iv.x, sr);
-                        sr = fmaf(-mv.y, iv.y, sr);
-                        si = fmaf(mv.x, iv.y, si);
-                        si = fmaf(mv.y, iv.x, si);
+                        a0[t] = fmaf(mv.x, iv.x, a0[t]);
+                        a1[t] = fmaf(mv.y, iv.y, a1[t]);
+                        a2[t] = fmaf(mv.x, iv.y, a2[t]);
+                        a3[t] = fmaf(mv.y, iv.x, a3[t]);
                     }
                 }
+                const float sr = (a0[0] + a0[1]) - (a1[0] + a1[1]), si = (a2[0] + a2[1]) + (a3[0] + a3[1]);
                 float f = dl > 0 ? ldexpf(1.f, -dl * (n + 1)) : 1.f;  // (w_A / s)^(n+1)
                 if (n & 1) f = -f;
                 m2lx_two_sum(ahr[r], alr[r], f * sr);
@@ -935,25 +962,37 @@ __global__ void __launch_bounds__(32 * M2LX_FW, 2) m2lx_f_k(int nc, const int *_
 #pragma unroll
     for (int r = 0; r < NO; r++)
         if (on[r] >= 0) {
-            const int o = lane + 32 * r;
-            red[warp][2 * o] = (double)ahr[r] + (double)alr[r];
-            red[warp][2 * o + 1] = (double)ahi[r] + (double)ali[r];
+            const int o = hl + 16 * r;
+            red[(size_t)hw * 2 * NT + 2 * o] = (double)ahr[r] + (double)alr[r];
+            red[(size_t)hw * 2 * NT + 2 * o + 1] = (double)ahi[r] + (double)ali[r];
         }
     __syncthreads();
     if (warp) return;
     float *Lc = L + (size_t)c * PP;
-#pragma unroll
-    for (int r = 0; r < NO; r++) {
-        if (on[r] < 0) continue;
-        const int o = lane + 32 * r;
+    for (int o = lane; o < NT; o += 32) {
+        int n = 0;
+        while ((n + 1) * (n + 2) / 2 <= o) n++;
+        const int m = o - n * (n + 1) / 2;
         double sr = 0, si = 0;
-        for (int w = 0; w < M2LX_FW; w++) {
-            sr += red[w][2 * o];
-            si += red[w][2 * o + 1];
+        for (int w = 0; w < NH; w++) {  // every half-warp wrote all its outputs (zero without pairs)
+            sr += red[(size_t)w * 2 * NT + 2 * o];
+            si += red[(size_t)w * 2 * NT + 2 * o + 1];
         }
-        Lc[re_idx(on[r], om[r])] += (float)sr;
-        if (om[r]) Lc[im_idx(on[r], om[r])] += (float)si;
+        Lc[re_idx(n, m)] += (float)sr;
+        if (m) Lc[im_idx(n, m)] += (float)si;
     }
+}
+
+template <int P>
+static void m2lx_f_run(int nc, const int *ptr, const int *src, const int4 *xyz, const float *M, float *L, cudaStream_t s)
+{
+    constexpr size_t smem = m2lx_f_smem<P>();
+    static bool attr = false;
+    if (!attr) {
+        FMM_CUDA_TRY(cudaFuncSetAttribute(m2lx_f_k<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = true;
+    }
+    m2lx_f_k<P><<<nc, 32 * M2LX_FW, smem, s>>>(nc, ptr, src, xyz, M, L);
 }
 
 static bool m2lx_f_launch(int p, int nc, const int *ptr, const int *src, const int4 *xyz, const float *M, float *L,
@@ -961,7 +1000,7 @@ static bool m2lx_f_launch(int p, int nc, const int *ptr, const int *src, const i
 {
     switch (p) {
 #define FMM_M2LX_CASE(PV) \
-    case PV: m2lx_f_k<PV><<<nc, 32 * M2LX_FW, 0, s>>>(nc, ptr, src, xyz, M, L); return true;
+    case PV: m2lx_f_run<PV>(nc, ptr, src, xyz, M, L, s); return true;
         FMM_M2LX_CASE(2) FMM_M2LX_CASE(3) FMM_M2LX_CASE(4) FMM_M2LX_CASE(5) FMM_M2LX_CASE(6)
         FMM_M2LX_CASE(7) FMM_M2LX_CASE(8) FMM_M2LX_CASE(9) FMM_M2LX_CASE(10)
 #undef FMM_M2LX_CASE

@@ -794,22 +794,15 @@ __global__ void __launch_bounds__(32 * ROW_SORT_WARPS) row_sort_k(int nc, const 
 // uniform-tree fast path: on a full octree (every leaf on level L, every level
 // full) the traversal's P2P lists are the near-field lattice stencil of level
 // L, cut at the lattice boundary; cell id = first cell of level L + Morton
-// index of the lattice position.  A candidate pair is kept only if no pair of
-// ancestors is accepted, as in the traversal.
+// index of the lattice position.  The traversal reaches a pair of leaves only
+// if every pair of their ancestors was rejected; that holds for every near
+// pair: theta < 1 gives K0 >= 4, and a child offset with |v|^2 <= K0 - 1 has a
+// parent offset with |u_d| <= (|v_d| + 1) / 2, so
+// |u|^2 <= (|v|^2 + 2 sqrt(3) |v| + 3) / 4 < K0.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ bool near_pair_kept(int L, int px, int py, int pz, int qx, int qy, int qz, long long K0)
-{
-    for (int l = L - 1; l >= 1; l--) {
-        const int sh = L - l;
-        const long long ux = (qx >> sh) - (px >> sh), uy = (qy >> sh) - (py >> sh), uz = (qz >> sh) - (pz >> sh);
-        if (ux * ux + uy * uy + uz * uz >= K0) return false;
-    }
-    return true;
-}
-
 // write = false: row counts into cnt[c]; write = true: the rows at ptr[c]
 __global__ void near_rows_k(int ls, int le, int L, const int4 *__restrict__ xyz, const int4 *__restrict__ near,
-                            int nnear, long long K0, unsigned *__restrict__ cnt, const int *__restrict__ ptr,
+                            int nnear, unsigned *__restrict__ cnt, const int *__restrict__ ptr,
                             int *__restrict__ src, bool write)
 {
     const int c = ls + blockIdx.x * blockDim.x + threadIdx.x;
@@ -822,7 +815,6 @@ __global__ void near_rows_k(int ls, int le, int L, const int4 *__restrict__ xyz,
         const int4 v = near[e];
         const int qx = px + v.x, qy = py + v.y, qz = pz + v.z;
         if (qx < 0 || qy < 0 || qz < 0 || qx >= side || qy >= side || qz >= side) continue;
-        if (!near_pair_kept(L, px, py, pz, qx, qy, qz, K0)) continue;
         if (write) src[base + k] = ls + (int)morton3((uint32_t)qx, (uint32_t)qy, (uint32_t)qz);
         k++;
     }
@@ -1040,7 +1032,7 @@ static bool uniform_lists(fmm_ctx *h, long long K0, cudaStream_t s)
     h->p2p_ptr.ensure(sizeof(int) * (size_t)(nc + 1));
     h->row_cnt.ensure(sizeof(unsigned) * (size_t)(nc + 1));
     FMM_CUDA_TRY(cudaMemsetAsync(h->row_cnt.p, 0, sizeof(unsigned) * (size_t)(nc + 1), s));
-    near_rows_k<<<nblocks(le - ls, 128), 128, 0, s>>>(ls, le, L, h->c_xyz.as<int4>(), h->near_dev.as<int4>(), nn, K0,
+    near_rows_k<<<nblocks(le - ls, 128), 128, 0, s>>>(ls, le, L, h->c_xyz.as<int4>(), h->near_dev.as<int4>(), nn,
                                                       h->row_cnt.as<unsigned>(), nullptr, nullptr, false);
     count_launch(h);
     scan_exclusive_u32(h, h->row_cnt.as<unsigned>(), reinterpret_cast<unsigned *>(h->p2p_ptr.as<int>()), nc + 1, nullptr, s);
@@ -1049,7 +1041,7 @@ static bool uniform_lists(fmm_ctx *h, long long K0, cudaStream_t s)
     FMM_CUDA_TRY(cudaStreamSynchronize(s));
     h->n_p2p = (int64_t)*hp;
     h->p2p_src.ensure(sizeof(int) * (size_t)std::max<int64_t>(h->n_p2p, 1));
-    near_rows_k<<<nblocks(le - ls, 128), 128, 0, s>>>(ls, le, L, h->c_xyz.as<int4>(), h->near_dev.as<int4>(), nn, K0,
+    near_rows_k<<<nblocks(le - ls, 128), 128, 0, s>>>(ls, le, L, h->c_xyz.as<int4>(), h->near_dev.as<int4>(), nn,
                                                       nullptr, h->p2p_ptr.as<int>(), h->p2p_src.as<int>(), true);
     count_launch(h);
     row_sort_k<<<nblocks(nc, ROW_SORT_WARPS), 32 * ROW_SORT_WARPS, 0, s>>>(nc, h->p2p_ptr.as<int>(), h->p2p_src.as<int>());
