@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg (profiling runs)")
     ap.add_argument("--batch", type=int, default=512, help="systems in the batched-evaluation leg (0 = skip)")
     ap.add_argument("--diff-n", type=int, default=1_000_000, help="particles in the differentiation leg (0 = skip)")
+    ap.add_argument("--engines-n", type=int, default=1_000_000,
+                    help="particles of the M2L engine comparison at p = 8, 10, 16 (0 = skip)")
     ap.add_argument("--overlap", type=int, default=0, choices=[0, 1],
                     help="0 (default): far and near field in turn on one stream, so the P2P events time the kernel "
                          "alone; 1: on concurrent streams")
@@ -357,6 +359,45 @@ def run_diff(a, dev):
             "rel_l2_dE_dx": rel(xt.grad[t], dx), "rel_l2_dE_dq": rel(qt.grad[t], dq), "error_targets": 1024}
 
 
+def run_m2l_engines(a, dev):
+    """M2L launch time of each engine at p = 8, 10, 16 on one uniform cube
+    (theta = 0.5, ncrit = 64, FP32 inputs, mixed precision, far and near field
+    in turn so the M2L events time the phase alone): the split-TF32 tensor-core
+    contraction (p <= 11), the dense CUDA-core contraction and the rotation
+    engine. Error: relative L2 of phi on 512 sampled targets against the
+    library's FP64 direct sum."""
+    import numpy as np
+    import torch
+    from paper_1106_2176_gb300 import FMM, inputs
+
+    n = a.engines_n
+    x, q = inputs.uniform_cube(n, 17, dtype=np.float32)
+    xt, qt = torch.tensor(x, device=dev), torch.tensor(q, device=dev)
+    t = torch.as_tensor(inputs.sample_targets(n, 512, seed=5), device=dev)
+    g = FMM(n, p=2, theta=0.5, ncrit=64, precision="fp64")
+    pd, _ = g.direct(xt.double(), qt.double(), t)
+    g.close()
+    out = {"workload": "uniform cube N=%d, FP32, theta=0.5, ncrit=64, mixed precision" % n}
+    for p in (8, 10, 16):
+        row = {}
+        for eng in ("tensor", "cudacore", "rotation"):
+            if eng == "tensor" and p > 11:
+                continue
+            f = FMM(n, p=p, theta=0.5, ncrit=64, precision="mixed", m2l_engine=eng, overlap=False)
+            f.build(xt, qt)
+            phi, grad = f.evaluate()
+            ms = []
+            for _ in range(2):
+                f.evaluate(phi, grad)
+                ms.append(f.stats()["ms_m2l"])
+            st = f.stats()
+            err = float(torch.linalg.norm(phi[t].double() - pd) / torch.linalg.norm(pd))
+            row[eng] = {"ms_m2l": min(ms), "rel_l2_phi": err, "m2l_pairs": st["n_m2l_pairs"]}
+            f.close()
+        out["p%d" % p] = row
+    return out
+
+
 def main():
     a = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -534,12 +575,15 @@ def main():
                "gpu_launches": launches, "clocks": ck, "uniform_path": uni}
     f.close()
     if rank == 0:
-        if world == 1 and (a.batch > 0 or a.diff_n > 0):
+        if world == 1 and (a.batch > 0 or a.diff_n > 0 or a.engines_n > 0):
             del xt, qt, phi, grad
             torch.cuda.empty_cache()
+        if world == 1 and a.batch > 0:
             out["batch"] = run_batch(a, dev)
         if world == 1 and a.diff_n > 0:
             out["differentiation"] = run_diff(a, dev)
+        if world == 1 and a.engines_n > 0:
+            out["m2l_engines"] = run_m2l_engines(a, dev)
         print(json.dumps(out), flush=True)
     if dist:
         dist.barrier()

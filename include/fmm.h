@@ -71,7 +71,7 @@ enum {
 };
 
 /* M2L engine (FMM_MIXED only) */
-enum { FMM_M2L_AUTO = 0, FMM_M2L_TENSOR = 1, FMM_M2L_CUDACORE = 2 };
+enum { FMM_M2L_AUTO = 0, FMM_M2L_TENSOR = 1, FMM_M2L_CUDACORE = 2, FMM_M2L_ROTATION = 3 };
 
 typedef struct {
     int64_t n;              /* particles of the last build */
@@ -114,7 +114,14 @@ FMM_API int fmm_create(int64_t N, int p, double theta, int ncrit, fmm_handle *ou
 /* Select FMM_FP64 (default) or FMM_MIXED. Takes effect at the next build. */
 FMM_API int fmm_set_precision(fmm_handle h, int mode);
 
-/* Select the M2L engine for FMM_MIXED (FMM_M2L_AUTO uses the tensor cores). */
+/* Select the M2L engine; takes effect at the next build. FMM_M2L_AUTO: the
+ * tensor cores for FMM_MIXED (p <= 11), the CUDA-core dense contraction
+ * otherwise. FMM_M2L_TENSOR: split-TF32 tcgen05 contraction (FMM_MIXED,
+ * p <= 11). FMM_M2L_CUDACORE: dense O(p^4) contraction on the CUDA cores.
+ * FMM_M2L_ROTATION: rotate each translation onto the z axis, translate along
+ * z and rotate back, O(p^3) per pair (either precision, p <= 16). The
+ * different-level pairs of adaptive trees always take the per-pair kernel.
+ * Returns FMM_EINVAL for an unknown engine or one that does not support p. */
 FMM_API int fmm_set_m2l_engine(fmm_handle h, int engine);
 
 /* Scheduling of fmm_evaluate. on = 1 (default): the far field (P2M .. L2P)
@@ -244,6 +251,17 @@ FMM_API int fmm_export_expansions(fmm_handle h, double *M, double *L);
  */
 FMM_API int fmm_direct(fmm_handle h, const double *x, const double *q, int64_t n, const int64_t *tidx,
                int64_t nt, double *phi, double *grad);
+
+/* Rotation-based M2L of one expansion on the host, FP64, no GPU needed: the
+ * packed multipole M (p^2 reals: for each degree n, Re M_n^0, then Re and Im
+ * of M_n^m, m = 1..n) about c_M is translated into the local expansion L
+ * (same layout, overwritten) about c_L, u = c_L - c_M (|u| > 0), by rotating
+ * u onto the z axis, translating along z (only equal orders couple, O(p^3))
+ * and rotating back; the result equals the dense M2L
+ * L_n^m = (-1)^n sum_{j,k} M_j^k I_{j+n}^{k+m}(u) up to rounding. It uses the
+ * rotation maps of the FMM_M2L_ROTATION engine. Returns FMM_EINVAL for p
+ * outside [1, 20], a NULL pointer or u = 0. */
+FMM_API int fmm_m2l_rotation_host(int p, const double *u, const double *M, double *L);
 
 FMM_API int fmm_destroy(fmm_handle h);
 

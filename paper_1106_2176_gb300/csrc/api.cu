@@ -84,7 +84,7 @@ fmm_ctx::~fmm_ctx()
                            &frontB, &p2p_pairs, &m2lx_pairs, &near_dev, &pair_keys, &pair_keys2, &pair_vals, &pair_vals2,
                            &p2p_ptr, &p2p_src, &p2p_runs, &p2p_nrun, &m2lx_ptr, &m2lx_src, &row_cnt, &counters, &lvl_desc, &map_pool,
                            &m2l_tgt, &m2l_tiles, &m2l_misc, &msplit, &Mexp, &Lexp, &far, &near, &out_phi, &out_grad,
-                           &direct_part};
+                           &direct_part, &rot_tab};
     for (auto *b : bufs) b->release();
     hpin.release();
     if (tm.ok)
@@ -216,10 +216,12 @@ int fmm_set_precision(fmm_handle h, int mode)
 int fmm_set_m2l_engine(fmm_handle h, int engine)
 {
     if (!h) return fail(FMM_EINVAL, "fmm_set_m2l_engine: NULL handle");
-    if (engine != FMM_M2L_AUTO && engine != FMM_M2L_TENSOR && engine != FMM_M2L_CUDACORE)
+    if (engine != FMM_M2L_AUTO && engine != FMM_M2L_TENSOR && engine != FMM_M2L_CUDACORE && engine != FMM_M2L_ROTATION)
         return fail(FMM_EINVAL, "fmm_set_m2l_engine: unknown engine");
     if (engine == FMM_M2L_TENSOR && !fmm::tensor_m2l_supported(h))
         return fail(FMM_EINVAL, "fmm_set_m2l_engine: tensor-core M2L not supported for this p");
+    if (engine == FMM_M2L_ROTATION && !fmm::rotation_m2l_supported(h))
+        return fail(FMM_EINVAL, "fmm_set_m2l_engine: rotation M2L supports p <= 16");
     h->engine_req = engine;
     return FMM_OK;
 }
@@ -229,6 +231,19 @@ int fmm_set_overlap(fmm_handle h, int on)
     if (!h) return fail(FMM_EINVAL, "fmm_set_overlap: NULL handle");
     if (on != 0 && on != 1) return fail(FMM_EINVAL, "fmm_set_overlap: on must be 0 or 1");
     h->overlap = on;
+    return FMM_OK;
+}
+
+int fmm_m2l_rotation_host(int p, const double *u, const double *M, double *L)
+{
+    if (p < 1 || p > FMM_MAXP) return fail(FMM_EINVAL, "fmm_m2l_rotation_host: p must be in [1, 20]");
+    if (!u || !M || !L) return fail(FMM_EINVAL, "fmm_m2l_rotation_host: NULL argument");
+    if (!(u[0] * u[0] + u[1] * u[1] + u[2] * u[2] > 0)) return fail(FMM_EINVAL, "fmm_m2l_rotation_host: u = 0");
+    try {
+        fmm::m2l_rotation_ref(p, u, M, L);
+    } catch (...) {
+        return fail(FMM_ENOMEM, "fmm_m2l_rotation_host: out of host memory");
+    }
     return FMM_OK;
 }
 
@@ -263,7 +278,8 @@ int fmm_build(fmm_handle h, const void *x, const void *q, int64_t n, int dtype)
     h->dtype = dt;
     h->host_mem = host;
     h->precision = h->precision_req;
-    h->engine_used = (h->precision == FMM_MIXED && h->engine_req != FMM_M2L_CUDACORE && fmm::tensor_m2l_supported(h))
+    h->engine_used = h->engine_req == FMM_M2L_ROTATION ? FMM_M2L_ROTATION
+                     : (h->precision == FMM_MIXED && h->engine_req != FMM_M2L_CUDACORE && fmm::tensor_m2l_supported(h))
                          ? FMM_M2L_TENSOR
                          : FMM_M2L_CUDACORE;
     FMM_CUDA_TRY(cudaEventRecord(h->tm.ev[0], s));

@@ -1195,6 +1195,7 @@ static int floordiv2(int a) { return a >= 0 ? a / 2 : -((-a + 1) / 2); }
 int m2l_tile_size(fmm_ctx *h)
 {
     if (h->precision == FMM_MIXED && h->engine_used == FMM_M2L_TENSOR) return 128;
+    if (h->engine_used == FMM_M2L_ROTATION) return rotation_tile_rows();
     const int ntri = h->p * (h->p + 1) / 2;
     int t = std::min(32, (M2L_CC_T * M2L_CC_ACC) / ntri);
     return std::max(t, 1);
@@ -1481,6 +1482,8 @@ static void far_field_t(fmm_ctx *h, const P4 *xs, const T *rtab)
     if (h->depth >= 2) {
         if (std::is_same<T, float>::value && h->engine_used == FMM_M2L_TENSOR) {
             m2l_tensor(h, reinterpret_cast<float *>(L), reinterpret_cast<const float *>(M));
+        } else if (h->engine_used == FMM_M2L_ROTATION) {
+            m2l_rotation<T>(h, L, M);
         } else {
             const int tile = m2l_tile_size(h);
             size_t smem = sizeof(T) * 2 * ((size_t)Q * Q + (size_t)tile * PP) + sizeof(int) * 6 * tile;

@@ -161,6 +161,8 @@ struct fmm_ctx {
     fmm::DevBuf ttab;           // tensor-core M2L operators (split TF32 images), per vector
     size_t ttab_stride = 0;     // bytes per vector in ttab
     int ttab_nv = -1;           // stencil vectors the operator images were made for
+    fmm::DevBuf rot_tab;        // rotation M2L maps per vector ([A | B], FP32 or FP64)
+    int rot_nv = -1, rot_kind = 0;  // vectors and precision (1 FP32, 2 FP64) of rot_tab
     fmm::DevBuf msplit;         // M~ split into TF32 (hi, lo) rows for the tensor-core M2L
 
     // workspaces
@@ -215,6 +217,15 @@ void scan_exclusive_u32(fmm_ctx *h, const unsigned *in, unsigned *out, int64_t c
 // expansions.cu
 void operators_init(fmm_ctx *h);  // R tables of M2M / L2L
 void stencil_update(fmm_ctx *h);  // same-level M2L stencil for the current tree depth
+// rotation-based M2L: per-degree maps into / out of the frame whose z axis is u
+int rot_deg_off(int n);
+int rot_map_size(int p);
+void rotation_maps(int p, const double u[3], double *A, double *B);
+void m2l_rotation_ref(int p, const double u[3], const double *M, double *L);
+template <class T>
+void m2l_rotation(fmm_ctx *h, T *L, const T *M);  // same-level M2L of all tiles by rotation
+bool rotation_m2l_supported(fmm_ctx *h);           // p <= 16 (the maps of a vector fit shared memory)
+int rotation_tile_rows();
 // per (octant, level): how many of the octant's entries (shortest first) can
 // reach a cell of that level in the current tree; written after the offsets
 void stencil_levels(fmm_ctx *h, cudaStream_t s);

@@ -1,0 +1,465 @@
+// Rotation-based M2L (the paper's GPU code rotates expansions so that the
+// translation runs along z, O(p^3) per pair instead of O(p^4); Sec. 2.2 and
+// the prior GPU work it cites).
+//
+// For a translation u = c_L - c_M, a rotation Q takes u to |u| z. In the
+// rotated frame the irregular harmonics I_l^mu(|u| z) vanish unless mu = 0,
+// where I_l^0 = l! / |u|^(l+1), so the translation couples only equal orders:
+//   L'_n^m = (-1)^n sum_{j >= |m|} M'_j^-m (j+n)! / |u|^(j+n+1).
+// M' (the multipoles seen from the rotated frame) and L (the locals back in
+// the original frame) follow from M and L' by one dense map per degree n,
+// (2n+1) x (2n+1) real on the packed coefficients: 2 sum_n (2n+1)^2 + O(p^3)
+// multiply-adds per pair.
+//
+// The maps are built on the host in FP64. On the unit sphere both families
+// are multiples of Yt_n^m = P_n^m(cos t) e^{i m f} sqrt((n-m)!/(n+m)!)
+// (P without the Condon-Shortley phase): I_n^m = c_nm Yt_n^m and
+// R_n^m = Yt_n^m / c_nm with c_nm = sqrt((n+|m|)! (n-|m|)!). A rotation acts
+// unitarily on the Yt of one degree. With Q = R_y(-b) R_z(-a) (a, b the
+// azimuth and polar angle of u), Yt^m(x) = e^{i m a} sum_m' V_mm'(b) Yt^m'(Qx)
+// where V(b) is defined by Yt^m(R_y(b) y) = sum_m' V_mm'(b) Yt^m'(y); V is
+// found per distinct polar angle by least squares over a Fibonacci sphere of
+// sample points, the azimuth enters as exact phases. Then, with
+// U = diag(e^{i m a}) V:
+//   M'^m' = sum_m M^m c_m U_mm' / c_m'        (multipoles into the frame)
+//   L^m   = sum_m' L'^m' c_m U_mm' / c_m'     (locals back, U^-1 = U^H)
+
+#include <array>
+#include <cmath>
+#include <complex>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <tuple>
+#include <vector>
+
+#include "fmm_internal.cuh"
+
+namespace fmm {
+
+using cplx = std::complex<double>;
+
+// offset of degree n's (2n+1) x (2n+1) block in a per-vector map table
+int rot_deg_off(int n) { return n * (4 * n * n - 1) / 3; }
+int rot_map_size(int p) { return rot_deg_off(p); }
+
+// Q_n^m = r^n P_n^m(cos t) e^{i m f} for 0 <= m <= n <= N (triangular, n(n+1)/2 + m),
+// by the recurrences of the regular solid harmonics, no division by sin t
+static void qtab(int N, double x, double y, double z, std::vector<cplx> &Q)
+{
+    Q.assign((size_t)(N + 1) * (N + 2) / 2, cplx(0, 0));
+    auto id = [](int n, int m) { return n * (n + 1) / 2 + m; };
+    const double r2 = x * x + y * y + z * z;
+    cplx mm(1, 0);
+    const cplx xy(x, y);
+    for (int m = 0; m <= N; m++) {
+        if (m > 0) mm *= xy * (double)(2 * m - 1);
+        Q[id(m, m)] = mm;
+        if (m + 1 <= N) Q[id(m + 1, m)] = (double)(2 * m + 1) * z * mm;
+        for (int n = m + 2; n <= N; n++)
+            Q[id(n, m)] = ((double)(2 * n - 1) * z * Q[id(n - 1, m)] - (double)(n + m - 1) * r2 * Q[id(n - 2, m)]) /
+                          (double)(n - m);
+    }
+}
+
+static double fact(int k)
+{
+    double f = 1;
+    for (int i = 2; i <= k; i++) f *= i;
+    return f;
+}
+
+// Yt_n^m at a unit vector for m = -n..n (index m + n)
+static void ytil(int n, const std::vector<cplx> &Q, cplx *out)
+{
+    for (int m = 0; m <= n; m++) {
+        const cplx v = Q[n * (n + 1) / 2 + m] * std::sqrt(fact(n - m) / fact(n + m));
+        out[n + m] = v;
+        if (m) out[n - m] = ((m & 1) ? -1.0 : 1.0) * std::conj(v);
+    }
+}
+
+// solve A X = B in place (A: K x K, B: K x R, row-major), partial pivoting
+static void csolve(int K, int R, std::vector<cplx> &A, std::vector<cplx> &B)
+{
+    for (int c = 0; c < K; c++) {
+        int piv = c;
+        for (int r = c + 1; r < K; r++)
+            if (std::abs(A[(size_t)r * K + c]) > std::abs(A[(size_t)piv * K + c])) piv = r;
+        if (piv != c) {
+            for (int k = 0; k < K; k++) std::swap(A[(size_t)c * K + k], A[(size_t)piv * K + k]);
+            for (int k = 0; k < R; k++) std::swap(B[(size_t)c * R + k], B[(size_t)piv * R + k]);
+        }
+        const cplx d = A[(size_t)c * K + c];
+        for (int r = 0; r < K; r++) {
+            if (r == c) continue;
+            const cplx f = A[(size_t)r * K + c] / d;
+            if (f == cplx(0, 0)) continue;
+            for (int k = c; k < K; k++) A[(size_t)r * K + k] -= f * A[(size_t)c * K + k];
+            for (int k = 0; k < R; k++) B[(size_t)r * R + k] -= f * B[(size_t)c * R + k];
+        }
+    }
+    for (int r = 0; r < K; r++)
+        for (int k = 0; k < R; k++) B[(size_t)r * R + k] /= A[(size_t)r * K + r];
+}
+
+// V(b) for every degree n < p: Yt_n^m(R_y(b) y) = sum_m' V_mm' Yt_n^m'(y),
+// least squares over S points of a Fibonacci sphere. V[n] is (2n+1)^2, row m + n.
+static std::vector<std::vector<cplx>> vmaps(int p, double b)
+{
+    const int S = 8 * p + 16;
+    const double cb = std::cos(b), sb = std::sin(b);
+    std::vector<std::vector<cplx>> Yy(S), Yr(S);
+    std::vector<cplx> Q;
+    for (int s = 0; s < S; s++) {
+        const double z = 1.0 - 2.0 * (s + 0.5) / S, rho = std::sqrt(std::max(0.0, 1.0 - z * z));
+        const double f = s * 2.39996322972865332;  // golden angle
+        const double y[3] = {rho * std::cos(f), rho * std::sin(f), z};
+        // R_y(b) y
+        const double ry[3] = {cb * y[0] + sb * y[2], y[1], -sb * y[0] + cb * y[2]};
+        Yy[s].resize((size_t)p * p);
+        Yr[s].resize((size_t)p * p);
+        qtab(p - 1, y[0], y[1], y[2], Q);
+        for (int n = 0; n < p; n++) ytil(n, Q, &Yy[s][(size_t)n * n]);
+        qtab(p - 1, ry[0], ry[1], ry[2], Q);
+        for (int n = 0; n < p; n++) ytil(n, Q, &Yr[s][(size_t)n * n]);
+    }
+    std::vector<std::vector<cplx>> V(p);
+    for (int n = 0; n < p; n++) {
+        const int K = 2 * n + 1;
+        // normal equations: V G = H with G = sum_s y y^H, H = sum_s r y^H; G is
+        // Hermitian, so G V^H = H^H
+        std::vector<cplx> G((size_t)K * K, 0), Hh((size_t)K * K, 0);
+        for (int s = 0; s < S; s++) {
+            const cplx *yy = &Yy[s][(size_t)n * n], *rr = &Yr[s][(size_t)n * n];
+            for (int a = 0; a < K; a++)
+                for (int c = 0; c < K; c++) {
+                    G[(size_t)a * K + c] += yy[a] * std::conj(yy[c]);
+                    Hh[(size_t)a * K + c] += yy[a] * std::conj(rr[c]);  // (H^H)_ac = conj(H_ca)
+                }
+        }
+        csolve(K, K, G, Hh);  // Hh := V^H
+        V[n].resize((size_t)K * K);
+        for (int a = 0; a < K; a++)
+            for (int c = 0; c < K; c++) V[n][(size_t)a * K + c] = std::conj(Hh[(size_t)c * K + a]);
+    }
+    return V;
+}
+
+// real packed form of a complex degree-n map given as out^j = sum_i in^i T[i][j]
+// (i, j = m + n): column b of the result is the map applied to packed basis vector b
+static void packed(int n, const std::vector<cplx> &T, double *out)
+{
+    const int K = 2 * n + 1;
+    std::vector<cplx> in(K), o(K);
+    for (int b = 0; b < K; b++) {
+        std::fill(in.begin(), in.end(), cplx(0, 0));
+        const int m = (b + 1) / 2;
+        const cplx e = b == 0 ? cplx(1, 0) : ((b & 1) ? cplx(1, 0) : cplx(0, 1));
+        in[n + m] = e;
+        if (m) in[n - m] = ((m & 1) ? -1.0 : 1.0) * std::conj(e);
+        for (int j = 0; j < K; j++) {
+            cplx s(0, 0);
+            for (int i = 0; i < K; i++) s += in[i] * T[(size_t)i * K + j];
+            o[j] = s;
+        }
+        out[0 * K + b] = o[n].real();
+        for (int mm = 1; mm <= n; mm++) {
+            out[(size_t)(2 * mm - 1) * K + b] = o[n + mm].real();
+            out[(size_t)(2 * mm) * K + b] = o[n + mm].imag();
+        }
+    }
+}
+
+// V(b) cached per (p, b): the stencil has far fewer polar angles than vectors
+static std::mutex g_v_mu;
+static std::map<std::pair<int, double>, std::shared_ptr<const std::vector<std::vector<cplx>>>> g_v_cache;
+
+static std::shared_ptr<const std::vector<std::vector<cplx>>> vmaps_cached(int p, double b)
+{
+    const auto key = std::make_pair(p, b);
+    {
+        std::lock_guard<std::mutex> lk(g_v_mu);
+        auto it = g_v_cache.find(key);
+        if (it != g_v_cache.end()) return it->second;
+    }
+    auto v = std::make_shared<const std::vector<std::vector<cplx>>>(vmaps(p, b));
+    std::lock_guard<std::mutex> lk(g_v_mu);
+    g_v_cache[key] = v;
+    return v;
+}
+
+// forward (multipoles into the rotated frame) and backward (locals out of it)
+// maps for translation u, each rot_map_size(p) doubles, degree blocks row-major
+void rotation_maps(int p, const double u[3], double *A, double *B)
+{
+    const double rxy = std::hypot(u[0], u[1]);
+    const double a = rxy > 0 ? std::atan2(u[1], u[0]) : 0.0, b = std::atan2(rxy, u[2]);
+    auto V = vmaps_cached(p, b);
+    for (int n = 0; n < p; n++) {
+        const int K = 2 * n + 1;
+        std::vector<cplx> T((size_t)K * K);
+        for (int i = 0; i < K; i++) {
+            const int m = i - n;
+            const cplx ph = std::polar(1.0, m * a);
+            const double cm = std::sqrt(fact(n + std::abs(m)) * fact(n - std::abs(m)));
+            for (int j = 0; j < K; j++) {
+                const int mp = j - n;
+                const double cmp = std::sqrt(fact(n + std::abs(mp)) * fact(n - std::abs(mp)));
+                T[(size_t)i * K + j] = cm * ph * (*V)[n][(size_t)i * K + j] / cmp;
+            }
+        }
+        // both directions use T: M'^j = sum_i M^i T_ij, L^i = sum_j L'^j T_ij
+        packed(n, T, A + rot_deg_off(n));
+        std::vector<cplx> Tt((size_t)K * K);
+        for (int i = 0; i < K; i++)
+            for (int j = 0; j < K; j++) Tt[(size_t)j * K + i] = T[(size_t)i * K + j];
+        packed(n, Tt, B + rot_deg_off(n));
+    }
+}
+
+// the whole rotation M2L on the host, FP64, packed p^2 coefficients
+void m2l_rotation_ref(int p, const double u[3], const double *M, double *L)
+{
+    const int PP = p * p;
+    std::vector<double> A(rot_map_size(p)), B(rot_map_size(p)), Mr(PP), Lr(PP);
+    rotation_maps(p, u, A.data(), B.data());
+    for (int n = 0; n < p; n++) {
+        const int K = 2 * n + 1;
+        for (int r = 0; r < K; r++) {
+            double s = 0;
+            for (int c = 0; c < K; c++) s += A[rot_deg_off(n) + (size_t)r * K + c] * M[n * n + c];
+            Mr[n * n + r] = s;
+        }
+    }
+    const double d = std::sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    std::vector<double> g(2 * p);
+    for (int l = 0; l < 2 * p - 1; l++) g[l] = fact(l) / std::pow(d, l + 1);
+    for (int n = 0; n < p; n++)
+        for (int m = 0; m <= n; m++) {
+            double sr = 0, si = 0;
+            for (int j = m; j < p; j++) {
+                sr += Mr[re_idx(j, m)] * g[j + n];
+                if (m) si += Mr[im_idx(j, m)] * g[j + n];
+            }
+            const double sg = ((n + m) & 1) ? -1.0 : 1.0;
+            Lr[re_idx(n, m)] = sg * sr;
+            if (m) Lr[im_idx(n, m)] = -sg * si;
+        }
+    for (int n = 0; n < p; n++) {
+        const int K = 2 * n + 1;
+        for (int r = 0; r < K; r++) {
+            double s = 0;
+            for (int c = 0; c < K; c++) s += B[rot_deg_off(n) + (size_t)r * K + c] * Lr[n * n + c];
+            L[n * n + r] = s;
+        }
+    }
+}
+
+}  // namespace fmm
+
+// ---------------------------------------------------------------------------
+// device engine
+// ---------------------------------------------------------------------------
+namespace fmm {
+
+// maps of every stencil vector, [A | B] per vector id (2 rot_map_size(p)
+// doubles), one host image per process for each (p, MAC constant, stencil bound)
+static std::mutex g_rot_mu;
+static std::map<std::tuple<int, double, int>, std::shared_ptr<const std::vector<double>>> g_rot_cache;
+
+static std::shared_ptr<const std::vector<double>> rot_image(fmm_ctx *h)
+{
+    const auto key = std::make_tuple(h->p, h->cmac, h->st_R);
+    {
+        std::lock_guard<std::mutex> lk(g_rot_mu);
+        auto it = g_rot_cache.find(key);
+        if (it != g_rot_cache.end()) return it->second;
+    }
+    const int p = h->p, RS = rot_map_size(p), nv = h->nV;
+    std::vector<std::array<int, 3>> vec((size_t)nv);
+    const int ne = h->st_off[8];
+    for (int e = 0; e < ne; e++) {
+        const int *v = &h->st_host[4 * (size_t)e];
+        vec[(size_t)(v[3] & 0xffff)] = {v[0], v[1], v[2]};
+    }
+    auto img = std::make_shared<std::vector<double>>((size_t)nv * 2 * RS);
+    // vectors in parallel on the host cores; u = c_L - c_M = -(source - target)
+    const unsigned nt = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    std::vector<std::thread> pool;
+    for (unsigned t = 0; t < nt; t++)
+        pool.emplace_back([&, t] {
+            for (int i = (int)t; i < nv; i += (int)nt) {
+                const double u[3] = {-(double)vec[i][0], -(double)vec[i][1], -(double)vec[i][2]};
+                rotation_maps(p, u, img->data() + (size_t)i * 2 * RS, img->data() + (size_t)i * 2 * RS + RS);
+            }
+        });
+    for (auto &th : pool) th.join();
+    std::lock_guard<std::mutex> lk(g_rot_mu);
+    g_rot_cache[key] = img;
+    return img;
+}
+
+void rotation_tables_update(fmm_ctx *h, bool fp64)
+{
+    const int want = fp64 ? 2 : 1;
+    if (h->rot_nv == h->nV && h->rot_kind == want && h->rot_tab.p) return;
+    auto img = rot_image(h);
+    if (fp64) {
+        h->rot_tab.ensure(sizeof(double) * img->size());
+        FMM_CUDA_TRY(cudaMemcpy(h->rot_tab.p, img->data(), sizeof(double) * img->size(), cudaMemcpyHostToDevice));
+    } else {
+        std::vector<float> f(img->size());
+        for (size_t i = 0; i < f.size(); i++) f[i] = (float)(*img)[i];
+        h->rot_tab.ensure(sizeof(float) * f.size());
+        FMM_CUDA_TRY(cudaMemcpy(h->rot_tab.p, f.data(), sizeof(float) * f.size(), cudaMemcpyHostToDevice));
+    }
+    h->rot_nv = h->nV;
+    h->rot_kind = want;
+}
+
+constexpr int ROT_W = 16;   // warps per CTA: one target row each
+constexpr int ROT_NK = 8;   // packed outputs per lane: p^2 <= 256
+
+// One CTA per tile of up to 16 target cells (one warp per cell). For each
+// stencil vector of the tile's set (the prefix that can reach the level), the
+// CTA stages the vector's two maps and the z factors g_l = l! / |u|^(l+1) in
+// shared memory; each warp whose cell has a source at that offset loads the
+// source's M~, rotates it (lane i: packed output i, a dot product over the
+// degree), translates along z (sums over j of equal order), rotates back and
+// adds into its registers. The cell's L~ is written once at the end.
+template <class T>
+__global__ void __launch_bounds__(32 * ROT_W) m2l_rot_k(int p, const M2LTile *__restrict__ tiles, const int *__restrict__ ntiles,
+                                                      const int *__restrict__ tgt, const int4 *__restrict__ xyz,
+                                                      const uint64_t *__restrict__ anchor, const LevelDesc *__restrict__ ld,
+                                                      const int *__restrict__ map_pool, const int4 *__restrict__ st,
+                                                      const int *__restrict__ st_off, const T *__restrict__ rot,
+                                                      const T *__restrict__ M, T *__restrict__ L)
+{
+    if ((int)blockIdx.x >= *ntiles) return;
+    const M2LTile td = tiles[blockIdx.x];
+    const int PP = p * p, RS = p * (4 * p * p - 1) / 3;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sA = reinterpret_cast<T *>(smem_raw);
+    T *sB = sA + RS;
+    T *sg = sB + RS;                       // 2p - 1 factors (2p slots)
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    T *sM = sg + 2 * p + (size_t)warp * 2 * PP;
+    T *sP = sM + PP;
+    // this warp's cell
+    int cell = -1, rl = td.level, px = 0, py = 0, pz = 0, ro = 0;
+    if (warp < td.count) {
+        cell = tgt[td.start + warp];
+        const int4 a = xyz[cell];
+        rl = a.w;
+        const int sh = FMM_MAXLEVEL - rl;
+        px = a.x >> sh;
+        py = a.y >> sh;
+        pz = a.z >> sh;
+        ro = (px & 1) | ((py & 1) << 1) | ((pz & 1) << 2);
+    }
+    const LevelDesc LD = ld[rl];
+    // this lane's packed outputs i = lane + 32 k: degree n, index a in the degree
+    int dn[ROT_NK], da[ROT_NK];
+#pragma unroll
+    for (int k = 0; k < ROT_NK; k++) {
+        const int i = lane + 32 * k;
+        int n = 0;
+        while ((n + 1) * (n + 1) <= i) n++;
+        dn[k] = i < PP ? n : -1;
+        da[k] = i - n * n;
+    }
+    double acc[ROT_NK];
+#pragma unroll
+    for (int k = 0; k < ROT_NK; k++) acc[k] = 0;
+
+    const int e0 = st_off[td.octant], nvec = st_off[10 + td.octant * (FMM_MAXLEVEL + 1) + td.level];
+    for (int e = e0; e < e0 + nvec; e++) {
+        const int4 v = st[e];
+        __syncthreads();
+        const T *src = rot + (size_t)(v.w & 0xffff) * 2 * RS;
+        for (int i = threadIdx.x; i < 2 * RS; i += blockDim.x) sA[i] = src[i];
+        if ((int)threadIdx.x < 2 * p - 1) {
+            const double d = sqrt((double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z);
+            double g = 1.0 / d;
+            for (int l = 1; l <= (int)threadIdx.x; l++) g *= (double)l / d;
+            sg[threadIdx.x] = (T)g;
+        }
+        __syncthreads();
+        int b = -1;
+        if (cell >= 0 && ((v.w >> (16 + ro)) & 1))
+            b = level_lookup(LD, map_pool, anchor, rl, px + v.x, py + v.y, pz + v.z);
+        if (b < 0) continue;  // warp-uniform
+        for (int i = lane; i < PP; i += 32) sM[i] = M[(size_t)b * PP + i];
+        __syncwarp();
+        // multipoles into the rotated frame
+#pragma unroll
+        for (int k = 0; k < ROT_NK; k++) {
+            if (dn[k] < 0) continue;
+            const int n = dn[k], K = 2 * n + 1;
+            const T *Ar = sA + n * (4 * n * n - 1) / 3 + da[k] * K;
+            const T *Mn = sM + n * n;
+            T s = 0;
+            for (int c = 0; c < K; c++) s += Ar[c] * Mn[c];
+            sP[lane + 32 * k] = s;
+        }
+        __syncwarp();
+        // translation along z: only equal orders couple
+#pragma unroll
+        for (int k = 0; k < ROT_NK; k++) {
+            if (dn[k] < 0) continue;
+            const int n = dn[k], a = da[k], m = (a + 1) >> 1;
+            T s = 0;
+            for (int j = m; j < p; j++) s += sP[j * j + a] * sg[j + n];
+            const bool im = a > 0 && !(a & 1);
+            sM[lane + 32 * k] = (((n + m) & 1) != im) ? -s : s;
+        }
+        __syncwarp();
+        // locals back to the original frame
+#pragma unroll
+        for (int k = 0; k < ROT_NK; k++) {
+            if (dn[k] < 0) continue;
+            const int n = dn[k], K = 2 * n + 1;
+            const T *Br = sB + n * (4 * n * n - 1) / 3 + da[k] * K;
+            const T *Ln = sM + n * n;
+            T s = 0;
+            for (int c = 0; c < K; c++) s += Br[c] * Ln[c];
+            acc[k] += s;
+        }
+        __syncwarp();
+    }
+    if (cell < 0) return;
+#pragma unroll
+    for (int k = 0; k < ROT_NK; k++)
+        if (dn[k] >= 0) L[(size_t)cell * PP + lane + 32 * k] += (T)acc[k];
+}
+
+template <class T>
+void m2l_rotation(fmm_ctx *h, T *L, const T *M)
+{
+    rotation_tables_update(h, sizeof(T) == 8);
+    const int p = h->p, PP = p * p, RS = rot_map_size(p);
+    const size_t smem = sizeof(T) * (2 * (size_t)RS + 2 * p + (size_t)ROT_W * 2 * PP);
+    static size_t set_smem[2] = {0, 0};
+    size_t &ss = set_smem[sizeof(T) == 8];
+    if (smem > ss) {
+        FMM_CUDA_TRY(cudaFuncSetAttribute(m2l_rot_k<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        ss = smem;
+    }
+    const int *ntiles = reinterpret_cast<const int *>(h->m2l_misc.as<unsigned>() + 24 * (FMM_MAXLEVEL + 1));
+    m2l_rot_k<T><<<h->ntiles_max, 32 * ROT_W, smem, h->work>>>(
+        p, h->m2l_tiles.as<M2LTile>(), ntiles, h->m2l_tgt.as<int>(), h->c_xyz.as<int4>(), h->c_anchor.as<uint64_t>(),
+        h->lvl_desc.as<LevelDesc>(), h->map_pool.as<int>(), h->st_dev.as<int4>(), stencil_offsets(h),
+        h->rot_tab.as<T>(), M, L);
+    count_launch(h);
+    check_launch("m2l rotation");
+}
+
+template void m2l_rotation<float>(fmm_ctx *, float *, const float *);
+template void m2l_rotation<double>(fmm_ctx *, double *, const double *);
+
+bool rotation_m2l_supported(fmm_ctx *h) { return h->p >= 1 && h->p <= 16; }
+int rotation_tile_rows() { return ROT_W; }
+
+}  // namespace fmm

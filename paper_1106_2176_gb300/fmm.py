@@ -24,7 +24,7 @@ _HEADER = os.path.join(_HERE, "..", "include", "fmm.h")
 FMM_OK, FMM_EINVAL, FMM_ENOMEM, FMM_ESTATE, FMM_ECUDA, FMM_ENONFINITE, FMM_ENODEV = 0, -1, -2, -3, -4, -5, -6
 FMM_F32, FMM_F64, FMM_HOST_MEM = 0, 1, 0x100
 FMM_FP64, FMM_MIXED = 0, 1
-FMM_M2L_AUTO, FMM_M2L_TENSOR, FMM_M2L_CUDACORE = 0, 1, 2
+FMM_M2L_AUTO, FMM_M2L_TENSOR, FMM_M2L_CUDACORE, FMM_M2L_ROTATION = 0, 1, 2, 3
 
 _ERRNAMES = {FMM_EINVAL: "FMM_EINVAL", FMM_ENOMEM: "FMM_ENOMEM", FMM_ESTATE: "FMM_ESTATE",
              FMM_ECUDA: "FMM_ECUDA", FMM_ENONFINITE: "FMM_ENONFINITE", FMM_ENODEV: "FMM_ENODEV"}
@@ -79,6 +79,7 @@ def lib():
     L.fmm_set_overlap.argtypes = [_vp, i32]
     L.fmm_set_stream.argtypes = [_vp, _vp]
     L.fmm_set_uniform_path.argtypes = [_vp, ctypes.c_int]
+    L.fmm_m2l_rotation_host.argtypes = [ctypes.c_int, _vp, _vp, _vp]
     L.fmm_build.argtypes = [_vp, _vp, _vp, i64, i32]
     L.fmm_evaluate.argtypes = [_vp, _vp, _vp]
     L.fmm_get_stats.argtypes = [_vp, ctypes.POINTER(fmm_stats)]
@@ -137,7 +138,8 @@ class FMM:
         self.precision = precision
 
     def set_m2l_engine(self, engine):
-        e = {"auto": FMM_M2L_AUTO, "tensor": FMM_M2L_TENSOR, "cudacore": FMM_M2L_CUDACORE}[engine]
+        e = {"auto": FMM_M2L_AUTO, "tensor": FMM_M2L_TENSOR, "cudacore": FMM_M2L_CUDACORE,
+             "rotation": FMM_M2L_ROTATION}[engine]
         _check(lib().fmm_set_m2l_engine(self._h, e), self._h)
 
     def set_overlap(self, on):
@@ -316,3 +318,15 @@ def unscale(M, L, level, R0, p):
                 out[:, n * n + n + m] = v
                 out[:, n * n + n - m] = (-1) ** m * np.conj(v)
     return outM, outL
+
+
+def m2l_rotation_host(p, u, M):
+    """Rotation-based M2L of one packed expansion on the host (FP64): L for
+    translation u = c_L - c_M. Runs the library's host code; no GPU needed."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    M = np.ascontiguousarray(M, dtype=np.float64)
+    if M.shape != (p * p,) or u.shape != (3,):
+        raise ValueError("M must have p^2 entries and u 3")
+    out = np.zeros(p * p)
+    _check(lib().fmm_m2l_rotation_host(int(p), _vp(u.ctypes.data), _vp(M.ctypes.data), _vp(out.ctypes.data)))
+    return out
