@@ -1195,7 +1195,7 @@ static int floordiv2(int a) { return a >= 0 ? a / 2 : -((-a + 1) / 2); }
 int m2l_tile_size(fmm_ctx *h)
 {
     if (h->precision == FMM_MIXED && h->engine_used == FMM_M2L_TENSOR) return 128;
-    if (h->engine_used == FMM_M2L_ROTATION) return rotation_tile_rows();
+    if (h->engine_used == FMM_M2L_ROTATION) return rotation_tile_rows(h);
     const int ntri = h->p * (h->p + 1) / 2;
     int t = std::min(32, (M2L_CC_T * M2L_CC_ACC) / ntri);
     return std::max(t, 1);

@@ -225,7 +225,7 @@ void m2l_rotation_ref(int p, const double u[3], const double *M, double *L);
 template <class T>
 void m2l_rotation(fmm_ctx *h, T *L, const T *M);  // same-level M2L of all tiles by rotation
 bool rotation_m2l_supported(fmm_ctx *h);           // p <= 16 (the maps of a vector fit shared memory)
-int rotation_tile_rows();
+int rotation_tile_rows(fmm_ctx *h);  // target cells per tile (two per warp)
 // per (octant, level): how many of the octant's entries (shortest first) can
 // reach a cell of that level in the current tree; written after the offsets
 void stencil_levels(fmm_ctx *h, cudaStream_t s);

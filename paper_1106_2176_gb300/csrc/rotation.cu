@@ -264,8 +264,20 @@ void m2l_rotation_ref(int p, const double u[3], const double *M, double *L)
 // ---------------------------------------------------------------------------
 namespace fmm {
 
-// maps of every stencil vector, [A | B] per vector id (2 rot_map_size(p)
-// doubles), one host image per process for each (p, MAC constant, stencil bound)
+// Device layout of one vector's data (padded so that rows and degree blocks
+// start on 16 bytes): A then B, degree n a block of K = 2n+1 rows of
+// K4 = K rounded up to 4 entries (zeros past K), then the factors
+// g_l = l! / |u|^(l+1), l < 2p - 1, rounded up to 4 entries.
+static int k4(int n) { return (2 * n + 1 + 3) & ~3; }
+static int rot_blocks(int p)  // entries of A (or B), padded
+{
+    int s = 0;
+    for (int n = 0; n < p; n++) s += (2 * n + 1) * k4(n);
+    return s;
+}
+static int rot_vec_stride(int p) { return 2 * rot_blocks(p) + ((2 * p - 1 + 3) & ~3); }
+
+// one host image per process for each (p, MAC constant, stencil bound)
 static std::mutex g_rot_mu;
 static std::map<std::tuple<int, double, int>, std::shared_ptr<const std::vector<double>>> g_rot_cache;
 
@@ -277,22 +289,40 @@ static std::shared_ptr<const std::vector<double>> rot_image(fmm_ctx *h)
         auto it = g_rot_cache.find(key);
         if (it != g_rot_cache.end()) return it->second;
     }
-    const int p = h->p, RS = rot_map_size(p), nv = h->nV;
+    const int p = h->p, RS = rot_map_size(p), nv = h->nV, VS = rot_vec_stride(p), SA = rot_blocks(p);
     std::vector<std::array<int, 3>> vec((size_t)nv);
     const int ne = h->st_off[8];
     for (int e = 0; e < ne; e++) {
         const int *v = &h->st_host[4 * (size_t)e];
         vec[(size_t)(v[3] & 0xffff)] = {v[0], v[1], v[2]};
     }
-    auto img = std::make_shared<std::vector<double>>((size_t)nv * 2 * RS);
+    auto img = std::make_shared<std::vector<double>>((size_t)nv * VS, 0.0);
     // vectors in parallel on the host cores; u = c_L - c_M = -(source - target)
     const unsigned nt = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
     std::vector<std::thread> pool;
     for (unsigned t = 0; t < nt; t++)
         pool.emplace_back([&, t] {
+            std::vector<double> A(RS), B(RS);
             for (int i = (int)t; i < nv; i += (int)nt) {
                 const double u[3] = {-(double)vec[i][0], -(double)vec[i][1], -(double)vec[i][2]};
-                rotation_maps(p, u, img->data() + (size_t)i * 2 * RS, img->data() + (size_t)i * 2 * RS + RS);
+                rotation_maps(p, u, A.data(), B.data());
+                double *o = img->data() + (size_t)i * VS;
+                int off = 0;
+                for (int n = 0; n < p; n++) {
+                    const int K = 2 * n + 1, K4 = k4(n);
+                    for (int r = 0; r < K; r++)
+                        for (int c = 0; c < K; c++) {
+                            o[off + r * K4 + c] = A[rot_deg_off(n) + r * K + c];
+                            o[SA + off + r * K4 + c] = B[rot_deg_off(n) + r * K + c];
+                        }
+                    off += K * K4;
+                }
+                const double d = std::sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+                double g = 1.0 / d;
+                for (int l = 0; l < 2 * p - 1; l++) {
+                    if (l) g *= (double)l / d;
+                    o[2 * SA + l] = g;
+                }
             }
         });
     for (auto &th : pool) th.join();
@@ -319,128 +349,217 @@ void rotation_tables_update(fmm_ctx *h, bool fp64)
     h->rot_kind = want;
 }
 
-constexpr int ROT_W = 16;   // warps per CTA: one target row each
-constexpr int ROT_NK = 8;   // packed outputs per lane: p^2 <= 256
-
-// One CTA per tile of up to 16 target cells (one warp per cell). For each
-// stencil vector of the tile's set (the prefix that can reach the level), the
-// CTA stages the vector's two maps and the z factors g_l = l! / |u|^(l+1) in
-// shared memory; each warp whose cell has a source at that offset loads the
-// source's M~, rotates it (lane i: packed output i, a dot product over the
-// degree), translates along z (sums over j of equal order), rotates back and
-// adds into its registers. The cell's L~ is written once at the end.
+// 16-byte vectors of T and their dot product
 template <class T>
-__global__ void __launch_bounds__(32 * ROT_W) m2l_rot_k(int p, const M2LTile *__restrict__ tiles, const int *__restrict__ ntiles,
-                                                      const int *__restrict__ tgt, const int4 *__restrict__ xyz,
-                                                      const uint64_t *__restrict__ anchor, const LevelDesc *__restrict__ ld,
-                                                      const int *__restrict__ map_pool, const int4 *__restrict__ st,
-                                                      const int *__restrict__ st_off, const T *__restrict__ rot,
-                                                      const T *__restrict__ M, T *__restrict__ L)
+struct V16;
+template <>
+struct V16<float> {
+    using type = float4;
+    static constexpr int n = 4;
+    static __device__ __forceinline__ float dot(float4 a, float4 b, float s)
+    {
+        return fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, fmaf(a.x, b.x, s))));
+    }
+};
+template <>
+struct V16<double> {
+    using type = double2;
+    static constexpr int n = 2;
+    static __device__ __forceinline__ double dot(double2 a, double2 b, double s) { return fma(a.y, b.y, fma(a.x, b.x, s)); }
+};
+
+template <class T>
+struct RotCfg {
+    static constexpr int W = 8;  // warps per CTA, two target cells each
+    static constexpr int MINB = sizeof(T) == 4 ? 2 : 1;  // CTAs per SM the registers are sized for
+    static constexpr int NK = 8;                       // packed outputs per lane: p^2 <= 256
+    static constexpr int NL = 10;                      // padded entries per lane: sum K4 <= 320
+};
+
+// One CTA per tile of up to 2W target cells, two per warp. For each stencil
+// vector of the tile's set (the prefix that can reach the level), the CTA
+// stages the vector's maps and z factors in shared memory; each warp loads
+// the M~ of its two cells' sources at that offset (zero where there is none),
+// rotates them (lane i: packed output i, 16-byte dot products over its
+// degree's padded row, one map entry for both cells), translates along z
+// (sums over j of equal order), rotates back and adds into FP64 registers.
+// The cells' L~ is written once at the end.
+template <class T>
+__global__ void __launch_bounds__(32 * RotCfg<T>::W, RotCfg<T>::MINB) m2l_rot_k(int p, const M2LTile *__restrict__ tiles,
+                                                             const int *__restrict__ ntiles, const int *__restrict__ tgt,
+                                                             const int4 *__restrict__ xyz, const uint64_t *__restrict__ anchor,
+                                                             const LevelDesc *__restrict__ ld, const int *__restrict__ map_pool,
+                                                             const int4 *__restrict__ st, const int *__restrict__ st_off,
+                                                             const T *__restrict__ rot, int VS, int SA, int PP4,
+                                                             const T *__restrict__ M, T *__restrict__ L)
 {
+    using C = RotCfg<T>;
+    using VT = typename V16<T>::type;
+    constexpr int VN = V16<T>::n;
     if ((int)blockIdx.x >= *ntiles) return;
     const M2LTile td = tiles[blockIdx.x];
-    const int PP = p * p, RS = p * (4 * p * p - 1) / 3;
+    const int PP = p * p;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *sA = reinterpret_cast<T *>(smem_raw);
-    T *sB = sA + RS;
-    T *sg = sB + RS;                       // 2p - 1 factors (2p slots)
+    T *sTab = reinterpret_cast<T *>(smem_raw);
+    const T *sA = sTab, *sB = sTab + SA, *sg = sTab + 2 * SA;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    T *sM = sg + 2 * p + (size_t)warp * 2 * PP;
-    T *sP = sM + PP;
-    // this warp's cell
-    int cell = -1, rl = td.level, px = 0, py = 0, pz = 0, ro = 0;
-    if (warp < td.count) {
-        cell = tgt[td.start + warp];
-        const int4 a = xyz[cell];
-        rl = a.w;
-        const int sh = FMM_MAXLEVEL - rl;
-        px = a.x >> sh;
-        py = a.y >> sh;
-        pz = a.z >> sh;
-        ro = (px & 1) | ((py & 1) << 1) | ((pz & 1) << 2);
-    }
-    const LevelDesc LD = ld[rl];
-    // this lane's packed outputs i = lane + 32 k: degree n, index a in the degree
-    int dn[ROT_NK], da[ROT_NK];
+    T *sM[2], *sP[2];
+    sM[0] = sTab + VS + (size_t)warp * 4 * PP4;
+    sM[1] = sM[0] + PP4;
+    sP[0] = sM[0] + 2 * PP4;
+    sP[1] = sM[0] + 3 * PP4;
+    // the warp's two cells
+    int cell[2], rl[2], px[2], py[2], pz[2], ro[2];
 #pragma unroll
-    for (int k = 0; k < ROT_NK; k++) {
+    for (int r = 0; r < 2; r++) {
+        cell[r] = -1;
+        rl[r] = td.level;
+        px[r] = py[r] = pz[r] = ro[r] = 0;
+        if (2 * warp + r < td.count) {
+            cell[r] = tgt[td.start + 2 * warp + r];
+            const int4 a = xyz[cell[r]];
+            rl[r] = a.w;
+            const int sh = FMM_MAXLEVEL - a.w;
+            px[r] = a.x >> sh;
+            py[r] = a.y >> sh;
+            pz[r] = a.z >> sh;
+            ro[r] = (px[r] & 1) | ((py[r] & 1) << 1) | ((pz[r] & 1) << 2);
+        }
+    }
+    // this lane's packed outputs i = lane + 32 k: degree n, index a in the
+    // degree, position of the entry in the padded layout and of its map rows
+    int on[C::NK], oa[C::NK], opos[C::NK], orow[C::NK];
+#pragma unroll
+    for (int k = 0; k < C::NK; k++) {
         const int i = lane + 32 * k;
-        int n = 0;
-        while ((n + 1) * (n + 1) <= i) n++;
-        dn[k] = i < PP ? n : -1;
-        da[k] = i - n * n;
+        int n = 0, pos = 0, row = 0;
+        while ((n + 1) * (n + 1) <= i) {
+            const int K4 = (2 * n + 1 + 3) & ~3;
+            pos += K4;
+            row += (2 * n + 1) * K4;
+            n++;
+        }
+        on[k] = i < PP ? n : -1;
+        oa[k] = i - n * n;
+        opos[k] = pos + oa[k];
+        orow[k] = row + oa[k] * ((2 * n + 1 + 3) & ~3);
     }
-    double acc[ROT_NK];
+    // this lane's padded entries j = lane + 32 t: source index in the packed M~ (-1: padding)
+    int lsrc[C::NL];
 #pragma unroll
-    for (int k = 0; k < ROT_NK; k++) acc[k] = 0;
+    for (int t = 0; t < C::NL; t++) {
+        const int j = lane + 32 * t;
+        int n = 0, pos = 0;
+        while (n < p && pos + ((2 * n + 1 + 3) & ~3) <= j) {
+            pos += (2 * n + 1 + 3) & ~3;
+            n++;
+        }
+        lsrc[t] = (j < PP4 && j - pos < 2 * n + 1) ? n * n + (j - pos) : -1;
+    }
+    for (int j = lane; j < PP4; j += 32) sP[0][j] = sP[1][j] = T(0);
+    double acc[2][C::NK];
+#pragma unroll
+    for (int k = 0; k < C::NK; k++) acc[0][k] = acc[1][k] = 0.0;
 
     const int e0 = st_off[td.octant], nvec = st_off[10 + td.octant * (FMM_MAXLEVEL + 1) + td.level];
     for (int e = e0; e < e0 + nvec; e++) {
         const int4 v = st[e];
         __syncthreads();
-        const T *src = rot + (size_t)(v.w & 0xffff) * 2 * RS;
-        for (int i = threadIdx.x; i < 2 * RS; i += blockDim.x) sA[i] = src[i];
-        if ((int)threadIdx.x < 2 * p - 1) {
-            const double d = sqrt((double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z);
-            double g = 1.0 / d;
-            for (int l = 1; l <= (int)threadIdx.x; l++) g *= (double)l / d;
-            sg[threadIdx.x] = (T)g;
+        {
+            const VT *src = reinterpret_cast<const VT *>(rot + (size_t)(v.w & 0xffff) * VS);
+            VT *dst = reinterpret_cast<VT *>(sTab);
+            for (int i = threadIdx.x; i < VS / VN; i += blockDim.x) dst[i] = src[i];
         }
         __syncthreads();
-        int b = -1;
-        if (cell >= 0 && ((v.w >> (16 + ro)) & 1))
-            b = level_lookup(LD, map_pool, anchor, rl, px + v.x, py + v.y, pz + v.z);
-        if (b < 0) continue;  // warp-uniform
-        for (int i = lane; i < PP; i += 32) sM[i] = M[(size_t)b * PP + i];
+        int b[2];
+#pragma unroll
+        for (int r = 0; r < 2; r++) {
+            b[r] = -1;
+            if (cell[r] >= 0 && ((v.w >> (16 + ro[r])) & 1))
+                b[r] = level_lookup(ld[rl[r]], map_pool, anchor, rl[r], px[r] + v.x, py[r] + v.y, pz[r] + v.z);
+        }
+        if (b[0] < 0 && b[1] < 0) continue;  // warp-uniform
+#pragma unroll
+        for (int r = 0; r < 2; r++)
+#pragma unroll
+            for (int t = 0; t < C::NL; t++) {
+                const int j = lane + 32 * t;
+                if (j < PP4) sM[r][j] = (b[r] >= 0 && lsrc[t] >= 0) ? M[(size_t)b[r] * PP + lsrc[t]] : T(0);
+            }
         __syncwarp();
         // multipoles into the rotated frame
 #pragma unroll
-        for (int k = 0; k < ROT_NK; k++) {
-            if (dn[k] < 0) continue;
-            const int n = dn[k], K = 2 * n + 1;
-            const T *Ar = sA + n * (4 * n * n - 1) / 3 + da[k] * K;
-            const T *Mn = sM + n * n;
-            T s = 0;
-            for (int c = 0; c < K; c++) s += Ar[c] * Mn[c];
-            sP[lane + 32 * k] = s;
+        for (int k = 0; k < C::NK; k++) {
+            if (on[k] < 0) continue;
+            const int n = on[k], K4 = (2 * n + 1 + 3) & ~3, base = opos[k] - oa[k];
+            const VT *ar = reinterpret_cast<const VT *>(sA + orow[k]);
+            const VT *m0 = reinterpret_cast<const VT *>(sM[0] + base), *m1 = reinterpret_cast<const VT *>(sM[1] + base);
+            T s0 = 0, s1 = 0;
+            for (int c = 0; c < K4 / VN; c++) {
+                const VT w = ar[c];
+                s0 = V16<T>::dot(w, m0[c], s0);
+                s1 = V16<T>::dot(w, m1[c], s1);
+            }
+            sP[0][opos[k]] = s0;
+            sP[1][opos[k]] = s1;
         }
         __syncwarp();
         // translation along z: only equal orders couple
 #pragma unroll
-        for (int k = 0; k < ROT_NK; k++) {
-            if (dn[k] < 0) continue;
-            const int n = dn[k], a = da[k], m = (a + 1) >> 1;
-            T s = 0;
-            for (int j = m; j < p; j++) s += sP[j * j + a] * sg[j + n];
-            const bool im = a > 0 && !(a & 1);
-            sM[lane + 32 * k] = (((n + m) & 1) != im) ? -s : s;
+        for (int k = 0; k < C::NK; k++) {
+            if (on[k] < 0) continue;
+            const int n = on[k], a = oa[k], m = (a + 1) >> 1;
+            int pj = 0;
+            for (int j = 0; j < m; j++) pj += (2 * j + 1 + 3) & ~3;
+            T s0 = 0, s1 = 0;
+            for (int j = m; j < p; j++) {
+                const T g = sg[j + n];
+                s0 += sP[0][pj + a] * g;
+                s1 += sP[1][pj + a] * g;
+                pj += (2 * j + 1 + 3) & ~3;
+            }
+            const bool neg = (((n + m) & 1) != 0) != (a > 0 && !(a & 1));
+            sM[0][opos[k]] = neg ? -s0 : s0;
+            sM[1][opos[k]] = neg ? -s1 : s1;
         }
         __syncwarp();
         // locals back to the original frame
 #pragma unroll
-        for (int k = 0; k < ROT_NK; k++) {
-            if (dn[k] < 0) continue;
-            const int n = dn[k], K = 2 * n + 1;
-            const T *Br = sB + n * (4 * n * n - 1) / 3 + da[k] * K;
-            const T *Ln = sM + n * n;
-            T s = 0;
-            for (int c = 0; c < K; c++) s += Br[c] * Ln[c];
-            acc[k] += s;
+        for (int k = 0; k < C::NK; k++) {
+            if (on[k] < 0) continue;
+            const int n = on[k], K4 = (2 * n + 1 + 3) & ~3, base = opos[k] - oa[k];
+            const VT *br = reinterpret_cast<const VT *>(sB + orow[k]);
+            const VT *l0 = reinterpret_cast<const VT *>(sM[0] + base), *l1 = reinterpret_cast<const VT *>(sM[1] + base);
+            T s0 = 0, s1 = 0;
+            for (int c = 0; c < K4 / VN; c++) {
+                const VT w = br[c];
+                s0 = V16<T>::dot(w, l0[c], s0);
+                s1 = V16<T>::dot(w, l1[c], s1);
+            }
+            acc[0][k] += s0;
+            acc[1][k] += s1;
         }
         __syncwarp();
     }
-    if (cell < 0) return;
 #pragma unroll
-    for (int k = 0; k < ROT_NK; k++)
-        if (dn[k] >= 0) L[(size_t)cell * PP + lane + 32 * k] += (T)acc[k];
+    for (int r = 0; r < 2; r++) {
+        if (cell[r] < 0) continue;
+#pragma unroll
+        for (int k = 0; k < C::NK; k++)
+            if (on[k] >= 0) L[(size_t)cell[r] * PP + lane + 32 * k] += (T)acc[r][k];
+    }
 }
 
 template <class T>
 void m2l_rotation(fmm_ctx *h, T *L, const T *M)
 {
+    using C = RotCfg<T>;
     rotation_tables_update(h, sizeof(T) == 8);
-    const int p = h->p, PP = p * p, RS = rot_map_size(p);
-    const size_t smem = sizeof(T) * (2 * (size_t)RS + 2 * p + (size_t)ROT_W * 2 * PP);
+    const int p = h->p, VS = rot_vec_stride(p), SA = rot_blocks(p);
+    int PP4 = 0;
+    for (int n = 0; n < p; n++) PP4 += k4(n);
+    if (PP4 > 32 * C::NL) throw Error{FMM_EINVAL, "rotation M2L: p too large"};
+    const size_t smem = sizeof(T) * ((size_t)VS + (size_t)C::W * 4 * PP4);
     static size_t set_smem[2] = {0, 0};
     size_t &ss = set_smem[sizeof(T) == 8];
     if (smem > ss) {
@@ -448,10 +567,10 @@ void m2l_rotation(fmm_ctx *h, T *L, const T *M)
         ss = smem;
     }
     const int *ntiles = reinterpret_cast<const int *>(h->m2l_misc.as<unsigned>() + 24 * (FMM_MAXLEVEL + 1));
-    m2l_rot_k<T><<<h->ntiles_max, 32 * ROT_W, smem, h->work>>>(
+    m2l_rot_k<T><<<h->ntiles_max, 32 * C::W, smem, h->work>>>(
         p, h->m2l_tiles.as<M2LTile>(), ntiles, h->m2l_tgt.as<int>(), h->c_xyz.as<int4>(), h->c_anchor.as<uint64_t>(),
         h->lvl_desc.as<LevelDesc>(), h->map_pool.as<int>(), h->st_dev.as<int4>(), stencil_offsets(h),
-        h->rot_tab.as<T>(), M, L);
+        h->rot_tab.as<T>(), VS, SA, PP4, M, L);
     count_launch(h);
     check_launch("m2l rotation");
 }
@@ -460,6 +579,6 @@ template void m2l_rotation<float>(fmm_ctx *, float *, const float *);
 template void m2l_rotation<double>(fmm_ctx *, double *, const double *);
 
 bool rotation_m2l_supported(fmm_ctx *h) { return h->p >= 1 && h->p <= 16; }
-int rotation_tile_rows() { return ROT_W; }
+int rotation_tile_rows(fmm_ctx *h) { return 2 * (h->precision == FMM_FP64 ? RotCfg<double>::W : RotCfg<float>::W); }
 
 }  // namespace fmm
