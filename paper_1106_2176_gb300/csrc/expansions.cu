@@ -829,7 +829,7 @@ constexpr size_t m2lx_f_smem()
 }
 
 template <int P>
-__global__ void __launch_bounds__(32 * M2LX_FW, 2) m2lx_f_k(int nc, const int *__restrict__ ptr,
+__global__ void __launch_bounds__(32 * M2LX_FW, 3) m2lx_f_k(int nc, const int *__restrict__ ptr,
                                                             const int *__restrict__ src, const int4 *__restrict__ xyz,
                                                             const float *__restrict__ M, float *__restrict__ L)
 {
