@@ -48,12 +48,30 @@ def _throughput_ms(members, p, theta, ncrit, precision, streams, reps=2):
     return best
 
 
+def size_bucket(n):
+    """Half a decade of n: floor(2 log10 n)."""
+    return int(math.floor(2 * math.log10(max(int(n), 1))))
+
+
+def assign_streams(sizes, nstreams):
+    """Largest system first, each to the stream with the fewest particles so
+    far (ties to the lowest stream); returns the stream of each system."""
+    order = sorted(range(len(sizes)), key=lambda i: (-int(sizes[i]), i))
+    load = [0] * nstreams
+    lane = [0] * len(sizes)
+    for i in order:
+        s = min(range(nstreams), key=lambda k: (load[k], k))
+        lane[i] = s
+        load[s] += int(sizes[i])
+    return lane
+
+
 def tune_buckets(systems, p, theta, precision, candidates=NCRIT_CANDIDATES, nstreams=8, per_bucket=8):
     """ncrit per size bucket (half a decade of n): the candidate that
     evaluates up to per_bucket members of the bucket (spread over its sizes),
     side by side on nstreams streams, in the least time.
     Returns ({bucket: ncrit}, bucket of each system)."""
-    bucket = [int(math.floor(2 * math.log10(max(int(x.shape[0]), 1)))) for x, _ in systems]
+    bucket = [size_bucket(x.shape[0]) for x, _ in systems]
     streams = [torch.cuda.Stream() for _ in range(nstreams)]
     choice = {}
     for b in sorted(set(bucket)):
@@ -83,13 +101,7 @@ class FMMBatch:
             self.out.append(f.evaluate())  # warm-up: every workspace exists from here on
         torch.cuda.synchronize()
         self.nstreams = max(1, int(streams))
-        order = sorted(range(len(systems)), key=lambda i: -systems[i][0].shape[0])
-        load = [0] * self.nstreams
-        self.lane = [0] * len(systems)
-        for i in order:
-            s = min(range(self.nstreams), key=lambda k: load[k])
-            self.lane[i] = s
-            load[s] += systems[i][0].shape[0]
+        self.lane = assign_streams([x.shape[0] for x, _ in systems], self.nstreams)
         self.graph = None
         self.particles = sum(int(x.shape[0]) for x, _ in systems)
 

@@ -69,39 +69,6 @@ __host__ __device__ void regular_tri(int P, T x, T y, T z, T *re, T *im, int st)
     }
 }
 
-// I_n^m, 0 <= m <= n < Q, triangular storage; x != 0
-template <class T>
-__host__ __device__ void irregular_tri(int Q, T x, T y, T z, T *re, T *im)
-{
-    const T r2 = x * x + y * y + z * z;
-    const T ir2 = T(1) / r2;
-    T mre = sqrt(ir2), mim = T(0);
-    for (int m = 0; m < Q; m++) {
-        if (m > 0) {
-            const T f = T(2 * m - 1) * ir2;
-            const T a = (mre * x - mim * y) * f;
-            const T b = (mre * y + mim * x) * f;
-            mre = a;
-            mim = b;
-        }
-        re[tri(m, m)] = mre;
-        im[tri(m, m)] = mim;
-        if (m + 1 >= Q) continue;
-        const T f1 = T(2 * m + 1) * z * ir2;
-        T p2re = mre, p2im = mim, p1re = mre * f1, p1im = mim * f1;
-        re[tri(m + 1, m)] = p1re;
-        im[tri(m + 1, m)] = p1im;
-        for (int n = m + 2; n < Q; n++) {
-            const T a = T(2 * n - 1) * z, b = T((n + m - 1) * (n - m - 1));
-            const T cre = (a * p1re - b * p2re) * ir2;
-            const T cim = (a * p1im - b * p2im) * ir2;
-            re[tri(n, m)] = cre;
-            im[tri(n, m)] = cim;
-            p2re = p1re; p2im = p1im; p1re = cre; p1im = cim;
-        }
-    }
-}
-
 // complex coefficient (n, m), any -n <= m <= n, of a packed real expansion
 template <class T>
 __device__ __forceinline__ void cget(const T *__restrict__ X, int n, int m, T &re, T &im)
