@@ -24,12 +24,18 @@ def tune_ncrit(x, q, p, theta, precision="mixed", candidates=DEFAULT_CANDIDATES,
                 return int(d[key]["ncrit"]), d[key]["ms"]
         except Exception:
             pass
+    from .fmm import FMMError
+
     times = {}
     seen_depth = {}
     for nc in candidates:
         f = FMM(x.shape[0], p=p, theta=theta, ncrit=nc, precision=precision)
-        f.build(x, q)
-        f.evaluate()
+        try:
+            f.build(x, q)
+            f.evaluate()
+        except FMMError:  # e.g. lists beyond 2^31 entries for too small a leaf: not a candidate
+            f.close()
+            continue
         depth = f.stats()["depth"]
         sig = (depth, f.stats()["nleaves"])
         if sig in seen_depth:  # same tree as a smaller candidate: same cost
@@ -51,6 +57,8 @@ def tune_ncrit(x, q, p, theta, precision="mixed", candidates=DEFAULT_CANDIDATES,
             best = min(best, a.elapsed_time(b))
         times[nc] = best
         f.close()
+    if not times:
+        raise RuntimeError("tune_ncrit: no candidate leaf size could be built")
     best_nc = min(times, key=lambda k: (times[k], k))
     if cache and key:
         try:
