@@ -115,8 +115,8 @@ FMM_API int fmm_create(int64_t N, int p, double theta, int ncrit, fmm_handle *ou
 FMM_API int fmm_set_precision(fmm_handle h, int mode);
 
 /* Select the M2L engine; takes effect at the next build. FMM_M2L_AUTO: the
- * tensor cores for FMM_MIXED (p <= 11), the CUDA-core dense contraction
- * otherwise. FMM_M2L_TENSOR: split-TF32 tcgen05 contraction (FMM_MIXED,
+ * tensor cores for FMM_MIXED with p <= 11, otherwise rotation for p <= 16
+ * (FP64 included), otherwise the CUDA-core dense contraction. FMM_M2L_TENSOR: split-TF32 tcgen05 contraction (FMM_MIXED,
  * p <= 11). FMM_M2L_CUDACORE: dense O(p^4) contraction on the CUDA cores.
  * FMM_M2L_ROTATION: rotate each translation onto the z axis, translate along
  * z and rotate back, O(p^3) per pair (either precision, p <= 16). The

@@ -278,10 +278,14 @@ int fmm_build(fmm_handle h, const void *x, const void *q, int64_t n, int dtype)
     h->dtype = dt;
     h->host_mem = host;
     h->precision = h->precision_req;
-    h->engine_used = h->engine_req == FMM_M2L_ROTATION ? FMM_M2L_ROTATION
-                     : (h->precision == FMM_MIXED && h->engine_req != FMM_M2L_CUDACORE && fmm::tensor_m2l_supported(h))
-                         ? FMM_M2L_TENSOR
-                         : FMM_M2L_CUDACORE;
+    // automatic choice: the tensor cores for the mixed path where they apply,
+    // otherwise rotation (O(p^3), p <= 16), otherwise the dense CUDA-core path
+    const bool tc = h->precision == FMM_MIXED && fmm::tensor_m2l_supported(h);
+    if (h->engine_req == FMM_M2L_ROTATION) h->engine_used = FMM_M2L_ROTATION;
+    else if (h->engine_req == FMM_M2L_CUDACORE) h->engine_used = FMM_M2L_CUDACORE;
+    else if (tc) h->engine_used = FMM_M2L_TENSOR;
+    else if (h->engine_req == FMM_M2L_AUTO && fmm::rotation_m2l_supported(h)) h->engine_used = FMM_M2L_ROTATION;
+    else h->engine_used = FMM_M2L_CUDACORE;
     FMM_CUDA_TRY(cudaEventRecord(h->tm.ev[0], s));
     const size_t es = dt == FMM_F64 ? 8 : 4;
     const void *xd = x, *qd = q;
