@@ -211,6 +211,17 @@ def phase_rooflines(phase, st, N, p, peaks, nsm):
     return out
 
 
+def job_rate(n_per_rank, ms, world, dist=None, device="cpu"):
+    """Whole-job rate of a step: every rank's particles over the slowest rank's
+    time (MAX over ranks). Returns (particles/s, ms of the slowest rank)."""
+    import torch
+    if dist is not None and world > 1:
+        t = torch.tensor([float(ms)], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return n_per_rank * world / (ms / 1000.0), ms
+
+
 def run_e2e(a, x, q, N, ncrit, world, dist, dev):
     """Same metric through the C ABI with pinned host buffers: every step copies
     x and q to the device and phi and grad back."""
@@ -231,12 +242,9 @@ def run_e2e(a, x, q, N, ncrit, world, dist, dev):
         fh.evaluate(ph.numpy(), gh.numpy())
     torch.cuda.synchronize()
     e2e_ms = 1000.0 * (time.perf_counter() - t0) / a.steps
-    if dist:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_value, e2e_ms = job_rate(N, e2e_ms, world, dist, dev)
     fh.close()
-    e2e = {"value": N * world / (e2e_ms / 1000.0), "unit": "particles/s", "ms_per_step": e2e_ms,
+    e2e = {"value": e2e_value, "unit": "particles/s", "ms_per_step": e2e_ms,
            "h2d_bytes_per_step": int(x.nbytes + q.nbytes), "d2h_bytes_per_step": int(ph.numpy().nbytes + gh.numpy().nbytes)}
 
     return e2e
@@ -468,11 +476,7 @@ def main():
     ms = e0.elapsed_time(e1) / a.steps
     st1 = f.stats()
     launches = (st1["kernel_launches"] - st0["kernel_launches"]) // a.steps
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = N * world / (ms / 1000.0)
+    value, ms = job_rate(N, ms, world, dist, dev)
 
     # accuracy: sampled targets against the FP64 direct sum on the GPU
     rel = lambda u, v: float(torch.linalg.norm(u - v) / torch.linalg.norm(v))
