@@ -27,6 +27,7 @@
 #include <array>
 #include <cmath>
 #include <complex>
+#include <exception>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -300,8 +301,10 @@ static std::shared_ptr<const std::vector<double>> rot_image(fmm_ctx *h)
     // vectors in parallel on the host cores; u = c_L - c_M = -(source - target)
     const unsigned nt = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
     std::vector<std::thread> pool;
+    std::vector<std::exception_ptr> fault(nt);  // an exception stays in its thread until the join
     for (unsigned t = 0; t < nt; t++)
         pool.emplace_back([&, t] {
+            try {
             std::vector<double> A(RS), B(RS);
             for (int i = (int)t; i < nv; i += (int)nt) {
                 const double u[3] = {-(double)vec[i][0], -(double)vec[i][1], -(double)vec[i][2]};
@@ -324,8 +327,13 @@ static std::shared_ptr<const std::vector<double>> rot_image(fmm_ctx *h)
                     o[2 * SA + l] = g;
                 }
             }
+            } catch (...) {
+                fault[t] = std::current_exception();
+            }
         });
     for (auto &th : pool) th.join();
+    for (auto &f : fault)
+        if (f) std::rethrow_exception(f);
     std::lock_guard<std::mutex> lk(g_rot_mu);
     g_rot_cache[key] = img;
     return img;
