@@ -66,11 +66,12 @@ enum { FMM_F32 = 0, FMM_F64 = 1, FMM_HOST_MEM = 0x100 };
 enum {
     FMM_FP64 = 0,  /* every stage in FP64 (the on-device reference path) */
     FMM_MIXED = 1  /* FP32 P2P and expansions, M2L on the tensor cores in
-                      split TF32 with FP32 accumulation, FP64 tree, FP64
-                      offsets and final sums */
+                      split TF32 with FP32 accumulation (p <= 11; FP32
+                      rotation M2L above), FP64 tree, FP64 offsets and final
+                      sums */
 };
 
-/* M2L engine (FMM_MIXED only) */
+/* M2L engine of the same-level pairs (fmm_set_m2l_engine) */
 enum { FMM_M2L_AUTO = 0, FMM_M2L_TENSOR = 1, FMM_M2L_CUDACORE = 2, FMM_M2L_ROTATION = 3 };
 
 typedef struct {
