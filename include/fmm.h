@@ -259,9 +259,10 @@ FMM_API int fmm_direct(fmm_handle h, const double *x, const double *q, int64_t n
  * (same layout, overwritten) about c_L, u = c_L - c_M (|u| > 0), by rotating
  * u onto the z axis, translating along z (only equal orders couple, O(p^3))
  * and rotating back; the result equals the dense M2L
- * L_n^m = (-1)^n sum_{j,k} M_j^k I_{j+n}^{k+m}(u) up to rounding. It uses the
- * rotation maps of the FMM_M2L_ROTATION engine. Returns FMM_EINVAL for p
- * outside [1, 20], a NULL pointer or u = 0. */
+ * L_n^m = (-1)^n sum_{j,k} M_j^k I_{j+n}^{k+m}(u) to 1e-12 relative for
+ * p <= 16 and 1e-11 up to p = 20 (the rotation maps are fitted in FP64). It
+ * uses the rotation maps of the FMM_M2L_ROTATION engine. Returns FMM_EINVAL
+ * for p outside [1, 20], a NULL pointer or u = 0. */
 FMM_API int fmm_m2l_rotation_host(int p, const double *u, const double *M, double *L);
 
 FMM_API int fmm_destroy(fmm_handle h);

@@ -35,7 +35,7 @@ U = [(3.0, 1.0, -2.0), (0.0, 0.0, 4.0), (0.0, 0.0, -5.0), (2.5, -3.5, 0.0), (-4.
      (7.0, -9.0, 11.0)]
 
 
-@pytest.mark.parametrize("P", [1, 2, 4, 8, 12, 16])
+@pytest.mark.parametrize("P", [1, 2, 4, 8, 12, 16, 20])
 def test_rotation_m2l_equals_dense_m2l(host, P):
     rng = np.random.default_rng(P)
     x = rng.uniform(-0.5, 0.5, (20, 3))
@@ -45,7 +45,10 @@ def test_rotation_m2l_equals_dense_m2l(host, P):
     for u in U:
         Lref = _packed(oracle.m2l(P, M, np.zeros(3), np.array(u)), P)
         L = host(P, u, Mp)
-        assert np.linalg.norm(L - Lref) <= 1e-12 * np.linalg.norm(Lref), (P, u)
+        # up to p = 16 (the GPU engine's range) the fitted rotation maps hold
+        # 1e-12; the factorial scalings of degrees 17..19 cost about one digit
+        tol = 1e-12 if P <= 16 else 1e-11
+        assert np.linalg.norm(L - Lref) <= tol * np.linalg.norm(Lref), (P, u)
 
 
 def test_rotation_m2l_is_linear_and_rejects_bad_input(host):
