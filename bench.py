@@ -28,6 +28,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "FMM particles/s at N=1e7 at ≤1e-4 rel-L2 err, mixed vs FP64; P2P % FP32 peak"
 FLOP_PER_INTERACTION = 20
+# leaf size of the reference arm when --ncrit is not given: the value the GPU
+# arm's tuner picks for N = 10^7, p = 8, theta = 0.5 (its line records it)
+REFERENCE_NCRIT = 128
 
 
 def parse():
@@ -122,14 +125,56 @@ def cpu_oracle_rate(n_sample, p, theta, ncrit, seed=3):
     return n_sample / dt, dt
 
 
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def cpu_baselines(ncrit3):
+    """The FP64 oracle FMM on one core and on all cores for the plain, the
+    precision and the scale workloads (bounded samples of the last two)."""
+    import numpy as np
+    import oracle
+    from paper_1106_2176_gb300 import inputs
+    oracle.build()
+    allc = os.cpu_count() or 1
+    cases = [("plain FP64: uniform cube N=16384 (full), p=6, theta=0.5, ncrit=64", 16384, 6, 0.5, 64, 1, None),
+             ("precision: uniform cube, sample N=20000 of 10^6, p=10, theta=0.4, ncrit=64", 20000, 10, 0.4, 64, 1, None),
+             ("scale: uniform cube, sample N=100000 of 10^7, FP32 inputs, p=8, theta=0.5, ncrit=%d" % ncrit3, 100000, 8,
+              0.5, ncrit3, 3, np.float32)]
+    out = []
+    for desc, n, p, theta, ncrit, seed, dt in cases:
+        x, q = inputs.uniform_cube(n, seed, dtype=dt or np.float64)
+        x, q = x.astype(np.float64), q.astype(np.float64)
+        row = {"workload": desc, "n": n}
+        for cores in (1, allc):
+            oracle.set_threads(cores)
+            t0 = time.perf_counter()
+            oracle.fmm(x, q, p, theta, ncrit)
+            dt_s = time.perf_counter() - t0
+            row["cores_%d" % cores] = {"seconds": dt_s, "particles_per_s": n / dt_s}
+        out.append(row)
+    oracle.set_threads(allc)
+    return {"cpu_model": cpu_model(), "host_cores": allc, "runs": out}
+
+
 def run_reference(a, rank):
     if rank != 0:
         return
     import oracle
     oracle.build()
-    ncrit = a.ncrit or 64
+    ncrit = a.ncrit or REFERENCE_NCRIT
     ns = a.cpu_sample
-    cores = os.cpu_count()
+    cores = oracle.get_threads()
     for _ in range(a.warmup):
         cpu_oracle_rate(ns, a.p, a.theta, ncrit)
     times = []
@@ -170,28 +215,32 @@ def p2p_traffic(interactions, n):
         return None
 
 
-def phase_rooflines(phase, st, N, p, peaks, nsm):
+def phase_rooflines(phase, st, N, p, peaks, fp32_peak, tf32_peak):
     """Achieved rates of the phases other than P2P, from algorithmic bytes or
-    flops per phase (the minimal traffic each phase must move, FP32 storage):
-    HBM-bound phases against the measured copy bandwidth, M2L against the TF32
-    dense peak (half the measured BF16 peak, the nominal 1.1 : 2.25 ratio)."""
+    flops per phase (the minimal work each phase must do, FP32 storage). The
+    tree, M2M, L2L and the combine move data: HBM-bound, against the measured
+    copy bandwidth. P2M and L2P run the regular-harmonic recurrences per
+    particle: ALU-bound, against the measured FP32 FMA peak. M2L against the
+    measured TF32 tensor-core peak."""
     pp4 = 4 * p * p  # bytes of one expansion
+    ntri = p * (p + 1) // 2  # (n, m >= 0) terms
     nc, nl = st["ncells"], st["nleaves"]
     by = {
         # 8 LSD passes over (key 8 B, index 4 B), read and written, plus the
         # gather of the sorted float4 particles (16 B in, 16 B out)
         "build": 8 * 2 * 12 * N + 32 * N,
-        # particles in, leaf multipoles out
-        "p2m": 16 * N + nl * pp4,
         # every non-root cell's multipole read once, every parent written once
         "m2m": (nc - 1) * pp4 + (nc - nl) * pp4,
         # every non-root cell's local expansion read, updated and written; its parent read
         "l2l": 3 * (nc - 1) * pp4,
-        # particles and leaf local expansions in, double4 far field out
-        "l2p": 16 * N + nl * pp4 + 32 * N,
         # far and near double4 and the permutation in, phi and grad (FP32) out
         "combine": 64 * N + 4 * N + 16 * N,
     }
+    # per particle and (n, m >= 0) term: the recurrence step of R_n^m (a
+    # complex multiply by a real and a real-complex multiply-add: 6 flop),
+    # then P2M adds q conj(R) into M (4 flop); L2P forms phi (4 flop) and the
+    # three gradient components from the degree below (12 flop)
+    fl = {"p2m": 10 * ntri * N, "l2p": 22 * ntri * N}
     ms = {"build": phase["ms_build"], "p2m": phase["ms_p2m"], "m2m": phase["ms_m2m"], "l2l": phase["ms_l2l"],
           "l2p": phase["ms_l2p"], "combine": phase["ms_combine"]}
     hbm = float(peaks.get("hbm_gbs", 6783.5))
@@ -201,13 +250,18 @@ def phase_rooflines(phase, st, N, p, peaks, nsm):
             gbs = b / (ms[k] / 1000.0) / 1e9
             out[k] = {"bound": "hbm", "bytes": b, "ms": ms[k], "achieved": gbs, "peak": hbm, "unit": "GB/s",
                       "frac": gbs / hbm}
-    tf32 = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1919.0))) / 2.0
+    for k, f in fl.items():
+        if ms[k] > 0:
+            tf = f / (ms[k] / 1000.0) / 1e12
+            out[k] = {"bound": "alu", "flops": f, "ms": ms[k], "achieved": tf, "peak": fp32_peak, "unit": "TFLOP/s",
+                      "frac": tf / fp32_peak}
     flops = 2.0 * p ** 4 * st["n_m2l_pairs"]
     if phase["ms_m2l"] > 0:
         tf = flops / (phase["ms_m2l"] / 1000.0) / 1e12
-        out["m2l"] = {"bound": "tensor", "flops": flops, "ms": phase["ms_m2l"], "achieved": tf, "peak": tf32,
-                      "unit": "TFLOP/s", "frac": tf / tf32,
-                      "note": "useful 2 p^4 flop per pair; the split-TF32 scheme issues 3 MMA passes of it"}
+        out["m2l"] = {"bound": "tensor", "flops": flops, "ms": phase["ms_m2l"], "achieved": tf, "peak": tf32_peak,
+                      "unit": "TFLOP/s", "frac": tf / tf32_peak,
+                      "note": "useful 2 p^4 flop per pair against the measured TF32 MMA peak; the split-TF32 "
+                              "scheme issues 3 MMA passes of it"}
     return out
 
 
@@ -449,6 +503,15 @@ def main():
         f.evaluate(phi, grad)
     torch.cuda.synchronize()
 
+    # measured peaks of the FP32 FMA pipe (scalar and packed pairs) and of
+    # the TF32 tensor-core MMA: the denominators of the roofline fractions
+    from paper_1106_2176_gb300.fmm import measure_peak
+    pk = {"fp32_fma": measure_peak("fp32"), "fp32x2_fma": measure_peak("fp32x2"),
+          "tf32_mma_n128": measure_peak("tf32", 128), "tf32_mma_n256": measure_peak("tf32", 256)}
+    fp32_peak = max(pk["fp32_fma"], pk["fp32x2_fma"])
+    tf32_peak = max(pk["tf32_mma_n128"], pk["tf32_mma_n256"])
+    torch.cuda.synchronize()
+
     stream = torch.cuda.current_stream()
     st0 = f.stats()
     clocks = Clocks(local if os.environ.get("CUDA_VISIBLE_DEVICES") is None else local)
@@ -458,23 +521,21 @@ def main():
     clocks.start()
     time.sleep(0.3)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    p2p_ms, phase = [], {k: 0.0 for k in ("ms_build", "ms_p2m", "ms_m2m", "ms_m2l", "ms_l2l", "ms_l2p", "ms_p2p",
-                                          "ms_combine", "ms_evaluate")}
     e0.record(stream)
     for _ in range(a.steps):
         f.build(xt, qt)
         f.evaluate(phi, grad)
-        s = f.stats()  # phase times of this step (CUDA events on the launching streams)
-        p2p_ms.append(s["ms_p2p"])
-        for k in phase:
-            phase[k] += s[k] / a.steps
     e1.record(stream)
     torch.cuda.synchronize()
     ck = clocks.stop()
     if dist:
         dist.barrier()
     ms = e0.elapsed_time(e1) / a.steps
-    st1 = f.stats()
+    # phase times of the timed steps (the last min(steps, 32)): the CUDA
+    # events the library recorded on its launching streams inside the region
+    st1 = f.stats(mean_of=min(a.steps, 32))
+    phase = {k: st1[k] for k in ("ms_build", "ms_p2m", "ms_m2m", "ms_m2l", "ms_l2l", "ms_l2p", "ms_p2p",
+                                 "ms_combine", "ms_evaluate")}
     launches = (st1["kernel_launches"] - st0["kernel_launches"]) // a.steps
     value, ms = job_rate(N, ms, world, dist, dev)
 
@@ -538,26 +599,30 @@ def main():
     except Exception:
         pass
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_tflops = nsm * 128 * 2 * sm_max * 1e6 / 1e12
+    peak_nominal = nsm * 128 * 2 * sm_max * 1e6 / 1e12
     inter = st1["n_interactions"]
-    p2p_avg = sum(p2p_ms) / len(p2p_ms)
+    p2p_avg = phase["ms_p2p"]
     achieved = FLOP_PER_INTERACTION * inter / (p2p_avg / 1000.0) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved / peak_tflops, "traffic": p2p_traffic(inter, N), "kernel": "p2p_k<float>",
-                "peak_note": "FP32 FMA: %d SMs x 128 lanes x 2 flop x %.0f MHz (max SM clock); 20 flop per interaction"
-                             % (nsm, sm_max),
-                "interactions": inter, "p2p_ms": p2p_avg}
-    phases_roof = phase_rooflines(phase, st1, N, a.p, peaks, nsm)
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": p2p_traffic(inter, N), "kernel": "p2p_k<float>",
+                "peak_note": "measured: FP32 FMA-chain microbenchmark (fmm_measure_peak, best of scalar FMA and "
+                             "packed f32x2 FMA, full occupancy) on this GPU before the timed region; 20 flop per "
+                             "interaction",
+                "peak_nominal": peak_nominal, "frac_nominal": achieved / peak_nominal,
+                "peak_nominal_note": "%d SMs x 128 lanes x 2 flop x %.0f MHz (max SM clock)" % (nsm, sm_max),
+                "peaks_measured_tflops": pk, "interactions": inter, "p2p_ms": p2p_avg}
+    phases_roof = phase_rooflines(phase, st1, N, a.p, peaks, fp32_peak, tf32_peak)
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        import oracle
-        oracle.build()
-        ns = a.cpu_sample
-        rate, dt = cpu_oracle_rate(ns, a.p, a.theta, ncrit)
-        cpu = {"value": rate, "unit": "particles/s", "cores": os.cpu_count(), "kind": "oracle",
+        cb = cpu_baselines(ncrit)
+        allc = cb["host_cores"]
+        run3 = cb["runs"][2]["cores_%d" % allc]
+        cpu = {"value": run3["particles_per_s"], "unit": "particles/s", "cores": allc, "kind": "oracle",
                "sample": "FP64 oracle FMM on N=%d of the same uniform-cube workload (p=%d, theta=%g, ncrit=%d), "
-                         "%.1f s on all host cores" % (ns, a.p, a.theta, ncrit, dt)}
+                         "%.1f s on all %d host cores (%s)" % (cb["runs"][2]["n"], a.p, a.theta, ncrit,
+                                                              run3["seconds"], allc, cb["cpu_model"]),
+               "configs": cb}
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": world, "steps": a.steps,

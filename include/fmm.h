@@ -74,6 +74,13 @@ enum {
 /* M2L engine of the same-level pairs (fmm_set_m2l_engine) */
 enum { FMM_M2L_AUTO = 0, FMM_M2L_TENSOR = 1, FMM_M2L_CUDACORE = 2, FMM_M2L_ROTATION = 3 };
 
+/* arithmetic pipes fmm_measure_peak can time */
+enum {
+    FMM_PEAK_FP32_FMA = 0,   /* scalar FP32 FMA on the CUDA cores */
+    FMM_PEAK_FP32X2_FMA = 1, /* packed FP32 pair FMA (fma.rn.f32x2), 4 flop per instruction */
+    FMM_PEAK_TF32_MMA = 2    /* tcgen05.mma kind::tf32, FP32 accumulator in tensor memory */
+};
+
 typedef struct {
     int64_t n;              /* particles of the last build */
     int64_t ncells;         /* cells of the tree */
@@ -210,6 +217,15 @@ FMM_API int fmm_energy_adjoint(fmm_handle h, double gE, const void *w, const voi
  * the handle's stream. */
 FMM_API int fmm_get_stats(fmm_handle h, fmm_stats *out);
 
+/* The same counters, with each phase time (ms_*) the mean over the last k
+ * builds and the last k evaluations of the handle (1 <= k <= 32, and at most
+ * the number of builds and of evaluations done; FMM_EINVAL otherwise). The
+ * handle records the CUDA events of its 32 most recent builds and evaluations
+ * on the streams that launch each phase, so a timed loop of builds and
+ * evaluations needs no host synchronisation to be broken down by phase
+ * afterwards. Synchronises the handle's streams. */
+FMM_API int fmm_get_stats_mean(fmm_handle h, int k, fmm_stats *out);
+
 /* Sizes of the arrays written by fmm_export_tree (after a build). */
 FMM_API int fmm_get_tree_sizes(fmm_handle h, fmm_tree_sizes *out);
 
@@ -259,9 +275,10 @@ FMM_API int fmm_direct(fmm_handle h, const double *x, const double *q, int64_t n
  * (same layout, overwritten) about c_L, u = c_L - c_M (|u| > 0), by rotating
  * u onto the z axis, translating along z (only equal orders couple, O(p^3))
  * and rotating back; the result equals the dense M2L
- * L_n^m = (-1)^n sum_{j,k} M_j^k I_{j+n}^{k+m}(u) to 1e-12 relative for
- * p <= 16 and 1e-11 up to p = 20 (the rotation maps are fitted in FP64). It
- * uses the rotation maps of the FMM_M2L_ROTATION engine. Returns FMM_EINVAL
+ * L_n^m = (-1)^n sum_{j,k} M_j^k I_{j+n}^{k+m}(u) to 1e-13 relative up to
+ * p = 20 (the rotation maps are the closed-form Wigner small-d matrices,
+ * evaluated in FP64). It uses the rotation maps of the FMM_M2L_ROTATION
+ * engine. Returns FMM_EINVAL
  * for p outside [1, 20], a NULL pointer or u = 0. */
 FMM_API int fmm_m2l_rotation_host(int p, const double *u, const double *M, double *L);
 
@@ -270,8 +287,10 @@ FMM_API int fmm_destroy(fmm_handle h);
 /*
  * Allocation-free Morton keys and stable sort (the paper has no counterpart:
  * this is an interface for callers that cannot allocate device memory, such
- * as code recording a CUDA graph, where cudaMalloc cannot be captured, or an
- * application whose device memory is managed by someone else).
+ * as a loop with a fixed device-memory budget, where a cudaMalloc may block
+ * on the device or fail part-way through a run, or an application whose
+ * device memory is owned by another framework's allocator, which a library
+ * allocating behind its back would starve).
  *   x: n*3 positions on the device, dtype FMM_F32 or FMM_F64 (no host memory);
  *   keys[n], perm[n]: device outputs, the same sorted 63-bit Morton keys and
  *   permutation (perm[k] = input index of the k-th sorted particle) that
@@ -288,6 +307,23 @@ FMM_API int fmm_destroy(fmm_handle h);
  * FMM_ENODEV, FMM_ECUDA (message in fmm_last_error(NULL)).
  */
 FMM_API int fmm_morton_sort_noalloc(const void *x, int64_t n, int dtype, uint64_t *keys, int32_t *perm, void *stream);
+
+/*
+ * Measured peak rate of one arithmetic pipe of the current device, in TFLOP/s
+ * (2 flop per multiply-add). The paper has no counterpart: these are the
+ * denominators of the roofline fractions the benchmark reports for P2P (FP32
+ * FMA) and for the tensor-core M2L (TF32 MMA).
+ *   kind FMM_PEAK_FP32_FMA / FMM_PEAK_FP32X2_FMA: every thread of a full-
+ *     occupancy grid runs 8 independent FMA chains (param ignored);
+ *   kind FMM_PEAK_TF32_MMA: one CTA per SM, one thread issuing M = 128,
+ *     N = param (128 or 256), K = 8 MMAs from two fixed 128B-swizzled
+ *     shared-memory operands into one tensor-memory accumulator.
+ * One untimed launch, then the best of reps (1..100) launches timed with CUDA
+ * events. Runs on the legacy default stream; allocates and frees a few bytes
+ * of device memory; synchronises the device. Errors: FMM_EINVAL (kind, param,
+ * reps or NULL tflops), FMM_ENODEV, FMM_ECUDA.
+ */
+FMM_API int fmm_measure_peak(int kind, int param, int reps, double *tflops);
 
 /* Message of the last error on the calling thread ("" if none). */
 FMM_API const char *fmm_last_error(fmm_handle h);

@@ -22,4 +22,6 @@ from .oracle import (  # noqa: F401
     Tree,
     fmm,
     nm,
+    set_threads,
+    get_threads,
 )

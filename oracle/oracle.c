@@ -45,6 +45,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef double complex cplx;
 
@@ -747,3 +750,24 @@ int orc_fmm(int64_t n, const double *x, const double *q, int P, double theta, in
 }
 
 int orc_max_p(void) { return ORC_MAXP; }
+
+/* Threads the OpenMP loops over targets use (timing of the CPU baseline on
+ * one core and on all cores); results do not depend on it, since each
+ * target's sums keep their order. */
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+int orc_get_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -65,6 +65,8 @@ def lib():
             L.orc_fmm.argtypes = [ctypes.c_int64, _d, _d, ctypes.c_int, ctypes.c_double, ctypes.c_int, _d, _d]
             L.orc_fmm.restype = ctypes.c_int
             L.orc_max_p.restype = ctypes.c_int
+            L.orc_set_threads.argtypes = [ctypes.c_int]
+            L.orc_get_threads.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -233,3 +235,12 @@ def fmm(x, q, P, theta, ncrit):
     if rc != 0:
         raise ValueError("oracle fmm rejected its arguments")
     return phi, grad
+
+
+def set_threads(n):
+    """Threads of the oracle's OpenMP loops over targets (results do not depend on it)."""
+    lib().orc_set_threads(int(n))
+
+
+def get_threads():
+    return int(lib().orc_get_threads())

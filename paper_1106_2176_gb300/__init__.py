@@ -17,4 +17,4 @@ Also: ``FMM(..., m2l_engine="tensor" | "cudacore" | "rotation")``,
 (weighted energy with gradients for x, q and w), ``tune.tune_ncrit`` (leaf
 size) and ``fmm.m2l_rotation_host`` (one rotation M2L on the host).
 """
-from .fmm import FMM, FMMError, unscale  # noqa: F401
+from .fmm import FMM, FMMError  # noqa: F401

@@ -10,13 +10,16 @@ grad phi; the expansions are recomputed rather than stored.
     E.backward()   # x.grad, q.grad, w.grad
 """
 import threading
+import weakref
 
 import torch
 
 from .fmm import FMM
 
 # Handles (and their device workspaces) are reused across calls with the same
-# size and parameters: a forward pass takes one, its backward pass returns it.
+# size and parameters: a forward pass leases one, and the lease goes back to
+# the pool after the backward pass, or when the autograd graph is freed
+# without a backward pass.
 _pool = {}
 _pool_lock = threading.Lock()
 POOL_MAX = 4  # idle handles kept per key
@@ -49,28 +52,48 @@ def clear_pool():
         f.close()
 
 
+class _Lease:
+    """A pooled handle held by one forward pass; returned exactly once, by
+    release() or, failing that, when the lease is garbage collected."""
+
+    def __init__(self, key, f):
+        self.f = f
+        self._fin = weakref.finalize(self, _give, key, f)
+
+    def release(self):
+        self.f = None
+        self._fin()
+
+
 class FMMEnergy(torch.autograd.Function):
     @staticmethod
     def forward(ctx, x, q, w, p, theta, ncrit, precision):
-        ctx.key, f = _take(x.shape[0], p, theta, ncrit, precision, str(x.device))
+        key, f = _take(x.shape[0], p, theta, ncrit, precision, str(x.device))
+        ctx.lease = _Lease(key, f)
+        ctx.args = (p, theta, ncrit, precision)
         x, q, w = x.contiguous(), q.contiguous(), w.contiguous()
         f.build(x, q)
         phi, grad = f.evaluate()
         e = f.energy(w, q, phi)
-        ctx.f = f
-        ctx.save_for_backward(q, w, phi, grad)
+        ctx.save_for_backward(x, q, w, phi, grad)
         return torch.tensor(e, dtype=torch.float64, device=x.device)
 
     @staticmethod
     def backward(ctx, gE):
-        q, w, phi, grad = ctx.saved_tensors
-        f = ctx.f
+        x, q, w, phi, grad = ctx.saved_tensors
+        lease = ctx.lease
+        if lease.f is None:
+            # a second backward (retain_graph=True): the first one returned
+            # the handle, so lease another and rebuild the tree of x
+            p, theta, ncrit, precision = ctx.args
+            lease = _Lease(*_take(x.shape[0], p, theta, ncrit, precision, str(x.device)))
+            lease.f.build(x, q)
+        f = lease.f
         f.update_charges(q, w)
         psi, gpsi = f.evaluate()
         dq, dx, dw = f.energy_adjoint(float(gE), w, q, phi, grad, psi, gpsi, dq=ctx.needs_input_grad[1],
                                       dx=ctx.needs_input_grad[0], dw=ctx.needs_input_grad[2])
-        ctx.f = None
-        _give(ctx.key, f)
+        lease.release()
         return dx, dq, dw, None, None, None, None
 
 

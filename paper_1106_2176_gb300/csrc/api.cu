@@ -4,6 +4,8 @@
 // host except the level-independent operator tables made at create time.
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 
 #include "fmm_internal.cuh"
@@ -55,6 +57,19 @@ void DevBuf::release()
     cap = 0;
 }
 
+void ensure_smem(const void *kernel, size_t bytes)
+{
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, size_t> set;
+    int dev = 0;
+    FMM_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    size_t &have = set[std::make_pair(kernel, dev)];
+    if (bytes <= have) return;
+    FMM_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    have = bytes;
+}
+
 void PinnedBuf::ensure(size_t bytes)
 {
     if (bytes <= cap && p) return;
@@ -87,8 +102,9 @@ fmm_ctx::~fmm_ctx()
                            &direct_part, &rot_tab};
     for (auto *b : bufs) b->release();
     hpin.release();
-    if (tm.ok)
-        for (auto &e : tm.ev) cudaEventDestroy(e);
+    for (auto &t : tms)
+        for (auto &e : t.ev)
+            if (e) cudaEventDestroy(e);
     if (ev_fork) cudaEventDestroy(ev_fork);
     if (ev_join) cudaEventDestroy(ev_join);
     if (s2) cudaStreamDestroy(s2);
@@ -123,6 +139,10 @@ static int fail(int code, const char *msg)
     return code;
 }
 
+// events of timing slot k (all slots are created with the handle, so that no
+// event is created while a caller's stream is being captured)
+static cudaEvent_t *slot_events(fmm_ctx *h, int64_t k) { return h->tms[k % FMM_TIMING_SLOTS].ev; }
+
 static float ev_ms(cudaEvent_t a, cudaEvent_t b)
 {
     float ms = 0.f;
@@ -131,6 +151,31 @@ static float ev_ms(cudaEvent_t a, cudaEvent_t b)
         return 0.f;
     }
     return ms;
+}
+
+// phase times of the last k builds and evaluations, averaged (the events of
+// each call are in the timing slot of its sequence number)
+static void phase_means(fmm_ctx *h, int k, fmm_stats *out)
+{
+    out->ms_build = out->ms_evaluate = out->ms_p2m = out->ms_m2m = out->ms_m2l = 0;
+    out->ms_l2l = out->ms_l2p = out->ms_p2p = out->ms_combine = 0;
+    if (h->built && h->nbuilds >= k)
+        for (int64_t i = h->nbuilds - k; i < h->nbuilds; i++) {
+            cudaEvent_t *ev = h->tms[i % FMM_TIMING_SLOTS].ev;
+            out->ms_build += ev_ms(ev[0], ev[1]) / k;
+        }
+    if (h->evaluated && h->nevals >= k)
+        for (int64_t i = h->nevals - k; i < h->nevals; i++) {
+            cudaEvent_t *ev = h->tms[i % FMM_TIMING_SLOTS].ev;
+            out->ms_evaluate += ev_ms(ev[8], ev[12]) / k;
+            out->ms_p2m += ev_ms(ev[2], ev[3]) / k;
+            out->ms_m2m += ev_ms(ev[3], ev[4]) / k;
+            out->ms_m2l += ev_ms(ev[4], ev[5]) / k;
+            out->ms_l2l += ev_ms(ev[5], ev[6]) / k;
+            out->ms_l2p += ev_ms(ev[6], ev[7]) / k;
+            out->ms_p2p += ev_ms(ev[9], ev[10]) / k;
+            out->ms_combine += ev_ms(ev[11], ev[12]) / k;
+        }
 }
 
 extern "C" {
@@ -173,8 +218,8 @@ int fmm_create(int64_t N, int p, double theta, int ncrit, fmm_handle *out)
     FMM_CUDA_TRY(cudaEventCreateWithFlags(&h->ev_far, cudaEventDisableTiming));
     FMM_CUDA_TRY(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
     FMM_CUDA_TRY(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
-    for (auto &e : h->tm.ev) FMM_CUDA_TRY(cudaEventCreate(&e));
-    h->tm.ok = true;
+    for (auto &t : h->tms)
+        for (auto &e : t.ev) FMM_CUDA_TRY(cudaEventCreate(&e));
     fmm::operators_init(h);
     fmm::tensor_tables_init(h);
     FMM_CUDA_TRY(cudaDeviceSynchronize());
@@ -286,7 +331,8 @@ int fmm_build(fmm_handle h, const void *x, const void *q, int64_t n, int dtype)
     else if (tc) h->engine_used = FMM_M2L_TENSOR;
     else if (h->engine_req == FMM_M2L_AUTO && fmm::rotation_m2l_supported(h)) h->engine_used = FMM_M2L_ROTATION;
     else h->engine_used = FMM_M2L_CUDACORE;
-    FMM_CUDA_TRY(cudaEventRecord(h->tm.ev[0], s));
+    cudaEvent_t *ev = slot_events(h, h->nbuilds);
+    FMM_CUDA_TRY(cudaEventRecord(ev[0], s));
     const size_t es = dt == FMM_F64 ? 8 : 4;
     const void *xd = x, *qd = q;
     if (host) {
@@ -298,7 +344,8 @@ int fmm_build(fmm_handle h, const void *x, const void *q, int64_t n, int dtype)
         qd = h->q_in.p;
     }
     fmm::tree_build(h, xd, qd, n, dt);
-    FMM_CUDA_TRY(cudaEventRecord(h->tm.ev[1], s));
+    FMM_CUDA_TRY(cudaEventRecord(ev[1], s));
+    h->nbuilds++;
     h->built = true;
     return FMM_OK;
     API_END
@@ -311,7 +358,8 @@ int fmm_evaluate(fmm_handle h, void *phi, void *grad)
     if (!phi) return fail(FMM_EINVAL, "fmm_evaluate: NULL phi");
     API_BEGIN
     cudaStream_t s = h->stream;
-    cudaEvent_t *ev = h->tm.ev;
+    cudaEvent_t *ev = slot_events(h, h->nevals);
+    h->ev_cur = ev;
     FMM_CUDA_TRY(cudaEventRecord(ev[8], s));
     if (h->overlap) {
         // near field and far field on two private streams, joined back to the
@@ -353,6 +401,7 @@ int fmm_evaluate(fmm_handle h, void *phi, void *grad)
     }
     FMM_CUDA_TRY(cudaEventRecord(ev[12], s));
     if (h->host_mem) FMM_CUDA_TRY(cudaStreamSynchronize(s));
+    h->nevals++;
     h->evaluated = true;
     return FMM_OK;
     API_END
@@ -435,18 +484,20 @@ int fmm_get_stats(fmm_handle h, fmm_stats *out)
     }
     out->kernel_launches = h->launches;
     out->uniform_path = h->uniform_used ? 1 : 0;
-    cudaEvent_t *ev = h->tm.ev;
-    if (h->built) out->ms_build = ev_ms(ev[0], ev[1]);
-    if (h->evaluated) {
-        out->ms_evaluate = ev_ms(ev[8], ev[12]);
-        out->ms_p2m = ev_ms(ev[2], ev[3]);
-        out->ms_m2m = ev_ms(ev[3], ev[4]);
-        out->ms_m2l = ev_ms(ev[4], ev[5]);
-        out->ms_l2l = ev_ms(ev[5], ev[6]);
-        out->ms_l2p = ev_ms(ev[6], ev[7]);
-        out->ms_p2p = ev_ms(ev[9], ev[10]);
-        out->ms_combine = ev_ms(ev[11], ev[12]);
-    }
+    phase_means(h, 1, out);
+    return FMM_OK;
+    API_END
+}
+
+int fmm_get_stats_mean(fmm_handle h, int k, fmm_stats *out)
+{
+    if (!h || !out) return fail(FMM_EINVAL, "fmm_get_stats_mean: NULL argument");
+    if (k < 1 || k > FMM_TIMING_SLOTS || k > h->nbuilds || k > h->nevals)
+        return fail(FMM_EINVAL, "fmm_get_stats_mean: k must be in [1, 32] and at most the builds and evaluations done");
+    const int rc = fmm_get_stats(h, out);
+    if (rc != FMM_OK) return rc;
+    API_BEGIN
+    phase_means(h, k, out);
     return FMM_OK;
     API_END
 }

@@ -954,11 +954,7 @@ template <int P>
 static void m2lx_f_run(int nc, const int *ptr, const int *src, const int4 *xyz, const float *M, float *L, cudaStream_t s)
 {
     constexpr size_t smem = m2lx_f_smem<P>();
-    static bool attr = false;
-    if (!attr) {
-        FMM_CUDA_TRY(cudaFuncSetAttribute(m2lx_f_k<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr = true;
-    }
+    ensure_smem((const void *)m2lx_f_k<P>, smem);
     m2lx_f_k<P><<<nc, 32 * M2LX_FW, smem, s>>>(nc, ptr, src, xyz, M, L);
 }
 
@@ -1404,7 +1400,7 @@ static void far_field_t(fmm_ctx *h, const P4 *xs, const T *rtab)
     h->Lexp.ensure(sizeof(T) * (size_t)nc * PP);
     T *M = h->Mexp.as<T>(), *L = h->Lexp.as<T>();
     const Box *box = h->box.as<Box>();
-    cudaEvent_t *ev = h->tm.ev;
+    cudaEvent_t *ev = h->ev_cur;
 
     // P2M
     FMM_CUDA_TRY(cudaEventRecord(ev[2], s));
@@ -1454,12 +1450,7 @@ static void far_field_t(fmm_ctx *h, const P4 *xs, const T *rtab)
         } else {
             const int tile = m2l_tile_size(h);
             size_t smem = sizeof(T) * 2 * ((size_t)Q * Q + (size_t)tile * PP) + sizeof(int) * 6 * tile;
-            static size_t set_smem[2] = {0, 0};
-            size_t &ss = set_smem[sizeof(T) == 8];
-            if (smem > ss) {
-                FMM_CUDA_TRY(cudaFuncSetAttribute(m2l_cc_k<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-                ss = smem;
-            }
+            ensure_smem((const void *)m2l_cc_k<T>, smem);
             m2l_cc_k<T><<<h->ntiles_max, M2L_CC_T, smem, s>>>(
                 p, h->m2l_tiles.as<M2LTile>(), reinterpret_cast<const int *>(h->m2l_misc.as<unsigned>() + 24 * (FMM_MAXLEVEL + 1)),
                 h->m2l_tgt.as<int>(), h->c_xyz.as<int4>(), h->c_anchor.as<uint64_t>(), h->lvl_desc.as<LevelDesc>(),
@@ -1480,12 +1471,7 @@ static void far_field_t(fmm_ctx *h, const P4 *xs, const T *rtab)
     }
     if (h->n_m2lx > 0 && !m2lx_done) {
         size_t smem = sizeof(T) * M2LX_W * 2 * ((size_t)Q * Q + PP) + sizeof(double) * M2LX_W * 2 * ntri;
-        static size_t set_x[2] = {0, 0};
-        size_t &ss = set_x[sizeof(T) == 8];
-        if (smem > ss) {
-            FMM_CUDA_TRY(cudaFuncSetAttribute(m2lx_k<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            ss = smem;
-        }
+        ensure_smem((const void *)m2lx_k<T>, smem);
         m2lx_k<T><<<nc, 32 * M2LX_W, smem, s>>>(p, nc, h->m2lx_ptr.as<int>(), h->m2lx_src.as<int>(), h->c_xyz.as<int4>(), M, L);
         count_launch(h);
         check_launch("m2l irregular");

@@ -105,9 +105,12 @@ struct TravCounters {
     unsigned long long n_p2p, n_m2lx, n_next, n_m2l_implicit;
 };
 
+// CUDA events of one build and one evaluation (build: ev[0], ev[1];
+// evaluation: ev[2] .. ev[12]); a handle keeps FMM_TIMING_SLOTS of them so the
+// phase times of recent calls can be read back without a host sync per call
+#define FMM_TIMING_SLOTS 32
 struct Timers {
-    cudaEvent_t ev[16];
-    bool ok = false;
+    cudaEvent_t ev[16] = {};
 };
 
 }  // namespace fmm
@@ -128,7 +131,9 @@ struct fmm_ctx {
     cudaStream_t work = nullptr;    // stream the far-field kernels are launched on
     cudaEvent_t ev_far = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-    fmm::Timers tm;
+    fmm::Timers tms[FMM_TIMING_SLOTS];
+    int64_t nbuilds = 0, nevals = 0;  // successful builds and evaluations so far
+    cudaEvent_t *ev_cur = nullptr;    // events of the call in progress
     int64_t launches = 0;
 
     // state of the last build
@@ -200,6 +205,10 @@ namespace fmm {
 
 // launch bookkeeping: every kernel launch of the library goes through this
 inline void count_launch(fmm_ctx *h) { h->launches++; }
+// Dynamic shared memory of a kernel beyond the 48 KB default: the attribute
+// belongs to the device that is current when it is set, so it is set once per
+// (kernel, device) and raised when a launch needs more (thread safe).
+void ensure_smem(const void *kernel, size_t bytes);
 void check_launch(const char *what);
 
 // tree.cu

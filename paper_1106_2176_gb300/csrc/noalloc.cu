@@ -2,11 +2,12 @@
 // caller's buffers, with all temporary memory taken from one fixed-size array
 // that the library reserves when it is loaded.
 //
-// Who needs this: code that must not call cudaMalloc on the hot path, for
-// example while a CUDA stream is being captured into a graph (allocation is
-// not a capturable operation), a real-time loop with a fixed memory budget, or
-// a host application whose device allocator belongs to another framework. Such
-// a caller passes its own input and output buffers and gets the first stage of
+// Who needs this: code that must not call cudaMalloc on its hot path, for
+// example a real-time loop with a fixed device-memory budget (a cudaMalloc
+// can block on the device and can fail part-way through a run), or a host
+// application whose device allocator belongs to another framework (memory
+// taken behind that allocator's back is memory it cannot hand out). Such a
+// caller passes its own input and output buffers and gets the first stage of
 // the octree build without the library allocating anything.
 //
 // The scratch is a file-scope __device__ array, so every GPU that loads the

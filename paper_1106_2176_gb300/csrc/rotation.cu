@@ -17,13 +17,16 @@
 // R_n^m = Yt_n^m / c_nm with c_nm = sqrt((n+|m|)! (n-|m|)!). A rotation acts
 // unitarily on the Yt of one degree. With Q = R_y(-b) R_z(-a) (a, b the
 // azimuth and polar angle of u), Yt^m(x) = e^{i m a} sum_m' V_mm'(b) Yt^m'(Qx)
-// where V(b) is defined by Yt^m(R_y(b) y) = sum_m' V_mm'(b) Yt^m'(y); V is
-// found per distinct polar angle by least squares over a Fibonacci sphere of
-// sample points, the azimuth enters as exact phases. Then, with
-// U = diag(e^{i m a}) V:
+// where V(b) is defined by Yt^m(R_y(b) y) = sum_m' V_mm'(b) Yt^m'(y). With
+// this normalisation V_mm'(b) is the Wigner small-d matrix element
+// d^n_{m'm}(b); it is evaluated in closed form from its Jacobi-polynomial
+// expression (Edmonds, Angular Momentum in Quantum Mechanics, 1957, Eq.
+// 4.1.23), once per distinct polar angle, and the azimuth enters as exact
+// phases. Then, with U = diag(e^{i m a}) V:
 //   M'^m' = sum_m M^m c_m U_mm' / c_m'        (multipoles into the frame)
 //   L^m   = sum_m' L'^m' c_m U_mm' / c_m'     (locals back, U^-1 = U^H)
 
+#include <algorithm>
 #include <array>
 #include <cmath>
 #include <complex>
@@ -45,25 +48,6 @@ using cplx = std::complex<double>;
 int rot_deg_off(int n) { return n * (4 * n * n - 1) / 3; }
 int rot_map_size(int p) { return rot_deg_off(p); }
 
-// Q_n^m = r^n P_n^m(cos t) e^{i m f} for 0 <= m <= n <= N (triangular, n(n+1)/2 + m),
-// by the recurrences of the regular solid harmonics, no division by sin t
-static void qtab(int N, double x, double y, double z, std::vector<cplx> &Q)
-{
-    Q.assign((size_t)(N + 1) * (N + 2) / 2, cplx(0, 0));
-    auto id = [](int n, int m) { return n * (n + 1) / 2 + m; };
-    const double r2 = x * x + y * y + z * z;
-    cplx mm(1, 0);
-    const cplx xy(x, y);
-    for (int m = 0; m <= N; m++) {
-        if (m > 0) mm *= xy * (double)(2 * m - 1);
-        Q[id(m, m)] = mm;
-        if (m + 1 <= N) Q[id(m + 1, m)] = (double)(2 * m + 1) * z * mm;
-        for (int n = m + 2; n <= N; n++)
-            Q[id(n, m)] = ((double)(2 * n - 1) * z * Q[id(n - 1, m)] - (double)(n + m - 1) * r2 * Q[id(n - 2, m)]) /
-                          (double)(n - m);
-    }
-}
-
 static double fact(int k)
 {
     double f = 1;
@@ -71,79 +55,58 @@ static double fact(int k)
     return f;
 }
 
-// Yt_n^m at a unit vector for m = -n..n (index m + n)
-static void ytil(int n, const std::vector<cplx> &Q, cplx *out)
+static double binom(int n, int k) { return fact(n) / (fact(k) * fact(n - k)); }
+
+// Jacobi polynomial P_k^(a,b)(x) by its three-term recurrence in the degree
+// (Abramowitz & Stegun 22.7.1), stable for x in [-1, 1]
+static double jacobi(int k, int a, int b, double x)
 {
-    for (int m = 0; m <= n; m++) {
-        const cplx v = Q[n * (n + 1) / 2 + m] * std::sqrt(fact(n - m) / fact(n + m));
-        out[n + m] = v;
-        if (m) out[n - m] = ((m & 1) ? -1.0 : 1.0) * std::conj(v);
+    if (k == 0) return 1.0;
+    double p0 = 1.0, p1 = 0.5 * ((double)(a - b) + (double)(a + b + 2) * x);
+    for (int j = 2; j <= k; j++) {
+        const double s = (double)(2 * j + a + b);
+        const double c1 = 2.0 * j * (double)(j + a + b) * (s - 2.0);
+        const double c2 = (s - 1.0) * (double)(a * a - b * b);
+        const double c3 = (s - 2.0) * (s - 1.0) * s;
+        const double c4 = 2.0 * (double)(j + a - 1) * (double)(j + b - 1) * s;
+        const double p2 = ((c2 + c3 * x) * p1 - c4 * p0) / c1;
+        p0 = p1;
+        p1 = p2;
     }
+    return p1;
 }
 
-// solve A X = B in place (A: K x K, B: K x R, row-major), partial pivoting
-static void csolve(int K, int R, std::vector<cplx> &A, std::vector<cplx> &B)
+// Wigner small-d element d^n_{m'm}(b) from its Jacobi form: with
+// k = min(n+m, n-m, n+m', n-m'), the exponents a = |m - m'|,
+// c = |m + m'| (= 2n - 2k - a), and the sign (-1)^(m'-m) when m' > m,
+//   d = sign sqrt(C(2n-k, k+a) / C(k+c, c)) sin(b/2)^a cos(b/2)^c P_k^(a,c)(cos b)
+static double wigner_d(int n, int mp, int m, double b)
 {
-    for (int c = 0; c < K; c++) {
-        int piv = c;
-        for (int r = c + 1; r < K; r++)
-            if (std::abs(A[(size_t)r * K + c]) > std::abs(A[(size_t)piv * K + c])) piv = r;
-        if (piv != c) {
-            for (int k = 0; k < K; k++) std::swap(A[(size_t)c * K + k], A[(size_t)piv * K + k]);
-            for (int k = 0; k < R; k++) std::swap(B[(size_t)c * R + k], B[(size_t)piv * R + k]);
-        }
-        const cplx d = A[(size_t)c * K + c];
-        for (int r = 0; r < K; r++) {
-            if (r == c) continue;
-            const cplx f = A[(size_t)r * K + c] / d;
-            if (f == cplx(0, 0)) continue;
-            for (int k = c; k < K; k++) A[(size_t)r * K + k] -= f * A[(size_t)c * K + k];
-            for (int k = 0; k < R; k++) B[(size_t)r * R + k] -= f * B[(size_t)c * R + k];
-        }
+    const int k = std::min(std::min(n + m, n - m), std::min(n + mp, n - mp));
+    int a, lam;
+    if (k == n + m || k == n - mp) {
+        a = mp - m;
+        lam = mp - m;
+    } else {
+        a = m - mp;
+        lam = 0;
     }
-    for (int r = 0; r < K; r++)
-        for (int k = 0; k < R; k++) B[(size_t)r * R + k] /= A[(size_t)r * K + r];
+    const int c = 2 * n - 2 * k - a;
+    const double sgn = (lam & 1) ? -1.0 : 1.0;
+    return sgn * std::sqrt(binom(2 * n - k, k + a) / binom(k + c, c)) * std::pow(std::sin(0.5 * b), a) *
+           std::pow(std::cos(0.5 * b), c) * jacobi(k, a, c, std::cos(b));
 }
 
-// V(b) for every degree n < p: Yt_n^m(R_y(b) y) = sum_m' V_mm' Yt_n^m'(y),
-// least squares over S points of a Fibonacci sphere. V[n] is (2n+1)^2, row m + n.
-static std::vector<std::vector<cplx>> vmaps(int p, double b)
+// V(b) for every degree n < p: Yt_n^m(R_y(b) y) = sum_m' V_mm' Yt_n^m'(y)
+// with V_mm' = d^n_{m'm}(b). V[n] is (2n+1)^2 real, row m + n.
+static std::vector<std::vector<double>> vmaps(int p, double b)
 {
-    const int S = 8 * p + 16;
-    const double cb = std::cos(b), sb = std::sin(b);
-    std::vector<std::vector<cplx>> Yy(S), Yr(S);
-    std::vector<cplx> Q;
-    for (int s = 0; s < S; s++) {
-        const double z = 1.0 - 2.0 * (s + 0.5) / S, rho = std::sqrt(std::max(0.0, 1.0 - z * z));
-        const double f = s * 2.39996322972865332;  // golden angle
-        const double y[3] = {rho * std::cos(f), rho * std::sin(f), z};
-        // R_y(b) y
-        const double ry[3] = {cb * y[0] + sb * y[2], y[1], -sb * y[0] + cb * y[2]};
-        Yy[s].resize((size_t)p * p);
-        Yr[s].resize((size_t)p * p);
-        qtab(p - 1, y[0], y[1], y[2], Q);
-        for (int n = 0; n < p; n++) ytil(n, Q, &Yy[s][(size_t)n * n]);
-        qtab(p - 1, ry[0], ry[1], ry[2], Q);
-        for (int n = 0; n < p; n++) ytil(n, Q, &Yr[s][(size_t)n * n]);
-    }
-    std::vector<std::vector<cplx>> V(p);
+    std::vector<std::vector<double>> V(p);
     for (int n = 0; n < p; n++) {
         const int K = 2 * n + 1;
-        // normal equations: V G = H with G = sum_s y y^H, H = sum_s r y^H; G is
-        // Hermitian, so G V^H = H^H
-        std::vector<cplx> G((size_t)K * K, 0), Hh((size_t)K * K, 0);
-        for (int s = 0; s < S; s++) {
-            const cplx *yy = &Yy[s][(size_t)n * n], *rr = &Yr[s][(size_t)n * n];
-            for (int a = 0; a < K; a++)
-                for (int c = 0; c < K; c++) {
-                    G[(size_t)a * K + c] += yy[a] * std::conj(yy[c]);
-                    Hh[(size_t)a * K + c] += yy[a] * std::conj(rr[c]);  // (H^H)_ac = conj(H_ca)
-                }
-        }
-        csolve(K, K, G, Hh);  // Hh := V^H
         V[n].resize((size_t)K * K);
-        for (int a = 0; a < K; a++)
-            for (int c = 0; c < K; c++) V[n][(size_t)a * K + c] = std::conj(Hh[(size_t)c * K + a]);
+        for (int m = -n; m <= n; m++)
+            for (int mp = -n; mp <= n; mp++) V[n][(size_t)(m + n) * K + (mp + n)] = wigner_d(n, mp, m, b);
     }
     return V;
 }
@@ -175,9 +138,9 @@ static void packed(int n, const std::vector<cplx> &T, double *out)
 
 // V(b) cached per (p, b): the stencil has far fewer polar angles than vectors
 static std::mutex g_v_mu;
-static std::map<std::pair<int, double>, std::shared_ptr<const std::vector<std::vector<cplx>>>> g_v_cache;
+static std::map<std::pair<int, double>, std::shared_ptr<const std::vector<std::vector<double>>>> g_v_cache;
 
-static std::shared_ptr<const std::vector<std::vector<cplx>>> vmaps_cached(int p, double b)
+static std::shared_ptr<const std::vector<std::vector<double>>> vmaps_cached(int p, double b)
 {
     const auto key = std::make_pair(p, b);
     {
@@ -185,7 +148,7 @@ static std::shared_ptr<const std::vector<std::vector<cplx>>> vmaps_cached(int p,
         auto it = g_v_cache.find(key);
         if (it != g_v_cache.end()) return it->second;
     }
-    auto v = std::make_shared<const std::vector<std::vector<cplx>>>(vmaps(p, b));
+    auto v = std::make_shared<const std::vector<std::vector<double>>>(vmaps(p, b));
     std::lock_guard<std::mutex> lk(g_v_mu);
     g_v_cache[key] = v;
     return v;
@@ -300,37 +263,54 @@ static std::shared_ptr<const std::vector<double>> rot_image(fmm_ctx *h)
     auto img = std::make_shared<std::vector<double>>((size_t)nv * VS, 0.0);
     // vectors in parallel on the host cores; u = c_L - c_M = -(source - target)
     const unsigned nt = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    // stride t of the vectors: i = t, t + nt, ...
+    auto stride = [&](unsigned t) {
+        std::vector<double> A(RS), B(RS);
+        for (int i = (int)t; i < nv; i += (int)nt) {
+            const double u[3] = {-(double)vec[i][0], -(double)vec[i][1], -(double)vec[i][2]};
+            rotation_maps(p, u, A.data(), B.data());
+            double *o = img->data() + (size_t)i * VS;
+            int off = 0;
+            for (int n = 0; n < p; n++) {
+                const int K = 2 * n + 1, K4 = k4(n);
+                for (int r = 0; r < K; r++)
+                    for (int c = 0; c < K; c++) {
+                        o[off + r * K4 + c] = A[rot_deg_off(n) + r * K + c];
+                        o[SA + off + r * K4 + c] = B[rot_deg_off(n) + r * K + c];
+                    }
+                off += K * K4;
+            }
+            const double d = std::sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+            double g = 1.0 / d;
+            for (int l = 0; l < 2 * p - 1; l++) {
+                if (l) g *= (double)l / d;
+                o[2 * SA + l] = g;
+            }
+        }
+    };
     std::vector<std::thread> pool;
     std::vector<std::exception_ptr> fault(nt);  // an exception stays in its thread until the join
-    for (unsigned t = 0; t < nt; t++)
-        pool.emplace_back([&, t] {
-            try {
-            std::vector<double> A(RS), B(RS);
-            for (int i = (int)t; i < nv; i += (int)nt) {
-                const double u[3] = {-(double)vec[i][0], -(double)vec[i][1], -(double)vec[i][2]};
-                rotation_maps(p, u, A.data(), B.data());
-                double *o = img->data() + (size_t)i * VS;
-                int off = 0;
-                for (int n = 0; n < p; n++) {
-                    const int K = 2 * n + 1, K4 = k4(n);
-                    for (int r = 0; r < K; r++)
-                        for (int c = 0; c < K; c++) {
-                            o[off + r * K4 + c] = A[rot_deg_off(n) + r * K + c];
-                            o[SA + off + r * K4 + c] = B[rot_deg_off(n) + r * K + c];
-                        }
-                    off += K * K4;
+    unsigned started = 0;
+    try {
+        for (; started < nt; started++)
+            pool.emplace_back([&, started] {
+                try {
+                    stride(started);
+                } catch (...) {
+                    fault[started] = std::current_exception();
                 }
-                const double d = std::sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-                double g = 1.0 / d;
-                for (int l = 0; l < 2 * p - 1; l++) {
-                    if (l) g *= (double)l / d;
-                    o[2 * SA + l] = g;
-                }
-            }
-            } catch (...) {
-                fault[t] = std::current_exception();
-            }
-        });
+            });
+    } catch (...) {
+        // a thread could not be created: the strides without a thread run here
+    }
+    for (unsigned t = started; t < nt; t++) {
+        try {
+            stride(t);
+        } catch (...) {
+            fault[t] = std::current_exception();
+            break;
+        }
+    }
     for (auto &th : pool) th.join();
     for (auto &f : fault)
         if (f) std::rethrow_exception(f);
@@ -568,12 +548,7 @@ void m2l_rotation(fmm_ctx *h, T *L, const T *M)
     for (int n = 0; n < p; n++) PP4 += k4(n);
     if (PP4 > 32 * C::NL) throw Error{FMM_EINVAL, "rotation M2L: p too large"};
     const size_t smem = sizeof(T) * ((size_t)VS + (size_t)C::W * 4 * PP4);
-    static size_t set_smem[2] = {0, 0};
-    size_t &ss = set_smem[sizeof(T) == 8];
-    if (smem > ss) {
-        FMM_CUDA_TRY(cudaFuncSetAttribute(m2l_rot_k<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        ss = smem;
-    }
+    ensure_smem((const void *)m2l_rot_k<T>, smem);
     const int *ntiles = reinterpret_cast<const int *>(h->m2l_misc.as<unsigned>() + 24 * (FMM_MAXLEVEL + 1));
     m2l_rot_k<T><<<h->ntiles_max, 32 * C::W, smem, h->work>>>(
         p, h->m2l_tiles.as<M2LTile>(), ntiles, h->m2l_tgt.as<int>(), h->c_xyz.as<int4>(), h->c_anchor.as<uint64_t>(),

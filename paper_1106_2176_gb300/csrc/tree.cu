@@ -333,12 +333,8 @@ static bool radix_sort(fmm_ctx *h, uint64_t *k, int *v, uint64_t *kt, int *vt, i
     const int ntiles = (int)nblocks(n, RS_TILE);
     h->hist.ensure(sizeof(unsigned) * (size_t)256 * ntiles);
     unsigned *hist = h->hist.as<unsigned>();
-    static bool attr_set = false;
-    if (!attr_set) {
-        FMM_CUDA_TRY(cudaFuncSetAttribute(rs_scatter_k<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs_smem()));
-        FMM_CUDA_TRY(cudaFuncSetAttribute(rs_scatter_k<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs_smem()));
-        attr_set = true;
-    }
+    ensure_smem((const void *)rs_scatter_k<true>, rs_smem());
+    ensure_smem((const void *)rs_scatter_k<false>, rs_smem());
     bool swapped = false;
     for (int shift = 0; shift < bits; shift += 8) {
         rs_hist_k<<<ntiles, RS_T, 0, s>>>(k, n, shift, hist, ntiles);

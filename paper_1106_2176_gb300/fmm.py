@@ -25,6 +25,7 @@ FMM_OK, FMM_EINVAL, FMM_ENOMEM, FMM_ESTATE, FMM_ECUDA, FMM_ENONFINITE, FMM_ENODE
 FMM_F32, FMM_F64, FMM_HOST_MEM = 0, 1, 0x100
 FMM_FP64, FMM_MIXED = 0, 1
 FMM_M2L_AUTO, FMM_M2L_TENSOR, FMM_M2L_CUDACORE, FMM_M2L_ROTATION = 0, 1, 2, 3
+FMM_PEAK_FP32_FMA, FMM_PEAK_FP32X2_FMA, FMM_PEAK_TF32_MMA = 0, 1, 2
 
 _ERRNAMES = {FMM_EINVAL: "FMM_EINVAL", FMM_ENOMEM: "FMM_ENOMEM", FMM_ESTATE: "FMM_ESTATE",
              FMM_ECUDA: "FMM_ECUDA", FMM_ENONFINITE: "FMM_ENONFINITE", FMM_ENODEV: "FMM_ENODEV"}
@@ -83,6 +84,7 @@ def lib():
     L.fmm_build.argtypes = [_vp, _vp, _vp, i64, i32]
     L.fmm_evaluate.argtypes = [_vp, _vp, _vp]
     L.fmm_get_stats.argtypes = [_vp, ctypes.POINTER(fmm_stats)]
+    L.fmm_get_stats_mean.argtypes = [_vp, i32, ctypes.POINTER(fmm_stats)]
     L.fmm_get_tree_sizes.argtypes = [_vp, ctypes.POINTER(fmm_tree_sizes)]
     L.fmm_export_tree.argtypes = [_vp] + [_vp] * 14
     L.fmm_export_expansions.argtypes = [_vp, _vp, _vp]
@@ -91,6 +93,7 @@ def lib():
     L.fmm_update_charges.argtypes = [_vp, _vp, _vp]
     L.fmm_energy.argtypes = [_vp, _vp, _vp, _vp, ctypes.POINTER(d)]
     L.fmm_energy_adjoint.argtypes = [_vp, d, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+    L.fmm_measure_peak.argtypes = [i32, i32, i32, ctypes.POINTER(d)]
     L.fmm_destroy.argtypes = [_vp]
     L.fmm_last_error.argtypes = [_vp]
     L.fmm_last_error.restype = ctypes.c_char_p
@@ -239,9 +242,14 @@ class FMM:
         return oq, ox, ow
 
     # -- introspection ---------------------------------------------------------
-    def stats(self):
+    def stats(self, mean_of=None):
+        """Counters and phase times (ms) of the last build and evaluation, or,
+        with mean_of=k, the phase times averaged over the last k of each."""
         s = fmm_stats()
-        _check(lib().fmm_get_stats(self._h, ctypes.byref(s)), self._h)
+        if mean_of is None:
+            _check(lib().fmm_get_stats(self._h, ctypes.byref(s)), self._h)
+        else:
+            _check(lib().fmm_get_stats_mean(self._h, int(mean_of), ctypes.byref(s)), self._h)
         return {k: getattr(s, k) for k, _ in fmm_stats._fields_}
 
     def tree_sizes(self):
@@ -302,22 +310,13 @@ class FMM:
             pass
 
 
-def unscale(M, L, level, R0, p):
-    """Turn exported scaled real expansions into complex full-storage ones
-    (entry n*n + n + m), multiplying back by the cell widths w = 2 R0 / 2^level."""
-    C = M.shape[0]
-    w = 2.0 * R0 / (2.0 ** np.asarray(level, dtype=np.float64))
-    outM = np.zeros((C, p * p), complex)
-    outL = np.zeros((C, p * p), complex)
-    for n in range(p):
-        for m in range(0, n + 1):
-            re = n * n + (0 if m == 0 else 2 * m - 1)
-            for X, out, sc in ((M, outM, w ** n), (L, outL, w ** (-(n + 1)))):
-                v = X[:, re] + (1j * X[:, n * n + 2 * m] if m else 0.0)
-                v = v * sc
-                out[:, n * n + n + m] = v
-                out[:, n * n + n - m] = (-1) ** m * np.conj(v)
-    return outM, outL
+def measure_peak(kind, param=0, reps=3):
+    """Measured TFLOP/s of one pipe of the current GPU: "fp32" (scalar FMA),
+    "fp32x2" (packed pair FMA) or "tf32" (tcgen05 MMA, N = param: 128 or 256)."""
+    k = {"fp32": FMM_PEAK_FP32_FMA, "fp32x2": FMM_PEAK_FP32X2_FMA, "tf32": FMM_PEAK_TF32_MMA}[kind]
+    out = ctypes.c_double()
+    _check(lib().fmm_measure_peak(k, int(param), int(reps), ctypes.byref(out)))
+    return out.value
 
 
 def m2l_rotation_host(p, u, M):

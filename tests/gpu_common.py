@@ -41,3 +41,21 @@ def run_fmm(x, q, p, theta, ncrit, precision="fp64", dtype=np.float64, engine="a
     phi, grad = f.evaluate()
     torch.cuda.synchronize()
     return phi.cpu().numpy().astype(np.float64), grad.cpu().numpy().astype(np.float64), f
+
+
+def unscale(M, L, level, R0, p):
+    """Turn exported scaled real expansions into complex full-storage ones
+    (entry n*n + n + m), multiplying back by the cell widths w = 2 R0 / 2^level."""
+    C = M.shape[0]
+    w = 2.0 * R0 / (2.0 ** np.asarray(level, dtype=np.float64))
+    outM = np.zeros((C, p * p), complex)
+    outL = np.zeros((C, p * p), complex)
+    for n in range(p):
+        for m in range(0, n + 1):
+            re = n * n + (0 if m == 0 else 2 * m - 1)
+            for X, out, sc in ((M, outM, w ** n), (L, outL, w ** (-(n + 1)))):
+                v = X[:, re] + (1j * X[:, n * n + 2 * m] if m else 0.0)
+                v = v * sc
+                out[:, n * n + n + m] = v
+                out[:, n * n + n - m] = (-1) ** m * np.conj(v)
+    return outM, outL

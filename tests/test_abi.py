@@ -54,3 +54,14 @@ def test_create_without_device_fails_cleanly(L):
     h = ctypes.c_void_p()
     rc = L.fmm_create(1000, 8, 0.5, 64, ctypes.byref(h))
     assert rc in (fmm.FMM_ENODEV, fmm.FMM_ECUDA) and not h.value
+
+
+def test_measurement_entry_points_check_arguments(L):
+    out = ctypes.c_double()
+    # unknown kind, reps out of range, bad MMA width, NULL output: rejected
+    # before any device call
+    assert L.fmm_measure_peak(7, 0, 3, ctypes.byref(out)) == fmm.FMM_EINVAL
+    assert L.fmm_measure_peak(fmm.FMM_PEAK_FP32_FMA, 0, 0, ctypes.byref(out)) == fmm.FMM_EINVAL
+    assert L.fmm_measure_peak(fmm.FMM_PEAK_TF32_MMA, 64, 3, ctypes.byref(out)) == fmm.FMM_EINVAL
+    assert L.fmm_measure_peak(fmm.FMM_PEAK_FP32_FMA, 0, 3, None) == fmm.FMM_EINVAL
+    assert L.fmm_get_stats_mean(None, 1, None) == fmm.FMM_EINVAL

@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import oracle
-from paper_1106_2176_gb300 import inputs, unscale
+from paper_1106_2176_gb300 import inputs
 
 from gpu_common import ensure_built, rel, run_fmm, torch_cuda
 

@@ -20,11 +20,11 @@ def gpu_tree(x, q, ncrit, theta, dtype=np.float64, precision="fp64", uniform_pat
     return f.export_tree(), f
 
 
-def compare(x, q, ncrit, theta, dtype=np.float64, uniform_path=True):
+def compare(x, q, ncrit, theta, dtype=np.float64, uniform_path=True, T=None):
     g, f = gpu_tree(x, q, ncrit, theta, dtype, uniform_path=uniform_path)
     # the oracle sees exactly the values the GPU saw
-    xo = np.asarray(x, dtype).astype(np.float64)
-    T = oracle.Tree(xo, ncrit, theta)
+    if T is None:
+        T = oracle.Tree(np.asarray(x, dtype).astype(np.float64), ncrit, theta)
     ic, key, perm = T.particles()
     org, R0 = T.box()
     assert np.array_equal(g["box"][:3], org) and g["box"][3] == R0
@@ -44,6 +44,7 @@ def compare(x, q, ncrit, theta, dtype=np.float64, uniform_path=True):
     # deepest level and every level is full
     full = T.nleaves == 8 ** T.depth and T.ncells == (8 ** (T.depth + 1) - 1) // 7 and T.depth >= 1
     assert s["uniform_path"] == int(uniform_path and full)
+    f.close()
     return T
 
 
@@ -96,3 +97,32 @@ def test_duplicate_keys_sorted_stably():
     x = base[rng.integers(0, 50, 5000)]
     q = rng.uniform(-1, 1, 5000)
     compare(x, q, 4, 0.5)
+
+
+@pytest.fixture(scope="module")
+def bench_size():
+    """The scale workload the bench times: N = 10^7 uniform cube, FP32
+    positions, ncrit = 128, theta = 0.5 (a full octree of depth 6, 262,144
+    leaves, 4.4e7 P2P and 3.2e8 M2L pairs), with the oracle's tree of it."""
+    n = 10_000_000
+    x, q = inputs.uniform_cube(n, 3, dtype=np.float32)
+    T = oracle.Tree(x.astype(np.float64), 128, 0.5)
+    return x, q, T
+
+
+@pytest.mark.parametrize("uniform_path", [True, False])
+def test_bench_size_tree_and_lists_bit_exact(bench_size, uniform_path):
+    # every array in full: keys, permutation, the seven cell arrays and both
+    # CSR lists (the M2L list is expanded from the implicit lattice pairs)
+    x, q, T = bench_size
+    compare(x, q, 128, 0.5, dtype=np.float32, uniform_path=uniform_path, T=T)
+    assert T.depth == 6 and T.nleaves == 8 ** 6
+
+
+def test_differentiation_tree_bit_exact():
+    # the adaptive tree of the differentiation workload: N = 10^6 Plummer
+    # sphere, FP32 positions, ncrit = 64, theta = 0.5 (pairs of cells on
+    # different levels in both lists)
+    x, q = inputs.plummer(1_000_000, 7)
+    T = compare(x.astype(np.float32), q.astype(np.float32), 64, 0.5, dtype=np.float32)
+    assert T.nleaves < 8 ** T.depth

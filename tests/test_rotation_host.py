@@ -45,9 +45,9 @@ def test_rotation_m2l_equals_dense_m2l(host, P):
     for u in U:
         Lref = _packed(oracle.m2l(P, M, np.zeros(3), np.array(u)), P)
         L = host(P, u, Mp)
-        # up to p = 16 (the GPU engine's range) the fitted rotation maps hold
-        # 1e-12; the factorial scalings of degrees 17..19 cost about one digit
-        tol = 1e-12 if P <= 16 else 1e-11
+        # closed-form Wigner-d maps: the whole rotate-translate-rotate chain
+        # stays within 1e-14 of the dense sum up to p = 20
+        tol = 1e-13
         assert np.linalg.norm(L - Lref) <= tol * np.linalg.norm(Lref), (P, u)
 
 

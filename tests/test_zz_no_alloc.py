@@ -1,9 +1,9 @@
 """The allocation-free entry point, fmm_morton_sort_noalloc, against fmm_build.
 
-Some callers cannot allocate device memory when they need the result: code
-that is recording a CUDA graph (cudaMalloc cannot be captured), a loop with a
-fixed memory budget, or an application whose device memory is owned by
-another framework. fmm_morton_sort_noalloc gives them the Morton keys and the
+Some callers cannot allocate device memory when they need the result: a
+loop with a fixed device-memory budget (a cudaMalloc can block on the device
+and can fail part-way through a run), or an application whose device memory
+is owned by another framework's allocator. fmm_morton_sort_noalloc gives them the Morton keys and the
 sorting permutation of the octree build using only the caller's buffers and a
 fixed scratch array that the library reserves when it is loaded.
 
