@@ -7,7 +7,7 @@ import pytest
 import oracle
 from paper_1106_2176_gb300 import inputs
 
-from gpu_common import ensure_built, rel, run_fmm, torch_cuda
+from gpu_common import ensure_built, rel, run_fmm, torch_cuda, unscale
 
 pytestmark = pytest.mark.gpu
 
