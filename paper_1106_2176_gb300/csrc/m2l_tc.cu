@@ -19,17 +19,23 @@
 // Per CTA (320 threads: two groups of 4 worker warps, 1 MMA warp, 1 operator
 // warp), for every unit (v, k-block) of 32 coefficients, taken by the group
 // u % 2:
-//   - each thread of the group copies, with cp.async, its target row's raw
-//     FP32 multipole block (source found by a lattice lookup fetched ahead into
-//     the thread's ring; zero fill if the cell is absent) into a 128B-swizzled
-//     stage of the group's A ring;
+//   - the group gathers the unit's raw FP32 multipole rows with cp.async into
+//     a 128B-swizzled stage of its A ring; each warp fills its own 32 rows,
+//     eight lanes per row, so that one copy instruction covers four whole
+//     rows (sources found by lattice lookups fetched ahead into a ring; zero
+//     fill where a cell is absent);
+//   - once the stage is full, each thread splits its row into TF32 hi and lo
+//     (lo = a - hi), stores both in the unit's compute stage in tensor memory
+//     and issues the copies of its group's next unit;
 //   - the operator warp bulk-copies the pre-split, pre-swizzled [T_hi ; T_lo]
-//     operator block into the unit's compute stage;
-//   - once its A stage is full, each thread splits its row into TF32 hi and lo
-//     (lo = a - hi), stores both in the compute stage's tensor-memory columns
-//     and refills its A stage;
-//   - one thread of the MMA warp issues the tcgen05.mma (A from tensor memory,
-//     the operator from shared memory) and commits to the stage's mbarrier.
+//     operator: for p <= 8 the blocks of a whole vector into a ring of its
+//     own, several vectors ahead; otherwise one block into the unit's
+//     compute stage;
+//   - the MMA warp issues the tcgen05.mma (A from tensor memory, the operator
+//     from shared memory) and commits; for p <= 8 it takes one whole vector
+//     per iteration, waiting once on a barrier that both worker groups and the
+//     operator warp arrive on, because every wait and commit costs the issuing
+//     thread a few hundred cycles.
 // Every wait is bounded; on a timeout the kernel records an error code and
 // leaves after its copies have landed and its TMEM is released.
 #include <algorithm>
@@ -59,11 +65,14 @@ __device__ int g_no_cell = -1;
 // hidden behind the other's. Warp 8 issues the MMAs; warp 9 copies the
 // operator blocks.
 //   A raw rings (RSG stages per group, shared memory): the gathered FP32
-//     multipoles of a unit, 128 B per row, 128B-swizzled. A thread copies and
-//     reads only its own row, so it refills a stage right after its split.
+//     multipoles of a unit, 128 B per row, 128B-swizzled. A warp copies and
+//     reads only its own 32 rows, so it refills a stage right after the
+//     warp's split.
 //   compute stages (CS): A_hi, A_lo in tensor memory (written by the unit's
-//     group with tcgen05.st, read by the MMA as its A operand) and the operator
-//     block in shared memory (one bulk copy). One MMA commit frees both.
+//     group with tcgen05.st, read by the MMA as its A operand), freed by the
+//     MMA commit of the unit (or of its vector).
+//   operator blocks in shared memory: VEC (p <= 8) a ring of OSV whole
+//     vectors; otherwise one block in each compute stage.
 // Tensor memory: AC accumulator buffers of 2 NP columns (main | correction)
 // followed by the CS A stages of 64 columns (hi 32 | lo 32). Thread (r, g)
 // drains output columns [g HN, (g + 1) HN) of row r.
@@ -77,18 +86,35 @@ struct TcCfg {
     static constexpr int A_RAW = M * 128;          // raw A k-block (FP32, swizzled)
     static constexpr int B_RAW = 2 * NP * 128;     // [T_hi ; T_lo] k-block (TF32 pair, swizzled)
     static constexpr int ACOLS = 64;               // TMEM columns of one A stage (hi, lo)
-    static constexpr int AC = 4 * NP + 2 * ACOLS <= 512 ? 2 : 1;  // accumulator buffers
-    static constexpr int CS = AC == 2 ? (4 * NP + 4 * ACOLS <= 512 ? 4 : 2)
-                                      : ((512 - 2 * NP) / ACOLS >= 4 ? 4 : (512 - 2 * NP) / ACOLS);
+    // accumulator buffers: two (the drain overlaps the next MMAs) when the
+    // compute stages of at least one whole vector (KB) still fit beside them
+    static constexpr int CS2 = (512 - 4 * NP) / ACOLS >= 4 ? 4 : (512 - 4 * NP) / ACOLS;
+    static constexpr int AC = CS2 >= KB && CS2 >= 2 ? 2 : 1;
+    static constexpr int CS = AC == 2 ? CS2 : ((512 - 2 * NP) / ACOLS >= 4 ? 4 : (512 - 2 * NP) / ACOLS);
     static constexpr int ACC_COLS = AC * 2 * NP;
     static constexpr int TCOLS = 512;
     static constexpr int QU = 8;                   // lookahead of the source lookups (units of the group)
     static constexpr int RINGU = 2 * QU;
     static constexpr int RING = NG * RINGU * M * 4;
+    // VEC (p <= 8): the MMA warp takes one stencil vector (KB units) per
+    // iteration, and the operator blocks of whole vectors sit in a ring of
+    // their own (OSV slots), filled up to OSV vectors ahead and freed by one
+    // commit per vector (VR "vector done" barriers). Otherwise the operator
+    // block of a unit travels in that unit's compute stage.
+    static constexpr bool VEC = KB <= 2 && CS >= 2 * KB;
+    static constexpr int OPV = KB * B_RAW;         // operator bytes of one vector
+    static constexpr int VR = 8;
+    static constexpr int RSG_V = 2;
+    static constexpr int OSV_FIT = (220 * 1024 - RING - 512 - 1024 - NG * RSG_V * A_RAW) / OPV;
+    static constexpr int OSV = OSV_FIT > 6 ? 6 : OSV_FIT;
     static constexpr int BUDGET = 220 * 1024 - RING - 512 - 1024 - CS * B_RAW;
-    static constexpr int RSG = BUDGET / (NG * A_RAW) >= 3 ? 3 : BUDGET / (NG * A_RAW);  // raw stages per group
-    static constexpr int SMEM = NG * RSG * A_RAW + CS * B_RAW + RING + 512 + 1024;
-    static_assert(RSG >= 2 && RSG <= 3 && CS >= 2 && QU >= RSG && ACC_COLS + CS * ACOLS <= TCOLS && SMEM <= 227 * 1024,
+    static constexpr int RSG_U = BUDGET / (NG * A_RAW) >= 3 ? 3 : BUDGET / (NG * A_RAW);
+    static constexpr int RSG = VEC ? RSG_V : RSG_U;  // raw stages per group
+    static constexpr int OPB = VEC ? OSV * OPV : CS * B_RAW;  // operator bytes in shared memory
+    static constexpr int SMEM = NG * RSG * A_RAW + OPB + RING + 512 + 1024;
+    static_assert(!VEC || (OSV >= 2 && OSV <= VR), "operator ring");
+    static_assert(RSG >= 2 && RSG <= 3 && CS >= 2 && CS >= KB && QU >= RSG && ACC_COLS + CS * ACOLS <= TCOLS &&
+                      SMEM <= 227 * 1024,
                   "stage budget");
     static constexpr int GV = 8;                   // vectors per accumulator drain
     static constexpr int HN = NP / 2;              // output coefficients per thread
@@ -119,17 +145,21 @@ __global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     unsigned char *araw = base;                           // NG x RSG x A_RAW
-    unsigned char *bops = araw + NG * RSG * C::A_RAW;     // CS x B_RAW
-    int *ring = reinterpret_cast<int *>(bops + CS * C::B_RAW);  // NG x RINGU x M
+    constexpr bool VEC = C::VEC;
+    constexpr int NB = VEC ? C::OSV : CS;     // operator slots
+    constexpr int NF = VEC ? C::VR : CS;      // "free" barriers: per vector (VEC) or per compute stage
+    unsigned char *bops = araw + NG * RSG * C::A_RAW;     // operator slots (VEC: OSV x OPV; else CS x B_RAW)
+    int *ring = reinterpret_cast<int *>(bops + C::OPB);  // NG x RINGU x M
     uint64_t *bar = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(ring) + C::RING);
     uint64_t *a_full = bar;                   // NG x RSG: cp.async arrivals of the group's 128 threads
-    uint64_t *b_full = a_full + NG * RSG;     // CS: operator copy (transaction bytes)
-    uint64_t *cmp_full = b_full + CS;         // CS: one arrival per warp of the unit's group
-    uint64_t *cmp_free = cmp_full + CS;       // CS: MMA commits
-    uint64_t *acc_full = cmp_free + CS;       // AC: MMA commits at the end of a group of vectors
+    uint64_t *b_full = a_full + NG * RSG;     // NB: operator copies (transaction bytes)
+    uint64_t *cmp_full = b_full + NB;         // CS: one arrival per warp of the unit's group
+    uint64_t *cmp_free = cmp_full + CS;       // NF: MMA commits (VEC: vector w done, slot w % VR)
+    uint64_t *acc_full = cmp_free + NF;       // AC: MMA commits at the end of a group of vectors
     uint64_t *acc_empty = acc_full + AC;      // AC: one arrival per worker warp after a drain
     uint64_t *fin = acc_empty + AC;           // 1
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(fin + 1);
+    uint64_t *ready = fin + 1;                // VEC, VR: vector w ready (its KB units split, its operator landed)
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(ready + C::VR);
     int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -159,16 +189,17 @@ __global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
 
     if (tid == 0) {
         for (int s = 0; s < NG * RSG; s++) mbar_init(&a_full[s], 128);
-        for (int s = 0; s < CS; s++) {
-            mbar_init(&b_full[s], 1);
-            mbar_init(&cmp_full[s], C::NW / C::NG);
-            mbar_init(&cmp_free[s], 1);
-        }
+        for (int s = 0; s < NB; s++) mbar_init(&b_full[s], 1);
+        for (int s = 0; s < CS; s++) mbar_init(&cmp_full[s], C::NW / C::NG);
+        for (int s = 0; s < NF; s++) mbar_init(&cmp_free[s], 1);
         for (int b = 0; b < AC; b++) {
             mbar_init(&acc_full[b], 1);
             mbar_init(&acc_empty[b], C::NW);
         }
         mbar_init(fin, 1);
+        // per vector: one arrival per warp of the groups that split its KB
+        // units, and one from the operator warp once the operator landed
+        for (int s = 0; s < C::VR; s++) mbar_init(&ready[s], 4 * KB + 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -185,59 +216,108 @@ __global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
 
     if (warp == C::MMA_WARP) {
         // ------------------------------------------------------------ MMA warp
+        // VEC: one iteration per stencil vector (its KB compute stages and its
+        // operator slot), so the waits and commits, a few hundred cycles each
+        // on the issuing thread, are paid once per vector. Otherwise one
+        // iteration per unit. The whole warp runs the loop; lane 0 issues.
+        const uint32_t id_full = idesc_tf32(128, 2 * NP), id_half = idesc_tf32(128, NP);
+        constexpr int STEP = VEC ? KB : 1;
+        for (int u0 = 0; u0 < nunits; u0 += STEP) {
+            const int vi = u0 / KB, g = vi / C::GV, b = g % AC;
+            bool ok = true;
+#pragma unroll
+            for (int kb = 0; kb < (VEC ? 0 : STEP); kb++) ok = ok && mbar_wait(&cmp_full[(u0 + kb) % CS], (uint32_t)(((u0 + kb) / CS) & 1));
+            if (VEC) ok = mbar_wait(&ready[vi % C::VR], (uint32_t)((vi / C::VR) & 1));
+            if (ok && u0 % KB == 0 && vi % C::GV == 0 && g >= AC) ok = mbar_wait(&acc_empty[b], (uint32_t)(((g - AC) / AC) & 1));
+            ok = __all_sync(0xffffffffu, ok) && !*(volatile int *)abort_flag;
+            if (!ok) {
+                if (lane == 0) atomicExch(abort_flag, 1);
+                break;
+            }
+            tc_fence_after();
+            if (lane == 0) {
+                const uint32_t dmain = tmem + (uint32_t)(b * 2 * NP), dcorr = dmain + NP;
+                const bool first = vi % C::GV == 0;
+#pragma unroll
+                for (int kk = 0; kk < STEP; kk++) {
+                    const int u = u0 + kk, c = u % CS, kb = u % KB;
+                    const uint32_t ahi = tmem + (uint32_t)(C::ACC_COLS + c * C::ACOLS), alo = ahi + 32;
+                    const uint32_t bb = VEC ? smem_u32(bops + (vi % NB) * C::OPV + kb * C::B_RAW) : smem_u32(bops + c * C::B_RAW);
+#pragma unroll
+                    for (int k = 0; k < 4; k++) {
+                        // A_hi [T_hi ; T_lo] -> main | correction, then A_lo T_hi -> correction
+                        mma_tf32_ta(dmain, ahi + 8 * k, sdesc(bb + 32 * k), id_full, (first && kb == 0 && k == 0) ? 0u : 1u);
+                        mma_tf32_ta(dcorr, alo + 8 * k, sdesc(bb + 32 * k), id_half, 1u);
+                    }
+                }
+                if (VEC) mma_commit(&cmp_free[vi % NF]);
+                else mma_commit(&cmp_free[u0 % CS]);
+                if ((u0 + STEP) % KB == 0 && ((vi % C::GV == C::GV - 1) || vi == nv - 1)) mma_commit(&acc_full[b]);
+            }
+            __syncwarp();
+        }
         if (lane == 0) {
-            const uint32_t id_full = idesc_tf32(128, 2 * NP), id_half = idesc_tf32(128, NP);
-            for (int u = 0; u < nunits; u++) {
+            // every commit has arrived before the shared memory goes away
+            mma_commit(fin);
+            mbar_wait(fin, 0);
+            if (VEC)
+                for (int w = max(0, nv - NF); w < nv; w++) mbar_wait(&cmp_free[w % NF], (uint32_t)((w / NF) & 1));
+            else
+                for (int u = max(0, nunits - CS); u < nunits; u++) mbar_wait(&cmp_free[u % CS], (uint32_t)((u / CS) & 1));
+        }
+        __syncwarp();
+    } else if (warp == C::B_WARP) {
+        // ------------------------------------------------------- operator warp
+        // VEC: the vector's KB operator blocks (contiguous in the image) in one
+        // bulk copy into slot w % OSV, once vector w - OSV is done. Otherwise
+        // one block per unit into its compute stage, once that stage is free.
+        if (lane == 0) {
+            int issued = 0;
+            const int nitems = VEC ? nv : nunits;
+            for (int w = 0; w < nitems; w++) {
                 if (*(volatile int *)abort_flag) break;
-                const int c = u % CS;
-                const int vi = u / KB, kb = u % KB, g = vi / C::GV, b = g % AC;
-                bool ok = mbar_wait(&cmp_full[c], (uint32_t)((u / CS) & 1));
-                if (ok && kb == 0 && vi % C::GV == 0 && g >= AC)
-                    ok = mbar_wait(&acc_empty[b], (uint32_t)(((g - AC) / AC) & 1));
+                bool ok = true;
+                if (VEC) {
+                    if (w >= NB) ok = mbar_wait(&cmp_free[(w - NB) % NF], (uint32_t)(((w - NB) / NF) & 1));
+                } else if (w >= CS) {
+                    ok = mbar_wait(&cmp_free[w % CS], (uint32_t)(((w - CS) / CS) & 1));
+                }
                 if (!ok) {
                     atomicExch(abort_flag, 1);
                     break;
                 }
-                tc_fence_after();
-                const uint32_t ahi = tmem + (uint32_t)(C::ACC_COLS + c * C::ACOLS), alo = ahi + 32;
-                const uint32_t bb = smem_u32(bops + c * C::B_RAW);
-                const uint32_t dmain = tmem + (uint32_t)(b * 2 * NP), dcorr = dmain + NP;
-                const bool first = (vi % C::GV == 0) && kb == 0;
-#pragma unroll
-                for (int k = 0; k < 4; k++) {
-                    // A_hi [T_hi ; T_lo] -> main | correction, then A_lo T_hi -> correction
-                    mma_tf32_ta(dmain, ahi + 8 * k, sdesc(bb + 32 * k), id_full, (first && k == 0) ? 0u : 1u);
-                    mma_tf32_ta(dcorr, alo + 8 * k, sdesc(bb + 32 * k), id_half, 1u);
+                const int bs = w % NB;
+                if (VEC) {
+                    const int4 v = st[e0 + w];
+                    mbar_arrive_tx(&b_full[bs], C::OPV);
+                    bulk_g2s(smem_u32(bops + bs * C::OPV), ttab + (size_t)(v.w & 0xffff) * C::OPV, C::OPV, &b_full[bs]);
+                    // vector w - 1's operator has landed: its readiness
+                    if (w >= 1) {
+                        if (!mbar_wait(&b_full[(w - 1) % NB], (uint32_t)(((w - 1) / NB) & 1))) {
+                            atomicExch(abort_flag, 1);
+                            issued = w + 1;
+                            break;
+                        }
+                        mbar_arrive(&ready[(w - 1) % C::VR]);
+                    }
+                } else {
+                    const int4 v = st[e0 + w / KB];
+                    mbar_arrive_tx(&b_full[bs], C::B_RAW);
+                    bulk_g2s(smem_u32(bops + bs * C::B_RAW), ttab + ((size_t)(v.w & 0xffff) * KB + w % KB) * C::B_RAW,
+                             C::B_RAW, &b_full[bs]);
                 }
-                mma_commit(&cmp_free[c]);
-                if ((kb == KB - 1) && ((vi % C::GV == C::GV - 1) || vi == nv - 1)) mma_commit(&acc_full[b]);
+                issued = w + 1;
             }
-            // every commit has arrived before the shared memory goes away
-            mma_commit(fin);
-            mbar_wait(fin, 0);
-            for (int u = max(0, nunits - CS); u < nunits; u++) mbar_wait(&cmp_free[u % CS], (uint32_t)((u / CS) & 1));
-        }
-    } else if (warp == C::B_WARP) {
-        // ------------------------------------------------------- operator warp
-        if (lane == 0) {
-            int issued = 0;
-            for (int u = 0; u < nunits; u++) {
-                if (*(volatile int *)abort_flag) break;
-                const int c = u % CS;
-                if (u >= CS && !mbar_wait(&cmp_free[c], (uint32_t)(((u - CS) / CS) & 1))) {
+            if (VEC && issued == nitems && nitems > 0 && !*(volatile int *)abort_flag) {
+                if (mbar_wait(&b_full[(nitems - 1) % NB], (uint32_t)(((nitems - 1) / NB) & 1)))
+                    mbar_arrive(&ready[(nitems - 1) % C::VR]);
+                else
                     atomicExch(abort_flag, 1);
-                    break;
-                }
-                const int4 v = st[e0 + u / KB];
-                mbar_arrive_tx(&b_full[c], C::B_RAW);
-                bulk_g2s(smem_u32(bops + c * C::B_RAW), ttab + ((size_t)(v.w & 0xffff) * KB + u % KB) * C::B_RAW, C::B_RAW,
-                         &b_full[c]);
-                issued = u + 1;
             }
             // copies still in flight when the pipeline stopped early land
             // before the shared memory goes away (bounded waits)
             if (*(volatile int *)abort_flag)
-                for (int u = max(0, issued - CS); u < issued; u++) mbar_wait(&b_full[u % CS], (uint32_t)((u / CS) & 1));
+                for (int w = max(0, issued - NB); w < issued; w++) mbar_wait(&b_full[w % NB], (uint32_t)((w / NB) & 1));
         }
     } else {
         // ---------------------------------------------------------- worker warps
@@ -255,12 +335,20 @@ __global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
         // ahead into ring slot j % RINGU (cp.async of the lattice-map entry, or
         // a search of the level's keys); only this thread reads the slot, after
         // the raw-stage barrier that its own later copies arrive on
+        // stencil entry of the group's unit j; the next call's entry is
+        // loaded one call ahead (calls come in order), so its latency is hidden
+        int4 st_next = make_int4(0, 0, 0, 0);
+        int st_next_j = -1;
         auto fetch = [&](int j) {
             if (j >= nown) return;
+            const int4 v = st_next_j == j ? st_next : st[e0 + (2 * j + g) / KB];
+            if (j + 1 < nown) {
+                st_next = st[e0 + (2 * (j + 1) + g) / KB];
+                st_next_j = j + 1;
+            }
             const uint32_t slot = smem_u32(myring + (j % RINGU) * C::M + row);
             int r = -1;
             if (cell >= 0) {
-                const int4 v = st[e0 + (2 * j + g) / KB];
                 const int x = px + v.x, y = py + v.y, z = pz + v.z, side = 1 << rl;
                 if (((v.w >> (16 + ro)) & 1) && x >= 0 && y >= 0 && z >= 0 && x < side && y < side && z < side) {
                     if (dense) {
@@ -273,16 +361,24 @@ __global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
             if (dense) cp_async4(slot, &g_no_cell);
             else myring[(j % RINGU) * C::M + row] = r;
         };
-        // copy the group's unit j into its raw stage j % RSG: this thread's row (128 B)
+        // copy the group's unit j into its raw stage j % RSG. The warp fills
+        // its own 32 rows: in copy i, lanes 8s .. 8s+7 take the eight 16-byte
+        // chunks of row 4i + s, so one warp instruction reads 4 whole rows
+        // (4 cache lines, not 32); the source of each row comes from the lane
+        // that looked it up
         auto load_unit = [&](int j) {
             const int u = 2 * j + g, kb = u % KB;
             const int src = myring[(j % RINGU) * C::M + row];
             fetch(j + QU);
-            const uint32_t ar = smem_u32(araw + (g * RSG + j % RSG) * C::A_RAW) + (uint32_t)row * 128u;
-            const float *gs = mrow + ((size_t)(src >= 0 ? src : 0) * KP + kb * 32);
+            const uint32_t ab = smem_u32(araw + (g * RSG + j % RSG) * C::A_RAW);
+            const int ch = lane & 7, sub = lane >> 3, r0 = row - lane;  // r0: the warp's first row
 #pragma unroll
-            for (int ch = 0; ch < 8; ch++)
-                cp_async16(ar + ((((uint32_t)ch) ^ ((uint32_t)row & 7u)) << 4), gs + ch * 4, src >= 0 ? 16u : 0u);
+            for (int i = 0; i < 8; i++) {
+                const int rr = r0 + 4 * i + sub;
+                const int s = __shfl_sync(0xffffffffu, src, 4 * i + sub);
+                const float *gs = mrow + ((size_t)(s >= 0 ? s : 0) * KP + kb * 32) + ch * 4;
+                cp_async16(ab + (uint32_t)rr * 128u + ((((uint32_t)ch) ^ ((uint32_t)rr & 7u)) << 4), gs, s >= 0 ? 16u : 0u);
+            }
             cp_async_arrive_noinc(&a_full[g * RSG + j % RSG]);
         };
 
@@ -329,8 +425,13 @@ __global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
                 drained++;
                 if (*(volatile int *)abort_flag) break;
             }
-            const bool ok = mbar_wait2(u >= CS ? 3u : 1u, &a_full[g * RSG + j % RSG], (uint32_t)((j / RSG) & 1),
-                                       &cmp_free[c], (uint32_t)((max(u - CS, 0) / CS) & 1));
+            // the compute stage is free once the unit that used it last (u - CS)
+            // is done: its vector's commit (VEC) or its own (otherwise)
+            const int wprev = max(u - CS, 0) / KB;
+            const bool ok = VEC ? mbar_wait2(u >= CS ? 3u : 1u, &a_full[g * RSG + j % RSG], (uint32_t)((j / RSG) & 1),
+                                             &cmp_free[wprev % NF], (uint32_t)((wprev / NF) & 1))
+                                : mbar_wait2(u >= CS ? 3u : 1u, &a_full[g * RSG + j % RSG], (uint32_t)((j / RSG) & 1),
+                                             &cmp_free[c], (uint32_t)((max(u - CS, 0) / CS) & 1));
             if (!ok) {
                 atomicExch(abort_flag, 1);
                 break;
@@ -356,16 +457,18 @@ __global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
                 tmem_st16(ta + 16 * h, hi);
                 tmem_st16(ta + 32 + 16 * h, lo);
             }
+            // every lane of the warp has read its row of the raw stage: the
+            // next unit's copies may overwrite it while the stores complete
+            __syncwarp();
+            if (j + RSG < nown) load_unit(j + RSG);
             tmem_wait_st();
             tc_fence_before();
             __syncwarp();
             if (lane == 0) {
-                // the group's first warp also waits for the operator block
-                if ((warp & 3) == 0 && !mbar_wait(&b_full[c], (uint32_t)((u / CS) & 1))) atomicExch(abort_flag, 1);
-                mbar_arrive(&cmp_full[c]);
+                // (per unit) the group's first warp also waits for the operator block
+                if (!VEC && (warp & 3) == 0 && !mbar_wait(&b_full[c], (uint32_t)((u / CS) & 1))) atomicExch(abort_flag, 1);
+                mbar_arrive(VEC ? &ready[(u / KB) % C::VR] : &cmp_full[c]);
             }
-            // this thread has read its row of the raw stage: refill it
-            if (j + RSG < nown) load_unit(j + RSG);
             // two accumulator buffers: drain group gg once group gg + 1 is well under way
             if (AC == 2 && vi >= C::DRAIN_AT && (vi - C::DRAIN_AT) / C::GV > drained) {
                 drain(drained);
