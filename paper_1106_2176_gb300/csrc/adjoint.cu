@@ -41,6 +41,7 @@ void update_charges(fmm_ctx *h, const void *q, const void *w)
                                                           xs64, xs32);
     count_launch(h);
     check_launch("charges");
+    p2p_pairs_fill(h, s);  // the packed P2P reads the charges from its pair records
 }
 
 // E = 1/2 sum w q phi: FP64 block sums, then the blocks in order

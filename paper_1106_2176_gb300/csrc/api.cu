@@ -97,7 +97,7 @@ fmm_ctx::~fmm_ctx()
                            &idx2, &hist, &scan_tmp, &xs64, &xs32, &xs32lo, &c_level, &c_anchor, &c_begin, &c_end, &c_child,
                            &c_nchild, &c_parent, &c_xyz, &split_cnt, &split_off, &split_bnd, &leaves, &frontA,
                            &frontB, &p2p_pairs, &m2lx_pairs, &near_dev, &pair_keys, &pair_keys2, &pair_vals, &pair_vals2,
-                           &p2p_ptr, &p2p_src, &p2p_runs, &p2p_nrun, &m2lx_ptr, &m2lx_src, &row_cnt, &counters, &lvl_desc, &map_pool,
+                           &p2p_ptr, &p2p_src, &p2p_runs, &p2p_nrun, &pr_pad, &pr_flag, &pr_pairs, &p2p_runs_pr, &m2lx_ptr, &m2lx_src, &row_cnt, &counters, &lvl_desc, &map_pool,
                            &m2l_tgt, &m2l_tiles, &m2l_misc, &msplit, &Mexp, &Lexp, &far, &near, &out_phi, &out_grad,
                            &direct_part, &rot_tab};
     for (auto *b : bufs) b->release();
@@ -477,10 +477,11 @@ int fmm_get_stats(fmm_handle h, fmm_stats *out)
     out->n_stencil = h->st_off.empty() ? 0 : h->st_off[8];
     out->m2l_engine = h->engine_used;
     if (h->m2l_misc.p) {
-        int e = 0;
-        FMM_CUDA_TRY(cudaMemcpy(&e, h->m2l_misc.as<unsigned>() + 24 * (FMM_MAXLEVEL + 1) + 4, sizeof(int),
+        // device-side timeouts of the last evaluate: M2L (bit 0), P2P (bit 1)
+        int e[2] = {0, 0};
+        FMM_CUDA_TRY(cudaMemcpy(e, h->m2l_misc.as<unsigned>() + 24 * (FMM_MAXLEVEL + 1) + 4, sizeof(e),
                                 cudaMemcpyDeviceToHost));
-        out->async_error = e;
+        out->async_error = (e[0] ? 1 : 0) | (e[1] ? 2 : 0);
     }
     out->kernel_launches = h->launches;
     out->uniform_path = h->uniform_used ? 1 : 0;

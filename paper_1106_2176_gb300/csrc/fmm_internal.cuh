@@ -189,6 +189,11 @@ struct fmm_ctx {
     fmm::DevBuf pair_keys, pair_keys2, pair_vals, pair_vals2;
     fmm::DevBuf p2p_ptr, p2p_src, m2lx_ptr, m2lx_src, row_cnt;
     fmm::DevBuf p2p_runs, p2p_nrun;     // P2P sources merged into particle runs per target leaf
+    // packed P2P of FP32 inputs: sorted particles as pair records (x0 x1 y0 y1 | z0 z1 q0 q1), each leaf
+    // padded to an even count by a zero-charge copy of its last particle; pad[i] = padding before
+    // particle i; the runs in pair units
+    fmm::DevBuf pr_pad, pr_flag, pr_pairs, p2p_runs_pr;
+    bool pr_ready = false;
     fmm::DevBuf counters;
     fmm::DevBuf lvl_desc, map_pool;
     fmm::DevBuf m2l_tgt, m2l_tiles, m2l_misc;
@@ -250,6 +255,8 @@ void m2l_tensor(fmm_ctx *h, float *L, const float *M);
 
 // p2p.cu
 void near_field(fmm_ctx *h, cudaStream_t s);  // P2P into h->near
+void p2p_prepare(fmm_ctx *h, cudaStream_t s);  // pair records and pair-unit runs of the packed P2P (build)
+void p2p_pairs_fill(fmm_ctx *h, cudaStream_t s);  // pair records from the sorted particles (build, new charges)
 void combine_unsort(fmm_ctx *h, void *phi, void *grad);
 void update_charges(fmm_ctx *h, const void *q, const void *w);
 double energy(fmm_ctx *h, const void *w, const void *q, const void *phi);

@@ -21,6 +21,7 @@
 #include <type_traits>
 
 #include "fmm_internal.cuh"
+#include "ptx_sm100.cuh"
 
 namespace fmm {
 
@@ -110,7 +111,7 @@ constexpr int P2P_MAXSEG = 32;
 // source pairs summed in FP32 before they are folded into the TwoSum state,
 // and the source pairs of one fully unrolled step of the pair loop
 #ifndef FMM_P2P_FOLD
-#define FMM_P2P_FOLD 128
+#define FMM_P2P_FOLD 256
 #endif
 #ifndef FMM_P2P_STEP
 #define FMM_P2P_STEP 8
@@ -643,6 +644,347 @@ __global__ void __launch_bounds__(P2P_T, sizeof(T) == 4 ? FMM_P2P_MINB : 1) p2p_
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Packed P2P of FP32 inputs with source chunks staged by bulk copies.
+//
+// The sorted particles are kept a second time as pair records
+// (x0 x1 y0 y1 | z0 z1 q0 q1), each leaf padded to an even count by a
+// zero-charge copy of its last particle, so every run of source leaves is a
+// whole number of records and copies as one contiguous block. Warp 0 turns
+// the target leaf's runs into chunks of up to PR_CHP records: one
+// cp.async.bulk per run piece, completion counted in bytes on the chunk's
+// mbarrier, PR_D chunks ahead of the one being computed. The warps compute a
+// chunk as soon as it has landed and release it with one arrival each, so no
+// CTA-wide barrier separates the chunks. The arithmetic and the summation
+// order per thread are those of p2p_k. Ring shape (2 buffers of 344 pairs,
+// one chunk ahead, packed sums folded every 256 pairs) from a sweep at
+// N = 10^7: 31.5 ms against 32.3 ms for the cp.async staging of p2p_k.
+// ---------------------------------------------------------------------------
+#ifndef FMM_PR_NB
+#define FMM_PR_NB 2
+#endif
+#ifndef FMM_PR_CHP
+#define FMM_PR_CHP 344
+#endif
+#ifndef FMM_PR_D
+#define FMM_PR_D (FMM_PR_NB - 1)
+#endif
+constexpr int PR_NB = FMM_PR_NB;    // chunk buffers
+constexpr int PR_CHP = FMM_PR_CHP;  // source pairs per chunk
+constexpr int PR_D = FMM_PR_D;      // chunk c + PR_D is produced when chunk c starts (PR_D < PR_NB)
+static_assert(PR_D >= 1 && PR_D < PR_NB, "produce ahead within the ring");
+
+// flag[i] = 1 for the last particle of a leaf with an odd count
+__global__ void pr_flag_k(int64_t n, const int *__restrict__ pcell, const int *__restrict__ begin,
+                          const int *__restrict__ end, unsigned *__restrict__ flag)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int c = pcell[i];
+    flag[i] = (i == end[c] - 1 && ((end[c] - begin[c]) & 1)) ? 1u : 0u;
+}
+
+// particle i sits at padded position i + pad[i] (half (i + pad[i]) & 1 of
+// record (i + pad[i]) / 2); the last particle of an odd leaf, at an even
+// position, also fills the other half with its position and charge zero
+__global__ void pr_fill_k(int64_t n, const float4 *__restrict__ xs, const unsigned *__restrict__ pad,
+                          const unsigned *__restrict__ flag, float *__restrict__ pairs)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4 a = xs[i];
+    const int64_t pi = i + pad[i];
+    float *rec = pairs + 8 * (pi >> 1);
+    const int hh = (int)(pi & 1);
+    rec[hh] = a.x;
+    rec[2 + hh] = a.y;
+    rec[4 + hh] = a.z;
+    rec[6 + hh] = a.w;
+    if (flag[i]) {
+        rec[1] = a.x;
+        rec[3] = a.y;
+        rec[5] = a.z;
+        rec[7] = 0.f;
+    }
+}
+
+// runs of particles [b, e) (whole leaves) -> runs of records
+// [(b + pad[b]) / 2, (e + pad[e - 1] + flag[e - 1]) / 2)
+__global__ void pr_runs_k(int nleaves, const int *__restrict__ leaves, const int *__restrict__ ptr,
+                          const int *__restrict__ nrun, const int2 *__restrict__ runs, const unsigned *__restrict__ pad,
+                          const unsigned *__restrict__ flag, int2 *__restrict__ runs_pr)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nleaves) return;
+    const int A = leaves[i];
+    for (int k = ptr[A]; k < ptr[A] + nrun[A]; k++) {
+        const int2 r = runs[k];
+        runs_pr[k] = make_int2((int)((r.x + pad[r.x]) >> 1), (int)((r.y + pad[r.y - 1] + flag[r.y - 1]) >> 1));
+    }
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t tx)
+{
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(tx) : "memory");
+}
+
+// pairs [k0, k1) of a chunk against the TPT targets of a thread (every pair whole)
+template <bool CHECK, int TPT>
+__device__ __forceinline__ void p2p_pairs_pk(int k, int k1, const ulonglong2 *pr, const f2 (&tx)[TPT], const f2 (&ty)[TPT],
+                                             const f2 (&tz)[TPT], f2 (&acc)[4 * TPT], int &cnt)
+{
+    cnt += max(0, k1 - k);
+    for (; k + FMM_P2P_STEP <= k1; k += FMM_P2P_STEP) {
+#pragma unroll
+        for (int kk = 0; kk < FMM_P2P_STEP; kk++) {
+            const ulonglong2 A = pr[2 * (k + kk)], B = pr[2 * (k + kk) + 1];
+#pragma unroll
+            for (int t = 0; t < TPT; t++)
+                interact_pk<CHECK>(A.x, A.y, B.x, B.y, tx[t], ty[t], tz[t], acc[4 * t], acc[4 * t + 1], acc[4 * t + 2],
+                                   acc[4 * t + 3]);
+        }
+    }
+    for (; k < k1; k++) {
+        const ulonglong2 A = pr[2 * k], B = pr[2 * k + 1];
+#pragma unroll
+        for (int t = 0; t < TPT; t++)
+            interact_pk<CHECK>(A.x, A.y, B.x, B.y, tx[t], ty[t], tz[t], acc[4 * t], acc[4 * t + 1], acc[4 * t + 2],
+                               acc[4 * t + 3]);
+    }
+}
+
+template <int TPT>
+__global__ void __launch_bounds__(P2P_T, FMM_P2P_MINB)
+    p2p_pr_k(const float4 *__restrict__ xs, const float *__restrict__ pairs, const unsigned *__restrict__ pad,
+             const unsigned *__restrict__ flag, const int *__restrict__ leaves, const int *__restrict__ begin,
+             const int *__restrict__ end, const int *__restrict__ ptr, const int2 *__restrict__ runs_pr,
+             const int *__restrict__ nrun, double4_32a *__restrict__ near, int *__restrict__ err)
+{
+    __shared__ __align__(128) float4 buf[PR_NB][2 * PR_CHP];  // pair records, two float4 each
+    __shared__ float hls[8 * TPT * P2P_T];                      // per-thread TwoSum state, column-major
+    __shared__ int4 info[PR_NB];                                // per chunk: records, own-leaf records [lo, hi)
+    __shared__ uint64_t full[PR_NB], empty[PR_NB];
+    static_assert(sizeof(buf) >= sizeof(float2) * P2P_T * 4 * TPT, "slice sums reuse the chunk buffers");
+    float2 *red2 = reinterpret_cast<float2 *>(&buf[0][0]);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int A = leaves[blockIdx.x];
+    const int tb = begin[A], te = end[A];
+    const int k0 = ptr[A], k1 = ptr[A] + nrun[A];
+    const int op0 = (int)((tb + pad[tb]) >> 1), op1 = (int)((te + pad[te - 1] + flag[te - 1]) >> 1);
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < PR_NB; b++) {
+            mbar_init(&full[b], 1);
+            mbar_init(&empty[b], P2P_T / 32);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    bool bad = false;  // a bounded wait ran out: results of this leaf are void, err is set
+    int cc = 0;        // chunks consumed by this block so far (all passes)
+
+    for (int t0 = tb; t0 < te; t0 += TPT * P2P_T) {
+        const int nt = min(TPT * P2P_T, te - t0);
+        const int R = (nt + TPT - 1) / TPT;
+        const int S = max(1, P2P_T / R);
+        const int row = threadIdx.x % R, sl = threadIdx.x / R;
+        const bool act = sl < S;
+        f2 tx[TPT], ty[TPT], tz[TPT];
+#pragma unroll
+        for (int k = 0; k < TPT; k++) {
+            const int i = (act && row + k * R < nt) ? t0 + row + k * R : t0;
+            const float4 x = xs[i];
+            tx[k] = f2_pack(x.x, x.x);
+            ty[k] = f2_pack(x.y, x.y);
+            tz[k] = f2_pack(x.z, x.z);
+        }
+        f2 pacc[4 * TPT];
+        int pcnt = 0;
+#pragma unroll
+        for (int c = 0; c < 4 * TPT; c++) pacc[c] = 0ull;
+#pragma unroll
+        for (int c = 0; c < 8 * TPT; c++) hls[c * P2P_T + threadIdx.x] = 0.f;
+
+        // producer state (warp 0): run cursor in records, next chunk to make
+        int ck = k0, coff = 0, pnext = cc;
+        bool pdone = false;
+        // warp 0: chunk c into buffer c % PR_NB once its previous chunk is
+        // released; a chunk with no records marks the end of the stream
+        auto produce = [&](int c) {
+            const int b = c % PR_NB;
+            bool ok = true;
+            if (c >= PR_NB) ok = mbar_wait(&empty[b], (uint32_t)(((c - PR_NB) / PR_NB) & 1));
+            if (!__all_sync(0xffffffffu, ok)) {
+                bad = true;
+                if (lane == 0) atomicExch(err, 1);
+            }
+            int fill = 0, slo = 0, shi = 0;
+            while (!bad && ck < k1 && fill < PR_CHP) {
+                const int k = ck + lane;
+                int g0 = 0, len = 0;
+                if (k < k1) {
+                    const int2 rr = runs_pr[k];
+                    g0 = rr.x + (lane == 0 ? coff : 0);
+                    len = rr.y - g0;
+                }
+                int incl = len;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += v;
+                }
+                const int start = fill + incl - len;
+                const int take = max(0, min(len, PR_CHP - start));
+                const int cnt = __popc(__ballot_sync(0xffffffffu, take > 0));
+                if (cnt == 0) break;
+                int a0 = 0, a1 = 0;
+                if (take > 0) {
+                    mbar_expect_tx(&full[b], (uint32_t)take * 32u);
+                    bulk_g2s(smem_u32(&buf[b][2 * start]), pairs + 8 * (size_t)g0, (uint32_t)take * 32u, &full[b]);
+                    a0 = max(g0, op0);
+                    a1 = min(g0 + take, op1);
+                }
+                // the target leaf is one leaf of one run: at most one lane holds it
+                const unsigned own = __ballot_sync(0xffffffffu, a0 < a1);
+                if (own) {
+                    const int src = __ffs(own) - 1;
+                    slo = __shfl_sync(0xffffffffu, start + a0 - g0, src);
+                    shi = __shfl_sync(0xffffffffu, start + a1 - g0, src);
+                }
+                const int lt = __shfl_sync(0xffffffffu, take, cnt - 1), ll = __shfl_sync(0xffffffffu, len, cnt - 1),
+                          ls = __shfl_sync(0xffffffffu, start, cnt - 1);
+                fill = ls + lt;
+                if (lt == ll) {
+                    ck += cnt;
+                    coff = 0;
+                } else {
+                    coff = (cnt == 1 ? coff : 0) + lt;
+                    ck += cnt - 1;
+                }
+            }
+            __syncwarp();
+            if (lane == 0) {
+                info[b] = make_int4(fill, slo, shi, 0);
+                mbar_arrive(&full[b]);
+            }
+            __syncwarp();
+            return fill;
+        };
+        auto produce_upto = [&](int last) {
+            while (!pdone && pnext <= last) {
+                if (produce(pnext) == 0) pdone = true;
+                pnext++;
+            }
+        };
+        if (warp == 0) produce_upto(cc + PR_D);
+
+        for (;;) {
+            if (warp == 0) produce_upto(cc + PR_D);
+            const int b = cc % PR_NB;
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(&full[b], (uint32_t)((cc / PR_NB) & 1)));
+            if (!ok) {
+                if (lane == 0) atomicExch(err, 1);
+                bad = true;
+                break;
+            }
+            const int4 inf = info[b];
+            if (inf.x > 0 && act) {
+                // slice bounds in records; the target leaf's own records (the
+                // nearest, largest terms) are summed and folded on their own
+                const int np = inf.x;
+                const int jlo = (np * sl) / S, jhi = (np * (sl + 1)) / S;
+                const int slo = inf.y, shi = inf.z;
+                const ulonglong2 *pr = reinterpret_cast<const ulonglong2 *>(&buf[b][0]);
+                const bool ownp = max(jlo, slo) < min(jhi, shi);
+                p2p_pairs_pk<false, TPT>(jlo, min(jhi, slo), pr, tx, ty, tz, pacc, pcnt);
+                if (ownp) {
+                    p2p_fold_pk<TPT>(pacc, hls + threadIdx.x);
+                    p2p_pairs_pk<true, TPT>(max(jlo, slo), min(jhi, shi), pr, tx, ty, tz, pacc, pcnt);
+                    p2p_fold_pk<TPT>(pacc, hls + threadIdx.x);
+                    pcnt = 0;
+                }
+                p2p_pairs_pk<false, TPT>(max(jlo, shi), jhi, pr, tx, ty, tz, pacc, pcnt);
+                if (pcnt >= FMM_P2P_FOLD) {
+                    p2p_fold_pk<TPT>(pacc, hls + threadIdx.x);
+                    pcnt = 0;
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[b]);
+            cc++;
+            if (inf.x == 0) break;
+        }
+        // after a timeout, copies that may still be in flight land before the
+        // buffers are reused or released (bounded waits)
+        if (bad && warp == 0 && lane == 0)
+            for (int c = cc; c < pnext; c++) mbar_wait(&full[c % PR_NB], (uint32_t)((c / PR_NB) & 1));
+        __syncthreads();  // every warp is past the last chunk: the buffers take the slice sums
+        if (act) {
+            p2p_fold_pk<TPT>(pacc, hls + threadIdx.x);
+#pragma unroll
+            for (int c = 0; c < 4 * TPT; c++)
+                red2[(sl * R + row) * 4 * TPT + c] =
+                    make_float2(hls[c * P2P_T + threadIdx.x], hls[(4 * TPT + c) * P2P_T + threadIdx.x]);
+        }
+        __syncthreads();
+        if ((int)threadIdx.x < R) {
+            // slices in fixed order, compensated in FP32 (TwoSum of the leading
+            // parts, the trailing parts added), one conversion each
+            float oh[4 * TPT], ol[4 * TPT];
+#pragma unroll
+            for (int c = 0; c < 4 * TPT; c++) oh[c] = ol[c] = 0.f;
+            for (int s2 = 0; s2 < S; s2++)
+#pragma unroll
+                for (int c = 0; c < 4 * TPT; c++) {
+                    const float2 v = red2[(s2 * R + threadIdx.x) * 4 * TPT + c];
+                    acc2(oh[c], ol[c], v.x);
+                    ol[c] += v.y;
+                }
+#pragma unroll
+            for (int kk = 0; kk < TPT; kk++)
+                if ((int)threadIdx.x + kk * R < nt)
+                    near[t0 + threadIdx.x + kk * R] =
+                        make_double4_32a((double)oh[4 * kk] + (double)ol[4 * kk], (double)oh[4 * kk + 1] + (double)ol[4 * kk + 1],
+                                         (double)oh[4 * kk + 2] + (double)ol[4 * kk + 2],
+                                         (double)oh[4 * kk + 3] + (double)ol[4 * kk + 3]);
+        }
+        __syncthreads();  // the slice sums are read before the next pass reuses the buffers
+    }
+}
+
+void p2p_pairs_fill(fmm_ctx *h, cudaStream_t s)
+{
+    if (!h->pr_ready) return;
+    const int64_t n = h->n;
+    pr_fill_k<<<nblk(n, 256), 256, 0, s>>>(n, h->xs32.as<float4>(), h->pr_pad.as<unsigned>(), h->pr_flag.as<unsigned>(),
+                                           h->pr_pairs.as<float>());
+    count_launch(h);
+    check_launch("p2p pairs");
+}
+
+void p2p_prepare(fmm_ctx *h, cudaStream_t s)
+{
+    h->pr_ready = false;
+    if (!(h->precision == FMM_MIXED && h->dtype == FMM_F32) || h->nleaves == 0) return;
+    const int64_t n = h->n;
+    h->pr_flag.ensure(sizeof(unsigned) * (size_t)n);
+    h->pr_pad.ensure(sizeof(unsigned) * (size_t)n);
+    // at most one padding record half per leaf
+    h->pr_pairs.ensure(sizeof(float) * 8 * (size_t)((n + h->nleaves + 1) / 2 + 1));
+    h->p2p_runs_pr.ensure(sizeof(int2) * (size_t)std::max<int64_t>(h->n_p2p, 1));
+    pr_flag_k<<<nblk(n, 256), 256, 0, s>>>(n, h->pcell.as<int>(), h->c_begin.as<int>(), h->c_end.as<int>(),
+                                           h->pr_flag.as<unsigned>());
+    count_launch(h);
+    scan_exclusive_u32(h, h->pr_flag.as<unsigned>(), h->pr_pad.as<unsigned>(), n, nullptr, s);
+    pr_runs_k<<<nblk(h->nleaves, 128), 128, 0, s>>>(h->nleaves, h->leaves.as<int>(), h->p2p_ptr.as<int>(),
+                                                   h->p2p_nrun.as<int>(), h->p2p_runs.as<int2>(), h->pr_pad.as<unsigned>(),
+                                                   h->pr_flag.as<unsigned>(), h->p2p_runs_pr.as<int2>());
+    count_launch(h);
+    check_launch("p2p pair runs");
+    h->pr_ready = true;
+    p2p_pairs_fill(h, s);
+}
+
 void near_field(fmm_ctx *h, cudaStream_t s)
 {
     h->near.ensure(sizeof(double4_32a) * (size_t)h->n);
@@ -656,7 +998,13 @@ void near_field(fmm_ctx *h, cudaStream_t s)
     else if (h->dtype == FMM_F64)
         p2p_k<float, true, FMM_P2P_TPT><<<h->nleaves, P2P_T, 0, s>>>(h->xs32.as<float4>(), h->xs32lo.as<float4>(), lv, cb, ce, pp, ru,
                                                            nr, out);
-    else
+    else if (h->pr_ready) {
+        int *err = reinterpret_cast<int *>(h->m2l_misc.as<unsigned>() + 24 * (FMM_MAXLEVEL + 1) + 5);
+        FMM_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
+        p2p_pr_k<FMM_P2P_TPT><<<h->nleaves, P2P_T, 0, s>>>(h->xs32.as<float4>(), h->pr_pairs.as<float>(),
+                                                          h->pr_pad.as<unsigned>(), h->pr_flag.as<unsigned>(), lv, cb, ce,
+                                                          pp, h->p2p_runs_pr.as<int2>(), nr, out, err);
+    } else
         p2p_k<float, false, FMM_P2P_TPT><<<h->nleaves, P2P_T, 0, s>>>(h->xs32.as<float4>(), nullptr, lv, cb, ce, pp, ru, nr, out);
     count_launch(h);
     check_launch("p2p");

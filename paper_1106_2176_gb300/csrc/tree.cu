@@ -1321,6 +1321,7 @@ void tree_build(fmm_ctx *h, const void *x, const void *q, int64_t n, int dt)
         count_launch(h);
         check_launch("p2p runs");
     }
+    p2p_prepare(h, s);
     {
         unsigned long long *acc = reinterpret_cast<unsigned long long *>(h->counters.as<char>() + sizeof(TravCounters) + 8);
         FMM_CUDA_TRY(cudaMemsetAsync(acc, 0, 8, s));
