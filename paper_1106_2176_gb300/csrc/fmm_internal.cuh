@@ -100,6 +100,26 @@ struct M2LTile {
     int octant;
 };
 
+// One system's share of a persistent tensor-core M2L launch: its tile list
+// and the arrays the tiles read and write. Queue items item0 .. item0 + count
+// - 1 are its tiles (count < 0: *ntiles tiles, read on the device).
+struct M2LJob {
+    const M2LTile *tiles;
+    const int *ntiles;
+    const int *tgt;
+    const int4 *xyz;
+    const uint64_t *anchor;
+    const LevelDesc *ld;
+    const int *map_pool;
+    const int4 *st;
+    const int *st_off;
+    const float *mrow;
+    const unsigned char *ttab;
+    float *L;
+    int item0;
+    int count;
+};
+
 // counters written by the traversal and read back by the host
 struct TravCounters {
     unsigned long long n_p2p, n_m2lx, n_next, n_m2l_implicit;
@@ -252,6 +272,10 @@ void far_field(fmm_ctx *h);       // P2M, M2M, M2L, L2L, L2P into h->far
 void tensor_tables_init(fmm_ctx *h);
 bool tensor_m2l_supported(fmm_ctx *h);
 void m2l_tensor(fmm_ctx *h, float *L, const float *M);
+// the same-level M2L of several systems (same p; mrow already padded to
+// whole k-blocks where p^2 is not a multiple of 32) in one persistent launch
+void m2l_tensor_jobs(int p, int nsm, const M2LJob *jobs_dev, int njobs, int *queue, int *err, cudaStream_t s);
+M2LJob m2l_tensor_job(fmm_ctx *h, float *L, const float *M, cudaStream_t s);  // pads M if needed
 
 // p2p.cu
 void near_field(fmm_ctx *h, cudaStream_t s);  // P2P into h->near

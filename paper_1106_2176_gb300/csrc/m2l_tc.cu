@@ -131,17 +131,18 @@ __global__ void mpad_k(const float *__restrict__ M, int PP, int KP, int c0, int 
     out[(size_t)c * KP + k] = k < PP ? M[(size_t)c * PP + k] : 0.f;
 }
 
-template <int NP, int KB>
+template <int NP, int KB, bool PERSIST>
 __global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
-    m2l_tc_k(int p, const M2LTile *__restrict__ tiles, const int *__restrict__ ntiles, const int *__restrict__ tgt,
-             const int4 *__restrict__ xyz, const uint64_t *__restrict__ anchor, const LevelDesc *__restrict__ ld,
-             const int *__restrict__ map_pool, const int4 *__restrict__ st, const int *__restrict__ st_off,
-             const float *__restrict__ mrow, const unsigned char *__restrict__ ttab, float *__restrict__ L,
-             int *__restrict__ err)
+    m2l_tc_k(int p, const __grid_constant__ M2LJob one, const M2LJob *__restrict__ jobs, int njobs,
+             int *__restrict__ queue, int *__restrict__ err)
 {
+    // PERSIST (many systems: jobs[], njobs entries sorted by item0): each CTA
+    // takes tiles from the queue until it is empty. Otherwise CTA b computes
+    // tile b of the single job `one`, read from the parameter space, which
+    // measured faster for one system than the persistent loop (25.1 vs
+    // 27.7 ms at N = 1e7).
     using C = TcCfg<NP, KB>;
     constexpr int RSG = C::RSG, CS = C::CS, AC = C::AC, NG = C::NG, QU = C::QU, RINGU = C::RINGU, KP = KB * 32;
-    if ((int)blockIdx.x >= *ntiles) return;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     unsigned char *araw = base;                           // NG x RSG x A_RAW
@@ -161,11 +162,73 @@ __global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
     uint64_t *ready = fin + 1;                // VEC, VR: vector w ready (its KB units split, its operator landed)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(ready + C::VR);
     int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
+    int *s_tile = abort_flag + 1;                 // this CTA's current tile (-1: none left)
+    M2LJob *s_job = reinterpret_cast<M2LJob *>(reinterpret_cast<unsigned char *>(bar) + 384);  // its job
+    static_assert(sizeof(uint64_t) * (6 + 6 + 4 + 8 + 2 + 2 + 1 + 8) + 16 <= 384 && 384 + sizeof(M2LJob) <= 512,
+                  "barrier area");
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool worker = warp < C::NW;
     const int row = tid & 127, grp = (tid >> 7) & 1;  // worker: target row and group
-    const M2LTile td = tiles[blockIdx.x];
+    if (warp == C::MMA_WARP) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(C::TCOLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    for (int pass = 0; PERSIST || pass == 0; pass++) {
+    if (tid == 0) {
+        if (PERSIST) {
+            const int it = atomicAdd(queue, 1);
+            int lo = 0, hi = njobs - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (jobs[mid].item0 <= it) lo = mid;
+                else hi = mid - 1;
+            }
+            *s_job = jobs[lo];
+            const int t = it - s_job->item0;
+            *s_tile = (t >= 0 && t < s_job->count) ? t : -1;
+        } else {
+            *s_tile = (int)blockIdx.x < *one.ntiles ? (int)blockIdx.x : -1;
+        }
+        // the tile's barriers start from phase 0 (the previous tile left
+        // every barrier idle: all its waits, copies and commits completed)
+        for (int s = 0; s < NG * RSG; s++) mbar_init(&a_full[s], 128);
+        for (int s = 0; s < NB; s++) mbar_init(&b_full[s], 1);
+        for (int s = 0; s < CS; s++) mbar_init(&cmp_full[s], C::NW / C::NG);
+        for (int s = 0; s < NF; s++) mbar_init(&cmp_free[s], 1);
+        for (int b = 0; b < AC; b++) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], C::NW);
+        }
+        mbar_init(fin, 1);
+        // per vector: one arrival per warp of the groups that split its KB
+        // units, and one from the operator warp once the operator landed
+        for (int s = 0; s < C::VR; s++) mbar_init(&ready[s], 4 * KB + 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const int tile = *s_tile;
+    if (tile < 0) break;
+    const M2LJob &J = PERSIST ? *s_job : one;
+    const M2LTile *__restrict__ tiles = J.tiles;
+    const int *__restrict__ tgt = J.tgt;
+    const int4 *__restrict__ xyz = J.xyz;
+    const uint64_t *__restrict__ anchor = J.anchor;
+    const LevelDesc *__restrict__ ld = J.ld;
+    const int *__restrict__ map_pool = J.map_pool;
+    const int4 *__restrict__ st = J.st;
+    const int *__restrict__ st_off = J.st_off;
+    const float *__restrict__ mrow = J.mrow;
+    const unsigned char *__restrict__ ttab = J.ttab;
+    float *__restrict__ L = J.L;
+    const M2LTile td = tiles[tile];
     const int PP = p * p;
     const int l = td.level;
     // this row's cell, its level, lattice position and octant (a pooled tile
@@ -186,33 +249,6 @@ __global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
     const int e0 = st_off[td.octant], nv = st_off[10 + td.octant * (FMM_MAXLEVEL + 1) + l];
     const int nunits = nv * KB;
     const int ngroups = (nv + C::GV - 1) / C::GV;
-
-    if (tid == 0) {
-        for (int s = 0; s < NG * RSG; s++) mbar_init(&a_full[s], 128);
-        for (int s = 0; s < NB; s++) mbar_init(&b_full[s], 1);
-        for (int s = 0; s < CS; s++) mbar_init(&cmp_full[s], C::NW / C::NG);
-        for (int s = 0; s < NF; s++) mbar_init(&cmp_free[s], 1);
-        for (int b = 0; b < AC; b++) {
-            mbar_init(&acc_full[b], 1);
-            mbar_init(&acc_empty[b], C::NW);
-        }
-        mbar_init(fin, 1);
-        // per vector: one arrival per warp of the groups that split its KB
-        // units, and one from the operator warp once the operator landed
-        for (int s = 0; s < C::VR; s++) mbar_init(&ready[s], 4 * KB + 1);
-        *abort_flag = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp == C::MMA_WARP) {
-        __syncwarp();
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(C::TCOLS));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = *tmem_slot;
 
     if (warp == C::MMA_WARP) {
         // ------------------------------------------------------------ MMA warp
@@ -492,10 +528,17 @@ __global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
     }
     tc_fence_before();
     __syncthreads();
+    tc_fence_after();
+    const bool aborted = *(volatile int *)abort_flag != 0;
+    if (tid == 0 && aborted) atomicExch(err, 1);
+    __syncthreads();  // every thread has read the flag before the next tile resets it
+    if (aborted) break;
+    }  // tiles
+    tc_fence_before();
+    __syncthreads();
     if (warp == C::MMA_WARP) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TCOLS));
     }
-    if (tid == 0 && *(volatile int *)abort_flag) atomicExch(err, 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -673,46 +716,86 @@ void tensor_tables_update(fmm_ctx *h)
 }
 
 template <int NP, int KB>
-static void launch_tc(fmm_ctx *h, float *L, const float *M)
+static void launch_tc(int p, int grid, const M2LJob &one, const M2LJob *jobs, int njobs, int *queue, int *err,
+                      cudaStream_t s)
 {
     using C = TcCfg<NP, KB>;
-    cudaStream_t s = h->work;
+    // grid: one CTA per SM with a job list (persistent), else one per tile
+    if (jobs) {
+        ensure_smem((const void *)m2l_tc_k<NP, KB, true>, C::SMEM);
+        FMM_CUDA_TRY(cudaMemsetAsync(queue, 0, sizeof(int), s));
+        m2l_tc_k<NP, KB, true><<<grid, C::NT, C::SMEM, s>>>(p, one, jobs, njobs, queue, err);
+    } else {
+        ensure_smem((const void *)m2l_tc_k<NP, KB, false>, C::SMEM);
+        m2l_tc_k<NP, KB, false><<<grid, C::NT, C::SMEM, s>>>(p, one, jobs, njobs, queue, err);
+    }
+}
+
+static void launch_tc_p(int p, int nsm, const M2LJob &one, const M2LJob *jobs, int njobs, int *queue, int *err,
+                        cudaStream_t s)
+{
+    switch (tc_shape(p).NP) {
+    case 16: launch_tc<16, 1>(p, nsm, one, jobs, njobs, queue, err, s); break;
+    case 32: launch_tc<32, 1>(p, nsm, one, jobs, njobs, queue, err, s); break;
+    case 48: launch_tc<48, 2>(p, nsm, one, jobs, njobs, queue, err, s); break;
+    case 64: launch_tc<64, 2>(p, nsm, one, jobs, njobs, queue, err, s); break;
+    case 96: launch_tc<96, 3>(p, nsm, one, jobs, njobs, queue, err, s); break;
+    case 112: launch_tc<112, 4>(p, nsm, one, jobs, njobs, queue, err, s); break;
+    case 128: launch_tc<128, 4>(p, nsm, one, jobs, njobs, queue, err, s); break;
+    default: throw Error{FMM_EINVAL, "tensor-core M2L: unsupported p"};
+    }
+}
+
+M2LJob m2l_tensor_job(fmm_ctx *h, float *L, const float *M, cudaStream_t s)
+{
+    tensor_tables_update(h);
+    const TcShape sh = tc_shape(h->p);
     const int c0 = h->depth >= 2 ? h->lvl_start[2] : h->ncells;
-    const int nc = h->ncells, PP = h->p * h->p, KP = KB * 32;
+    const int nc = h->ncells, PP = h->p * h->p, KP = sh.KB * 32;
     const float *mrow = M;
     if (PP != KP) {  // zero-padded rows of KB * 32 coefficients
         h->msplit.ensure(sizeof(float) * (size_t)nc * KP);
-        mpad_k<<<nblk((int64_t)(nc - c0) * KP, 256), 256, 0, s>>>(M, PP, KP, c0, nc, h->msplit.as<float>());
-        count_launch(h);
+        if (nc > c0) {
+            mpad_k<<<nblk((int64_t)(nc - c0) * KP, 256), 256, 0, s>>>(M, PP, KP, c0, nc, h->msplit.as<float>());
+            count_launch(h);
+        }
         mrow = h->msplit.as<float>();
     }
-    ensure_smem((const void *)m2l_tc_k<NP, KB>, C::SMEM);
-    const int *st_off = stencil_offsets(h);
-    const int *ntiles = reinterpret_cast<const int *>(h->m2l_misc.as<unsigned>() + 24 * (FMM_MAXLEVEL + 1));
-    int *err = reinterpret_cast<int *>(h->m2l_misc.as<unsigned>() + 24 * (FMM_MAXLEVEL + 1) + 4);
-    FMM_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
-    m2l_tc_k<NP, KB><<<h->ntiles_max, C::NT, C::SMEM, s>>>(h->p, h->m2l_tiles.as<M2LTile>(), ntiles, h->m2l_tgt.as<int>(),
-                                                          h->c_xyz.as<int4>(), h->c_anchor.as<uint64_t>(),
-                                                          h->lvl_desc.as<LevelDesc>(), h->map_pool.as<int>(),
-                                                          h->st_dev.as<int4>(), st_off, mrow, h->ttab.as<unsigned char>(),
-                                                          L, err);
-    count_launch(h);
-    check_launch("m2l tensor");
+    M2LJob j;
+    j.tiles = h->m2l_tiles.as<M2LTile>();
+    j.ntiles = reinterpret_cast<const int *>(h->m2l_misc.as<unsigned>() + 24 * (FMM_MAXLEVEL + 1));
+    j.tgt = h->m2l_tgt.as<int>();
+    j.xyz = h->c_xyz.as<int4>();
+    j.anchor = h->c_anchor.as<uint64_t>();
+    j.ld = h->lvl_desc.as<LevelDesc>();
+    j.map_pool = h->map_pool.as<int>();
+    j.st = h->st_dev.as<int4>();
+    j.st_off = stencil_offsets(h);
+    j.mrow = mrow;
+    j.ttab = h->ttab.as<unsigned char>();
+    j.L = L;
+    j.item0 = 0;
+    j.count = -1;
+    return j;
+}
+
+void m2l_tensor_jobs(int p, int nsm, const M2LJob *jobs_dev, int njobs, int *queue, int *err, cudaStream_t s)
+{
+    M2LJob none;
+    std::memset(&none, 0, sizeof(none));
+    launch_tc_p(p, nsm, none, jobs_dev, njobs, queue, err, s);
 }
 
 void m2l_tensor(fmm_ctx *h, float *L, const float *M)
 {
-    tensor_tables_update(h);
-    switch (tc_shape(h->p).NP) {
-    case 16: launch_tc<16, 1>(h, L, M); break;
-    case 32: launch_tc<32, 1>(h, L, M); break;
-    case 48: launch_tc<48, 2>(h, L, M); break;
-    case 64: launch_tc<64, 2>(h, L, M); break;
-    case 96: launch_tc<96, 3>(h, L, M); break;
-    case 112: launch_tc<112, 4>(h, L, M); break;
-    case 128: launch_tc<128, 4>(h, L, M); break;
-    default: throw Error{FMM_EINVAL, "tensor-core M2L: unsupported p"};
-    }
+    cudaStream_t s = h->work;
+    const M2LJob j = m2l_tensor_job(h, L, M, s);
+    int *misc = reinterpret_cast<int *>(h->m2l_misc.as<unsigned>() + 24 * (FMM_MAXLEVEL + 1));
+    int *err = misc + 4, *queue = misc + 6;
+    FMM_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
+    launch_tc_p(h->p, h->ntiles_max, j, nullptr, 1, queue, err, s);
+    count_launch(h);
+    check_launch("m2l tensor");
 }
 
 }  // namespace fmm
