@@ -47,6 +47,7 @@ extern "C" {
 #endif
 
 typedef struct fmm_ctx *fmm_handle;
+typedef struct fmm_batch_s *fmm_batch;
 
 /* status codes */
 enum {
@@ -283,6 +284,43 @@ FMM_API int fmm_direct(fmm_handle h, const double *x, const double *q, int64_t n
 FMM_API int fmm_m2l_rotation_host(int p, const double *u, const double *M, double *L);
 
 FMM_API int fmm_destroy(fmm_handle h);
+
+/*
+ * Batched evaluation of many independent systems (the paper's GPU task queue,
+ * Sec. 5: work handed to the GPU in large contiguous pieces). Each system has
+ * its own handle, built with fmm_build (mixed precision, FP32 device inputs,
+ * all with the same p in [2, 10] on one device). fmm_batch_create fixes the
+ * systems and their outputs: phi[i] (n_i floats) and grad[i] (n_i x 3 floats),
+ * device memory, caller's order. The handles must outlive the batch and must
+ * not be rebuilt while it exists. Returns FMM_EINVAL (mismatched handles, p,
+ * precision or NULL arguments), FMM_ESTATE (a handle not built), FMM_ECUDA.
+ *
+ * fmm_batch_evaluate evaluates every system with a fixed number of launches
+ * (about eight, whatever the number of systems), asynchronously on `stream`
+ * (NULL: legacy default), which may be captured into a CUDA graph. Work items
+ * (system, phase, cell or tile) come from device queues: the upward and
+ * downward passes are persistent kernels whose items wait, bounded by about a
+ * second, for the level they depend on; the M2L and P2P kernels draw (system,
+ * tile) and (system, leaf) items. Each system's phi and grad are bitwise those
+ * of fmm_evaluate on its handle.
+ *
+ * fmm_batch_status synchronises the device and reports in *async_error the
+ * device-side waits of the last evaluation that gave up (bit 0: a dependency
+ * wait of the upward or downward pass, bit 1: tensor-core M2L, bit 2: P2P;
+ * the outputs of that evaluation are then void) and, if kernel_launches is
+ * not NULL, the kernels one evaluation launches.
+ *
+ * For failure-detection tests: fmm_batch_items reads work item `item` of pass
+ * 0 (upward) or 1 (downward) (its system, kind 0 P2M / 1 M2M / 2 L2L / 3 L2P,
+ * cell and level); fmm_batch_withhold removes it from the queue, so that the
+ * items that depend on it time out and report bit 0.
+ */
+FMM_API int fmm_batch_create(const fmm_handle *handles, int nsys, void *const *phi, void *const *grad, fmm_batch *out);
+FMM_API int fmm_batch_evaluate(fmm_batch b, void *stream);
+FMM_API int fmm_batch_status(fmm_batch b, int *async_error, int64_t *kernel_launches);
+FMM_API int fmm_batch_items(fmm_batch b, int pass, int64_t item, int *system, int *kind, int *cell, int *level);
+FMM_API int fmm_batch_withhold(fmm_batch b, int pass, int64_t item);
+FMM_API int fmm_batch_destroy(fmm_batch b);
 
 /*
  * Allocation-free Morton keys and stable sort (the paper has no counterpart:

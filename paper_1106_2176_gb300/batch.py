@@ -1,18 +1,27 @@
-"""Many independent FMM systems evaluated as one CUDA graph.
+"""Many independent FMM systems evaluated together.
 
-Each system keeps its own handle (tree, lists, expansions). After a warm-up
-evaluation nothing in fmm_evaluate allocates or synchronises, so the
-evaluations of all systems are captured once into a CUDA graph and replayed
-with one launch. The systems are spread over a few streams (largest first,
-each to the stream with the fewest particles so far), so that small systems,
-which cannot fill the GPU alone, run side by side. One launch sequence per
-system, in turn, is the baseline (evaluate_each).
+Each system keeps its own handle (tree, lists, expansions), built once. Two
+ways to evaluate the whole batch:
+
+- mode "persistent" (default): the library's batch engine (fmm_batch_* in
+  include/fmm.h). One evaluation is about eight launches whatever the number of
+  systems; persistent kernels draw (system, phase, cell or tile) work items from
+  device queues, and the upward and downward passes wait, bounded, on
+  per-system level counters. The evaluation can be captured into a CUDA graph
+  (capture / replay), so the whole batch is one graph launch.
+- mode "graph": every system's own fmm_evaluate captured into one CUDA graph
+  over a few streams (largest system first, each to the stream with the fewest
+  particles so far): thousands of kernels per replay.
+
+One launch sequence per system, in turn, is the baseline (evaluate_each).
+Every mode gives each system bitwise the result of its own fmm_evaluate.
 """
+import ctypes
 import math
 
 import torch
 
-from .fmm import FMM
+from .fmm import FMM, _check, _stream_ptr, _vp, lib
 
 NCRIT_CANDIDATES = (32, 64, 128, 256)
 
@@ -84,9 +93,13 @@ def tune_buckets(systems, p, theta, precision, candidates=NCRIT_CANDIDATES, nstr
 
 
 class FMMBatch:
-    def __init__(self, systems, p=6, theta=0.5, ncrit=64, precision="mixed", streams=8):
+    def __init__(self, systems, p=6, theta=0.5, ncrit=64, precision="mixed", streams=8, mode="persistent"):
         """systems: list of (x (n, 3), q (n,)) CUDA tensors of one dtype.
-        ncrit: a leaf size for every system, or "auto" for one per size bucket."""
+        ncrit: a leaf size for every system, or "auto" for one per size bucket.
+        mode: "persistent" (the batch engine) or "graph" (per-system launches in one graph)."""
+        if mode not in ("persistent", "graph"):
+            raise ValueError("mode must be 'persistent' or 'graph'")
+        self.mode = mode
         self.handles, self.out = [], []
         if ncrit == "auto":
             self.ncrit_by_bucket, bucket = tune_buckets(systems, p, theta, precision, nstreams=max(1, int(streams)))
@@ -102,8 +115,24 @@ class FMMBatch:
         torch.cuda.synchronize()
         self.nstreams = max(1, int(streams))
         self.lane = assign_streams([x.shape[0] for x, _ in systems], self.nstreams)
-        self.graph = None
+        self.graph = self.graph_streams = None
         self.particles = sum(int(x.shape[0]) for x, _ in systems)
+        self._b = _vp()
+        if mode == "persistent":
+            self.reattach()
+
+    def reattach(self):
+        """(Re)creates the batch engine over the built handles: fresh work
+        lists, queues and counters (after a failed evaluation, for instance)."""
+        self.graph = None
+        if self._b.value:
+            lib().fmm_batch_destroy(self._b)
+            self._b = _vp()
+        n = len(self.handles)
+        hs = (_vp * n)(*[f._h for f in self.handles])
+        ph = (_vp * n)(*[p_.data_ptr() for p_, _ in self.out])
+        gr = (_vp * n)(*[g_.data_ptr() for _, g_ in self.out])
+        _check(lib().fmm_batch_create(hs, n, ph, gr, ctypes.byref(self._b)))
 
     def evaluate_each(self):
         """One launch sequence per system, in turn on the current stream."""
@@ -111,30 +140,77 @@ class FMMBatch:
             f.evaluate(phi, grad)
         return self.out
 
-    def capture(self):
-        streams = [torch.cuda.Stream() for _ in range(self.nstreams)]
+    def evaluate(self):
+        """Every system, on the current stream: the batch engine, or in
+        "graph" mode the per-system launches over the streams."""
+        if self.mode == "persistent":
+            _check(lib().fmm_batch_evaluate(self._b, _stream_ptr()))
+            return self.out
+        return self.evaluate_streams()
+
+    def evaluate_streams(self):
+        """Every system's own launch sequence, spread over the streams."""
+        cur = torch.cuda.current_stream()
+        streams = getattr(self, "_streams", None) or [torch.cuda.Stream() for _ in range(self.nstreams)]
+        self._streams = streams
+        for s in streams:
+            s.wait_stream(cur)
+        for i, (f, (phi, grad)) in enumerate(zip(self.handles, self.out)):
+            with torch.cuda.stream(streams[self.lane[i]]):
+                f.evaluate(phi, grad)
+        for s in streams:
+            cur.wait_stream(s)
+        return self.out
+
+    def _capture(self, fn):
+        self._streams = [torch.cuda.Stream() for _ in range(self.nstreams)]
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g):
-            cap = torch.cuda.current_stream()
-            for s in streams:
-                s.wait_stream(cap)
-            for i, (f, (phi, grad)) in enumerate(zip(self.handles, self.out)):
-                with torch.cuda.stream(streams[self.lane[i]]):
-                    f.evaluate(phi, grad)
-            for s in streams:
-                cap.wait_stream(s)
-        self.graph = g
-        self._streams = streams
+            fn()
+        return g
+
+    def capture(self):
+        self.graph = self._capture(self.evaluate)
 
     def replay(self):
-        """Every system's evaluation, one graph launch; results in self.out."""
+        """evaluate() as one graph launch; results in self.out."""
         if self.graph is None:
             self.capture()
         self.graph.replay()
         return self.out
 
+    def replay_streams(self):
+        """evaluate_streams() as one graph launch (thousands of kernels)."""
+        if getattr(self, "graph_streams", None) is None:
+            self.graph_streams = self._capture(self.evaluate_streams)
+        self.graph_streams.replay()
+        return self.out
+
+    def status(self):
+        """(async_error, kernels per evaluation) of the batch engine: bit 0 a
+        dependency wait of the upward or downward pass gave up, bit 1 the
+        tensor-core M2L, bit 2 the P2P (synchronises)."""
+        e, k = ctypes.c_int(), ctypes.c_int64()
+        _check(lib().fmm_batch_status(self._b, ctypes.byref(e), ctypes.byref(k)))
+        return e.value, k.value
+
+    def item(self, pass_, index):
+        """Work item `index` of pass 0 (upward) or 1 (downward): (system, kind, cell, level);
+        kind 0 P2M, 1 M2M, 2 L2L, 3 L2P."""
+        v = [ctypes.c_int() for _ in range(4)]
+        _check(lib().fmm_batch_items(self._b, int(pass_), int(index), *[ctypes.byref(x) for x in v]))
+        return tuple(x.value for x in v)
+
+    def withhold(self, pass_, index):
+        """Failure-detection tests: drop one work item from the queue of pass
+        0 (upward) or 1 (downward); the items that depend on it time out."""
+        _check(lib().fmm_batch_withhold(self._b, int(pass_), int(index)))
+
     def close(self):
-        self.graph = None
+        self.graph = self.graph_streams = None
+        if getattr(self, "_b", None) and self._b.value:
+            lib().fmm_batch_destroy(self._b)
+            self._b = _vp()
         for f in self.handles:
             f.close()
         self.handles = []

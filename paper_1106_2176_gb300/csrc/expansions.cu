@@ -226,17 +226,13 @@ __device__ __forceinline__ void p2m_accum(T x, T y, T z, T q, T *are, T *aim)
 constexpr int P2M_WARPS = 8;
 constexpr int P2M_WARP_MAXP = 10;
 
+// P2M of leaf c by one warp (lane = threadIdx.x & 31)
 template <int P, class P4>
-__global__ void __launch_bounds__(32 * P2M_WARPS) p2m_warp_k(int nleaves, const int *__restrict__ leaves,
-                                                             const int *__restrict__ begin, const int *__restrict__ end,
-                                                             const int4 *__restrict__ xyz, const Box *__restrict__ box,
-                                                             const P4 *__restrict__ xs, float *__restrict__ M)
+__device__ __forceinline__ void p2m_leaf_warp(int c, int lane, const int *__restrict__ begin, const int *__restrict__ end,
+                                              const int4 *__restrict__ xyz, const Box *__restrict__ box,
+                                              const P4 *__restrict__ xs, float *__restrict__ M)
 {
     constexpr int NT = P * (P + 1) / 2;
-    const int lane = threadIdx.x & 31;
-    const int li = blockIdx.x * P2M_WARPS + (threadIdx.x >> 5);
-    if (li >= nleaves) return;
-    const int c = leaves[li];
     double cen[3], w;
     cell_geom(box, xyz[c], cen, w);
     const double iw = 1.0 / w;
@@ -267,6 +263,17 @@ __global__ void __launch_bounds__(32 * P2M_WARPS) p2m_warp_k(int nleaves, const 
                 if (m) Mc[im_idx(n, m)] = aim[k];
             }
         }
+}
+
+template <int P, class P4>
+__global__ void __launch_bounds__(32 * P2M_WARPS) p2m_warp_k(int nleaves, const int *__restrict__ leaves,
+                                                             const int *__restrict__ begin, const int *__restrict__ end,
+                                                             const int4 *__restrict__ xyz, const Box *__restrict__ box,
+                                                             const P4 *__restrict__ xs, float *__restrict__ M)
+{
+    const int li = blockIdx.x * P2M_WARPS + (threadIdx.x >> 5);
+    if (li >= nleaves) return;
+    p2m_leaf_warp<P, P4>(leaves[li], threadIdx.x & 31, begin, end, xyz, box, xs, M);
 }
 
 template <class P4>
@@ -413,19 +420,15 @@ __global__ void __launch_bounds__(32 * MV_WARPS) m2m_mv_k(int PP, int ls, int le
     }
 }
 
+// L2L into child c by one warp, sx: PP floats of the warp's shared memory
 template <int NR>
-__global__ void __launch_bounds__(32 * MV_WARPS) l2l_mv_k(int PP, int ls, int le, const int *__restrict__ parent,
-                                                         const int4 *__restrict__ xyz, const float *__restrict__ mat,
-                                                         float *__restrict__ L)
+__device__ __forceinline__ void l2l_child_warp(int c, int lane, int PP, const int *__restrict__ parent,
+                                               const int4 *__restrict__ xyz, const float *__restrict__ mat,
+                                               float *__restrict__ L, float *sx)
 {
-    extern __shared__ float sm_mv[];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int c = ls + blockIdx.x * MV_WARPS + w;
-    if (c >= le) return;
-    float *sx = sm_mv + w * PP;
     const float *T = mat + (size_t)child_octant(xyz[c]) * PP * PP;
     const float *Lp = L + (size_t)parent[c] * PP;
-    for (int j = lane; j < PP; j += 32) sx[j] = Lp[j];
+    for (int j = lane; j < PP; j += 32) sx[j] = __ldcg(Lp + j);
     __syncwarp();
     float acc[NR];
 #pragma unroll
@@ -443,7 +446,62 @@ __global__ void __launch_bounds__(32 * MV_WARPS) l2l_mv_k(int PP, int ls, int le
 #pragma unroll
     for (int r = 0; r < NR; r++) {
         const int i = lane + 32 * r;
-        if (i < PP) Lc[i] += acc[r];
+        if (i < PP) Lc[i] = __ldcg(Lc + i) + acc[r];
+    }
+}
+
+template <int NR>
+__global__ void __launch_bounds__(32 * MV_WARPS) l2l_mv_k(int PP, int ls, int le, const int *__restrict__ parent,
+                                                         const int4 *__restrict__ xyz, const float *__restrict__ mat,
+                                                         float *__restrict__ L)
+{
+    extern __shared__ float sm_mv[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int c = ls + blockIdx.x * MV_WARPS + w;
+    if (c >= le) return;
+    l2l_child_warp<NR>(c, lane, PP, parent, xyz, mat, L, sm_mv + w * PP);
+}
+
+// M2M of parent c by one warp, with the arithmetic of m2m_mv_k (each child's
+// map in the same order, the children's partial results added in child
+// order); sx: PP floats of the warp's shared memory
+template <int NR>
+__device__ __forceinline__ void m2m_parent_warp(int c, int lane, int PP, const int *__restrict__ child,
+                                                const int *__restrict__ nchild, const int4 *__restrict__ xyz,
+                                                const float *__restrict__ mat, float *__restrict__ M, float *sx)
+{
+    const int nc = nchild[c];
+    if (nc == 0) return;
+    float sum[NR];
+#pragma unroll
+    for (int r = 0; r < NR; r++) sum[r] = 0.f;
+    for (int k = 0; k < nc; k++) {
+        const int ch = child[c] + k;
+        const float *T = mat + (size_t)child_octant(xyz[ch]) * PP * PP;
+        const float *Mc = M + (size_t)ch * PP;
+        __syncwarp();
+        for (int j = lane; j < PP; j += 32) sx[j] = __ldcg(Mc + j);
+        __syncwarp();
+        float acc[NR];
+#pragma unroll
+        for (int r = 0; r < NR; r++) acc[r] = 0.f;
+        for (int j = 0; j < PP; j++) {
+            const float xj = sx[j];
+            const float *col = T + (size_t)j * PP;
+#pragma unroll
+            for (int r = 0; r < NR; r++) {
+                const int i = lane + 32 * r;
+                if (i < PP) acc[r] = fmaf(col[i], xj, acc[r]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < NR; r++) sum[r] += acc[r];
+    }
+    float *Mp = M + (size_t)c * PP;
+#pragma unroll
+    for (int r = 0; r < NR; r++) {
+        const int i = lane + 32 * r;
+        if (i < PP) Mp[i] = sum[r];
     }
 }
 
@@ -795,16 +853,14 @@ constexpr size_t m2lx_f_smem()
            sizeof(double) * 2 * M2LX_FW * (size_t)(P * (P + 1));
 }
 
+// different-level M2L into target cell c by one CTA of 32 M2LX_FW threads
 template <int P>
-__global__ void __launch_bounds__(32 * M2LX_FW, 3) m2lx_f_k(int nc, const int *__restrict__ ptr,
-                                                            const int *__restrict__ src, const int4 *__restrict__ xyz,
-                                                            const float *__restrict__ M, float *__restrict__ L)
+__device__ __forceinline__ void m2lx_f_cell(int c, const int *__restrict__ ptr, const int *__restrict__ src,
+                                            const int4 *__restrict__ xyz, const float *__restrict__ M,
+                                            float *__restrict__ L, unsigned char *smem_raw)
 {
     constexpr int PP = P * P, Q = 2 * P - 1, NT = P * (P + 1) / 2, NO = (NT + 15) / 16, NM = (PP + 15) / 16;
     constexpr int NH = 2 * M2LX_FW;  // half-warps
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int c = blockIdx.x;
-    if (c >= nc) return;
     const int k0 = ptr[c], npair = ptr[c + 1] - k0;
     if (npair == 0) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15;
@@ -951,6 +1007,16 @@ __global__ void __launch_bounds__(32 * M2LX_FW, 3) m2lx_f_k(int nc, const int *_
 }
 
 template <int P>
+__global__ void __launch_bounds__(32 * M2LX_FW, 3) m2lx_f_k(int nc, const int *__restrict__ ptr,
+                                                            const int *__restrict__ src, const int4 *__restrict__ xyz,
+                                                            const float *__restrict__ M, float *__restrict__ L)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if ((int)blockIdx.x >= nc) return;
+    m2lx_f_cell<P>((int)blockIdx.x, ptr, src, xyz, M, L, smem_raw);
+}
+
+template <int P>
 static void m2lx_f_run(int nc, const int *ptr, const int *src, const int4 *xyz, const float *M, float *L, cudaStream_t s)
 {
     constexpr size_t smem = m2lx_f_smem<P>();
@@ -1065,14 +1131,14 @@ __global__ void cgeo_k(int nc, const int4 *__restrict__ xyz, const Box *__restri
 // a leaf are consecutive, so a warp reads one or two expansions). The same
 // sums as l2p_k: phi = Re sum L_n^m conj(R_n^m), d/dz from L_{n+1}^m and
 // (d_x - i d_y) from L_{n+1}^{m-1} and L_{n+1}^{m+1} (Sec. 2.1, L2P).
-template <int P, class P4>
-__global__ void __launch_bounds__(256) l2p_flat_k(int64_t n, const int *__restrict__ pcell,
-                                                  const double4_32a *__restrict__ cgeo, const P4 *__restrict__ xs,
-                                                  const float *__restrict__ L, double4_32a *__restrict__ far)
+// L2P of sorted particle j (its leaf c). COHERENT: the local expansion may
+// have been written in the same launch by another SM, so it is read through
+// L2 (ld.cg) rather than the non-coherent read-only path.
+template <int P, class P4, bool COHERENT = false>
+__device__ __forceinline__ void l2p_particle(int64_t j, int c, const double4_32a *__restrict__ cgeo,
+                                             const P4 *__restrict__ xs, const float *__restrict__ L,
+                                             double4_32a *__restrict__ far)
 {
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    const int c = pcell[j];
     const double4_32a g = cgeo[c];
     const double cen[3] = {g.x, g.y, g.z};
     const double iw = g.w;
@@ -1080,7 +1146,7 @@ __global__ void __launch_bounds__(256) l2p_flat_k(int64_t n, const int *__restri
     const float x = (float)(pt.x * iw), y = (float)(pt.y * iw), z = (float)(pt.z * iw);
     const float r2 = x * x + y * y + z * z;
     const float *Lc = L + (size_t)c * (P * P);
-    auto ld = [&](int k) { return __ldg(Lc + k); };
+    auto ld = [&](int k) { return COHERENT ? __ldcg(Lc + k) : __ldg(Lc + k); };
     float F = 0.f, Fz = 0.f, Gr = 0.f, Gi = 0.f;
     float mre = 1.f, mim = 0.f;
 #pragma unroll
@@ -1133,6 +1199,16 @@ __global__ void __launch_bounds__(256) l2p_flat_k(int64_t n, const int *__restri
     }
     const double iw2 = iw * iw;
     far[j] = make_double4_32a((double)F * iw, (double)Gr * iw2, -(double)Gi * iw2, (double)Fz * iw2);
+}
+
+template <int P, class P4>
+__global__ void __launch_bounds__(256) l2p_flat_k(int64_t n, const int *__restrict__ pcell,
+                                                  const double4_32a *__restrict__ cgeo, const P4 *__restrict__ xs,
+                                                  const float *__restrict__ L, double4_32a *__restrict__ far)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    l2p_particle<P, P4>(j, pcell[j], cgeo, xs, L, far);
 }
 
 template <class P4>
@@ -1510,6 +1586,169 @@ static void far_field_t(fmm_ctx *h, const P4 *xs, const T *rtab)
     count_launch(h);
     check_launch("l2p");
     FMM_CUDA_TRY(cudaEventRecord(ev[7], s));
+}
+
+
+// ---------------------------------------------------------------------------
+// Batched evaluation of many systems: the upward and downward passes as
+// persistent kernels over a queue of per-warp work items (system, kind, cell,
+// level), with per-system, per-level counters of finished cells. The items
+// are queued in dependency order (P2M, then M2M from the deepest level up;
+// L2L from the top level down, then L2P), so a warp waiting on a level only
+// waits for items already taken by running warps. The arithmetic of every
+// item is that of the single-system kernels.
+// ---------------------------------------------------------------------------
+constexpr long long BATCH_WAIT_CYCLES = 2000000000LL;  // about a second at 2 GHz
+
+// wait until *cnt >= target (acquire); false, with bit 0 of *err set, once the
+// wait has run for BATCH_WAIT_CYCLES or another wait of the launch gave up
+__device__ bool batch_dep_wait(const unsigned *cnt, unsigned target, int *err)
+{
+    const long long t0 = clock64();
+    for (;;) {
+        unsigned v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(cnt) : "memory");
+        if (v >= target) return true;
+        if (*(volatile int *)err) return false;
+        if (clock64() - t0 > BATCH_WAIT_CYCLES) {
+            atomicOr(err, 1);
+            return false;
+        }
+        __nanosleep(128);
+    }
+}
+
+__device__ __forceinline__ void batch_done(unsigned *cnt)
+{
+    __threadfence();
+    atomicAdd(cnt, 1u);
+}
+
+template <int P, int NR>
+__global__ void __launch_bounds__(32 * MV_WARPS) batch_up_k(const BatchSys *__restrict__ sys, const int4 *__restrict__ items,
+                                                           int nitems, int *__restrict__ queue,
+                                                           const float *__restrict__ mat, int *__restrict__ err)
+{
+    __shared__ float sx[MV_WARPS][P * P];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (;;) {
+        int it = 0;
+        if (lane == 0) it = atomicAdd(queue, 1);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= nitems) break;
+        const int4 item = items[it];
+        const BatchSys &S = sys[item.x];
+        if (item.y == BATCH_P2M) {
+            p2m_leaf_warp<P, float4>(item.z, lane, S.begin, S.end, S.xyz, S.box, S.xs, S.M);
+        } else {
+            // the children, one level down, are all final
+            bool ok = true;
+            if (lane == 0)
+                ok = batch_dep_wait(S.cnt_up + item.w + 1, (unsigned)(S.lvl_start[item.w + 2] - S.lvl_start[item.w + 1]), err);
+            if (!__shfl_sync(0xffffffffu, ok, 0)) continue;
+            m2m_parent_warp<NR>(item.z, lane, P * P, S.child, S.nchild, S.xyz, mat, S.M, sx[w]);
+        }
+        __syncwarp();
+        if (lane == 0) batch_done(S.cnt_up + item.w);
+    }
+}
+
+template <int P, int NR>
+__global__ void __launch_bounds__(32 * MV_WARPS) batch_down_k(const BatchSys *__restrict__ sys,
+                                                             const int4 *__restrict__ items, int nitems,
+                                                             int *__restrict__ queue, const float *__restrict__ mat,
+                                                             int *__restrict__ err)
+{
+    __shared__ float sx[MV_WARPS][P * P];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (;;) {
+        int it = 0;
+        if (lane == 0) it = atomicAdd(queue, 1);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= nitems) break;
+        const int4 item = items[it];
+        const BatchSys &S = sys[item.x];
+        // L2L waits for the parents' level; L2P for its leaf's level
+        const int lw = item.y == BATCH_L2L ? item.w - 1 : item.w;
+        bool ok = true;
+        if (lane == 0) ok = batch_dep_wait(S.cnt_dn + lw, (unsigned)(S.lvl_start[lw + 1] - S.lvl_start[lw]), err);
+        if (!__shfl_sync(0xffffffffu, ok, 0)) continue;
+        if (item.y == BATCH_L2L) {
+            l2l_child_warp<NR>(item.z, lane, P * P, S.parent, S.xyz, mat, S.L, sx[w]);
+            __syncwarp();
+            if (lane == 0) batch_done(S.cnt_dn + item.w);
+        } else {
+            for (int j = S.begin[item.z] + lane; j < S.end[item.z]; j += 32)
+                l2p_particle<P, float4, true>(j, item.z, S.cgeo, S.xs, S.L, S.far);
+        }
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(32 * M2LX_FW, 3) batch_m2lx_k(const BatchSys *__restrict__ sys,
+                                                               const int2 *__restrict__ items, int nitems)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if ((int)blockIdx.x >= nitems) return;
+    const int2 item = items[blockIdx.x];
+    const BatchSys &S = sys[item.x];
+    m2lx_f_cell<P>(item.y, S.m2lx_ptr, S.m2lx_src, S.xyz, S.M, S.L, smem_raw);
+}
+
+void batch_up(int p, int nsm, const BatchSys *sys, const int4 *items, int nitems, int *queue, const float *m2m_mat,
+              int *err, cudaStream_t s)
+{
+    FMM_CUDA_TRY(cudaMemsetAsync(queue, 0, sizeof(int), s));
+    const unsigned g = (unsigned)nsm * 6;
+    switch (p) {
+#define FMM_BUP(PV) \
+    case PV: batch_up_k<PV, (PV * PV + 31) / 32><<<g, 32 * MV_WARPS, 0, s>>>(sys, items, nitems, queue, m2m_mat, err); break;
+        FMM_BUP(2) FMM_BUP(3) FMM_BUP(4) FMM_BUP(5) FMM_BUP(6) FMM_BUP(7) FMM_BUP(8) FMM_BUP(9) FMM_BUP(10)
+#undef FMM_BUP
+    default: throw Error{FMM_EINVAL, "batch: p must be in [2, 10]"};
+    }
+    check_launch("batch up");
+}
+
+void batch_down(int p, int nsm, const BatchSys *sys, const int4 *items, int nitems, int *queue, const float *l2l_mat,
+                int *err, cudaStream_t s)
+{
+    FMM_CUDA_TRY(cudaMemsetAsync(queue, 0, sizeof(int), s));
+    const unsigned g = (unsigned)nsm * 6;
+    switch (p) {
+#define FMM_BDN(PV) \
+    case PV: batch_down_k<PV, (PV * PV + 31) / 32><<<g, 32 * MV_WARPS, 0, s>>>(sys, items, nitems, queue, l2l_mat, err); break;
+        FMM_BDN(2) FMM_BDN(3) FMM_BDN(4) FMM_BDN(5) FMM_BDN(6) FMM_BDN(7) FMM_BDN(8) FMM_BDN(9) FMM_BDN(10)
+#undef FMM_BDN
+    default: throw Error{FMM_EINVAL, "batch: p must be in [2, 10]"};
+    }
+    check_launch("batch down");
+}
+
+void batch_m2lx(int p, const BatchSys *sys, const int2 *items, int nitems, cudaStream_t s)
+{
+    if (nitems == 0) return;
+    switch (p) {
+#define FMM_BMX(PV)                                                                                       \
+    case PV: {                                                                                            \
+        constexpr size_t smem = m2lx_f_smem<PV>();                                                        \
+        ensure_smem((const void *)batch_m2lx_k<PV>, smem);                                                \
+        batch_m2lx_k<PV><<<nitems, 32 * M2LX_FW, smem, s>>>(sys, items, nitems);                          \
+        break;                                                                                            \
+    }
+        FMM_BMX(2) FMM_BMX(3) FMM_BMX(4) FMM_BMX(5) FMM_BMX(6) FMM_BMX(7) FMM_BMX(8) FMM_BMX(9) FMM_BMX(10)
+#undef FMM_BMX
+    default: throw Error{FMM_EINVAL, "batch: p must be in [2, 10]"};
+    }
+    check_launch("batch m2l irregular");
+}
+
+void cell_geometry(fmm_ctx *h, cudaStream_t s)
+{
+    h->cgeo.ensure(sizeof(double4_32a) * (size_t)std::max(h->ncells, 1));
+    cgeo_k<<<nblk(h->ncells, 256), 256, 0, s>>>(h->ncells, h->c_xyz.as<int4>(), h->box.as<Box>(), h->cgeo.as<double4_32a>());
+    count_launch(h);
+    check_launch("cell geometry");
 }
 
 void far_field(fmm_ctx *h)

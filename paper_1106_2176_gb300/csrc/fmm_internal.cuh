@@ -120,6 +120,32 @@ struct M2LJob {
     int count;
 };
 
+// One system of a batched evaluation (mixed precision, FP32 inputs): the
+// arrays of its handle that the batch kernels read and write, its output
+// buffers and its dependency counters.
+struct BatchSys {
+    const int *leaves, *begin, *end, *child, *nchild, *parent, *pcell, *inv;
+    const int4 *xyz;
+    const Box *box;
+    const double4_32a *cgeo;
+    const float4 *xs;
+    float *M, *L;
+    double4_32a *far, *near;
+    const int *m2lx_ptr, *m2lx_src;
+    const float *pairs;
+    const unsigned *pad, *flag;
+    const int *p2p_ptr, *nrun;
+    const int2 *runs_pr;
+    float *phi, *grad;              // caller's order
+    unsigned *cnt_up, *cnt_dn;      // per level: cells whose M (up) / L (down) is final
+    float *mpad;                    // M rows zero-padded to whole k-blocks (tensor-core M2L), or null
+    int n, ncells, nleaves, depth, c0;  // c0: first cell of level 2
+    int lvl_start[FMM_MAXLEVEL + 2];
+};
+
+// work items of the batch kernels: system, kind, cell, level
+enum { BATCH_P2M = 0, BATCH_M2M = 1, BATCH_L2L = 2, BATCH_L2P = 3 };
+
 // counters written by the traversal and read back by the host
 struct TravCounters {
     unsigned long long n_p2p, n_m2lx, n_next, n_m2l_implicit;
@@ -268,6 +294,19 @@ void stencil_levels(fmm_ctx *h, cudaStream_t s);
 const int *stencil_offsets(fmm_ctx *h);
 void far_field(fmm_ctx *h);       // P2M, M2M, M2L, L2L, L2P into h->far
 
+// batched evaluation (expansions.cu, p2p.cu): persistent kernels over work
+// items of many systems; every dependency wait is bounded and reports a
+// timeout in *err (bit 0) instead of hanging
+void batch_up(int p, int nsm, const BatchSys *sys, const int4 *items, int nitems, int *queue, const float *m2m_mat,
+              int *err, cudaStream_t s);
+void batch_down(int p, int nsm, const BatchSys *sys, const int4 *items, int nitems, int *queue, const float *l2l_mat,
+                int *err, cudaStream_t s);
+void batch_m2lx(int p, const BatchSys *sys, const int2 *items, int nitems, cudaStream_t s);
+void batch_p2p(int nsm, const BatchSys *sys, const int2 *items, int nitems, int *queue, int *err, cudaStream_t s);
+void batch_zero(int p, const BatchSys *sys, int nsys, cudaStream_t s);
+void batch_combine(const BatchSys *sys, int nsys, const int *blk0, int nblocks, cudaStream_t s);
+void cell_geometry(fmm_ctx *h, cudaStream_t s);  // h->cgeo: centre and 1 / width of every cell
+
 // m2l_tc.cu
 void tensor_tables_init(fmm_ctx *h);
 bool tensor_m2l_supported(fmm_ctx *h);
@@ -276,6 +315,7 @@ void m2l_tensor(fmm_ctx *h, float *L, const float *M);
 // whole k-blocks where p^2 is not a multiple of 32) in one persistent launch
 void m2l_tensor_jobs(int p, int nsm, const M2LJob *jobs_dev, int njobs, int *queue, int *err, cudaStream_t s);
 M2LJob m2l_tensor_job(fmm_ctx *h, float *L, const float *M, cudaStream_t s);  // pads M if needed
+void batch_mpad(int p, const BatchSys *sys, int nsys, cudaStream_t s);  // every system's padded M rows
 
 // p2p.cu
 void near_field(fmm_ctx *h, cudaStream_t s);  // P2P into h->near

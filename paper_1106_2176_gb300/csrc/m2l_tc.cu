@@ -779,6 +779,25 @@ M2LJob m2l_tensor_job(fmm_ctx *h, float *L, const float *M, cudaStream_t s)
     return j;
 }
 
+__global__ void batch_mpad_k(int PP, int KP, const BatchSys *__restrict__ sys)
+{
+    const BatchSys &S = sys[blockIdx.y];
+    if (!S.mpad || S.c0 >= S.ncells) return;
+    const int64_t cnt = (int64_t)(S.ncells - S.c0) * KP;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
+        const int c = S.c0 + (int)(i / KP), k = (int)(i % KP);
+        S.mpad[(size_t)c * KP + k] = k < PP ? S.M[(size_t)c * PP + k] : 0.f;
+    }
+}
+
+void batch_mpad(int p, const BatchSys *sys, int nsys, cudaStream_t s)
+{
+    const int PP = p * p, KP = tc_shape(p).KB * 32;
+    if (PP == KP) return;
+    batch_mpad_k<<<dim3(16, (unsigned)nsys), 256, 0, s>>>(PP, KP, sys);
+    check_launch("batch pad");
+}
+
 void m2l_tensor_jobs(int p, int nsm, const M2LJob *jobs_dev, int njobs, int *queue, int *err, cudaStream_t s)
 {
     M2LJob none;

@@ -754,34 +754,50 @@ __device__ __forceinline__ void p2p_pairs_pk(int k, int k1, const ulonglong2 *pr
     }
 }
 
+// shared memory of one P2P block: chunk ring, TwoSum state, chunk table, barriers
 template <int TPT>
-__global__ void __launch_bounds__(P2P_T, FMM_P2P_MINB)
-    p2p_pr_k(const float4 *__restrict__ xs, const float *__restrict__ pairs, const unsigned *__restrict__ pad,
-             const unsigned *__restrict__ flag, const int *__restrict__ leaves, const int *__restrict__ begin,
-             const int *__restrict__ end, const int *__restrict__ ptr, const int2 *__restrict__ runs_pr,
-             const int *__restrict__ nrun, double4_32a *__restrict__ near, int *__restrict__ err)
+struct PRShared {
+    __align__(128) float4 buf[PR_NB][2 * PR_CHP];  // pair records, two float4 each
+    float hls[8 * TPT * P2P_T];                    // per-thread TwoSum state, column-major
+    int4 info[PR_NB];                              // per chunk: records, own-leaf records [lo, hi)
+    uint64_t full[PR_NB], empty[PR_NB];
+    int item;                                      // persistent blocks: the current work item
+};
+
+template <int TPT>
+__device__ __forceinline__ void p2p_pr_init(PRShared<TPT> &sh)
 {
-    __shared__ __align__(128) float4 buf[PR_NB][2 * PR_CHP];  // pair records, two float4 each
-    __shared__ float hls[8 * TPT * P2P_T];                      // per-thread TwoSum state, column-major
-    __shared__ int4 info[PR_NB];                                // per chunk: records, own-leaf records [lo, hi)
-    __shared__ uint64_t full[PR_NB], empty[PR_NB];
-    static_assert(sizeof(buf) >= sizeof(float2) * P2P_T * 4 * TPT, "slice sums reuse the chunk buffers");
-    float2 *red2 = reinterpret_cast<float2 *>(&buf[0][0]);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int A = leaves[blockIdx.x];
-    const int tb = begin[A], te = end[A];
-    const int k0 = ptr[A], k1 = ptr[A] + nrun[A];
-    const int op0 = (int)((tb + pad[tb]) >> 1), op1 = (int)((te + pad[te - 1] + flag[te - 1]) >> 1);
     if (threadIdx.x == 0) {
         for (int b = 0; b < PR_NB; b++) {
-            mbar_init(&full[b], 1);
-            mbar_init(&empty[b], P2P_T / 32);
+            mbar_init(&sh.full[b], 1);
+            mbar_init(&sh.empty[b], P2P_T / 32);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
+}
+
+// near field of target leaf A; cc counts the chunks this block has consumed
+// (it carries the barrier phases from one leaf to the next)
+template <int TPT>
+__device__ __forceinline__ void p2p_pr_leaf(int A, int &cc, PRShared<TPT> &sh, const float4 *__restrict__ xs,
+                                            const float *__restrict__ pairs, const unsigned *__restrict__ pad,
+                                            const unsigned *__restrict__ flag, const int *__restrict__ begin,
+                                            const int *__restrict__ end, const int *__restrict__ ptr,
+                                            const int2 *__restrict__ runs_pr, const int *__restrict__ nrun,
+                                            double4_32a *__restrict__ near, int *__restrict__ err)
+{
+    auto &buf = sh.buf;
+    float *hls = sh.hls;
+    int4 *info = sh.info;
+    uint64_t *full = sh.full, *empty = sh.empty;
+    static_assert(sizeof(sh.buf) >= sizeof(float2) * P2P_T * 4 * TPT, "slice sums reuse the chunk buffers");
+    float2 *red2 = reinterpret_cast<float2 *>(&buf[0][0]);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tb = begin[A], te = end[A];
+    const int k0 = ptr[A], k1 = ptr[A] + nrun[A];
+    const int op0 = (int)((tb + pad[tb]) >> 1), op1 = (int)((te + pad[te - 1] + flag[te - 1]) >> 1);
     bool bad = false;  // a bounded wait ran out: results of this leaf are void, err is set
-    int cc = 0;        // chunks consumed by this block so far (all passes)
 
     for (int t0 = tb; t0 < te; t0 += TPT * P2P_T) {
         const int nt = min(TPT * P2P_T, te - t0);
@@ -948,8 +964,106 @@ __global__ void __launch_bounds__(P2P_T, FMM_P2P_MINB)
                                          (double)oh[4 * kk + 2] + (double)ol[4 * kk + 2],
                                          (double)oh[4 * kk + 3] + (double)ol[4 * kk + 3]);
         }
-        __syncthreads();  // the slice sums are read before the next pass reuses the buffers
+        // the slice sums (generic writes) are read, and ordered before the
+        // bulk copies of the next pass or leaf that reuse the buffers
+        fence_proxy_async();
+        __syncthreads();
     }
+}
+
+template <int TPT>
+__global__ void __launch_bounds__(P2P_T, FMM_P2P_MINB)
+    p2p_pr_k(const float4 *__restrict__ xs, const float *__restrict__ pairs, const unsigned *__restrict__ pad,
+             const unsigned *__restrict__ flag, const int *__restrict__ leaves, const int *__restrict__ begin,
+             const int *__restrict__ end, const int *__restrict__ ptr, const int2 *__restrict__ runs_pr,
+             const int *__restrict__ nrun, double4_32a *__restrict__ near, int *__restrict__ err)
+{
+    __shared__ PRShared<TPT> sh;
+    p2p_pr_init(sh);
+    int cc = 0;
+    p2p_pr_leaf<TPT>(leaves[blockIdx.x], cc, sh, xs, pairs, pad, flag, begin, end, ptr, runs_pr, nrun, near, err);
+}
+
+// many systems: persistent blocks take (system, target leaf) items from the queue
+template <int TPT>
+__global__ void __launch_bounds__(P2P_T, FMM_P2P_MINB)
+    batch_p2p_k(const BatchSys *__restrict__ sys, const int2 *__restrict__ items, int nitems, int *__restrict__ queue,
+                int *__restrict__ err)
+{
+    __shared__ PRShared<TPT> sh;
+    p2p_pr_init(sh);
+    int cc = 0;
+    for (;;) {
+        if (threadIdx.x == 0) sh.item = atomicAdd(queue, 1);
+        __syncthreads();
+        const int it = sh.item;
+        __syncthreads();  // every thread has the item before thread 0 takes the next
+        if (it >= nitems) break;
+        const int2 item = items[it];
+        const BatchSys &S = sys[item.x];
+        p2p_pr_leaf<TPT>(item.y, cc, sh, S.xs, S.pairs, S.pad, S.flag, S.begin, S.end, S.p2p_ptr, S.runs_pr, S.nrun,
+                         S.near, err);
+    }
+}
+
+void batch_p2p(int nsm, const BatchSys *sys, const int2 *items, int nitems, int *queue, int *err, cudaStream_t s)
+{
+    FMM_CUDA_TRY(cudaMemsetAsync(queue, 0, sizeof(int), s));
+    batch_p2p_k<FMM_P2P_TPT><<<nsm * FMM_P2P_MINB, P2P_T, 0, s>>>(sys, items, nitems, queue, err);
+    check_launch("batch p2p");
+}
+
+// local expansions to zero; dependency counters to zero, except the root
+// level of the downward pass, whose only cell is final after M2L
+__global__ void batch_zero_k(int PP, const BatchSys *__restrict__ sys)
+{
+    const BatchSys &S = sys[blockIdx.y];
+    const int64_t cnt = (int64_t)S.ncells * PP;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x)
+        S.L[i] = 0.f;
+    if (blockIdx.x == 0 && threadIdx.x <= FMM_MAXLEVEL) {
+        S.cnt_up[threadIdx.x] = 0u;
+        S.cnt_dn[threadIdx.x] = threadIdx.x == 0 ? 1u : 0u;
+    }
+}
+
+void batch_zero(int p, const BatchSys *sys, int nsys, cudaStream_t s)
+{
+    batch_zero_k<<<dim3(16, (unsigned)nsys), 256, 0, s>>>(p * p, sys);
+    check_launch("batch zero");
+}
+
+// far + near back to each system's caller order: block b belongs to the
+// system whose block range [blk0[s], blk0[s + 1]) holds it
+__global__ void batch_combine_k(const BatchSys *__restrict__ sys, int nsys, const int *__restrict__ blk0)
+{
+    __shared__ int s_sys;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = nsys - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (blk0[mid] <= (int)blockIdx.x) lo = mid;
+            else hi = mid - 1;
+        }
+        s_sys = lo;
+    }
+    __syncthreads();
+    const BatchSys &S = sys[s_sys];
+    const int64_t j = (int64_t)(blockIdx.x - blk0[s_sys]) * blockDim.x + threadIdx.x;
+    if (j >= S.n) return;
+    const int64_t i = S.inv[j];
+    const double4_32a a = S.far[i], b = S.near[i];
+    S.phi[j] = (float)(a.x + b.x);
+    S.grad[3 * j + 0] = (float)(a.y + b.y);
+    S.grad[3 * j + 1] = (float)(a.z + b.z);
+    S.grad[3 * j + 2] = (float)(a.w + b.w);
+}
+
+void batch_combine(const BatchSys *sys, int nsys, const int *blk0, int nblocks, cudaStream_t s)
+{
+    if (nblocks == 0) return;
+    batch_combine_k<<<nblocks, 256, 0, s>>>(sys, nsys, blk0);
+    check_launch("batch combine");
 }
 
 void p2p_pairs_fill(fmm_ctx *h, cudaStream_t s)

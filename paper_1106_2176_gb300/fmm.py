@@ -94,6 +94,12 @@ def lib():
     L.fmm_energy.argtypes = [_vp, _vp, _vp, _vp, ctypes.POINTER(d)]
     L.fmm_energy_adjoint.argtypes = [_vp, d, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
     L.fmm_measure_peak.argtypes = [i32, i32, i32, ctypes.POINTER(d)]
+    L.fmm_batch_create.argtypes = [_vp, i32, _vp, _vp, ctypes.POINTER(_vp)]
+    L.fmm_batch_evaluate.argtypes = [_vp, _vp]
+    L.fmm_batch_status.argtypes = [_vp, ctypes.POINTER(i32), ctypes.POINTER(i64)]
+    L.fmm_batch_items.argtypes = [_vp, i32, i64] + [ctypes.POINTER(i32)] * 4
+    L.fmm_batch_withhold.argtypes = [_vp, i32, i64]
+    L.fmm_batch_destroy.argtypes = [_vp]
     L.fmm_destroy.argtypes = [_vp]
     L.fmm_last_error.argtypes = [_vp]
     L.fmm_last_error.restype = ctypes.c_char_p

@@ -65,3 +65,23 @@ def test_measurement_entry_points_check_arguments(L):
     assert L.fmm_measure_peak(fmm.FMM_PEAK_TF32_MMA, 64, 3, ctypes.byref(out)) == fmm.FMM_EINVAL
     assert L.fmm_measure_peak(fmm.FMM_PEAK_FP32_FMA, 0, 3, None) == fmm.FMM_EINVAL
     assert L.fmm_get_stats_mean(None, 1, None) == fmm.FMM_EINVAL
+
+
+def test_batch_entry_points_check_arguments(L):
+    # NULL arrays, nsys < 1, NULL batch or outputs, bad pass: rejected before
+    # any device call
+    b = ctypes.c_void_p(1234)
+    assert L.fmm_batch_create(None, 1, None, None, ctypes.byref(b)) == fmm.FMM_EINVAL
+    assert b.value is None
+    arr = (ctypes.c_void_p * 1)(None)
+    assert L.fmm_batch_create(arr, 0, arr, arr, ctypes.byref(b)) == fmm.FMM_EINVAL
+    assert L.fmm_batch_create(arr, 1, arr, arr, None) == fmm.FMM_EINVAL
+    assert L.fmm_batch_create(arr, 1, arr, arr, ctypes.byref(b)) == fmm.FMM_EINVAL
+    assert L.fmm_batch_evaluate(None, None) == fmm.FMM_EINVAL
+    e, k = ctypes.c_int(), ctypes.c_int64()
+    assert L.fmm_batch_status(None, ctypes.byref(e), ctypes.byref(k)) == fmm.FMM_EINVAL
+    i = [ctypes.c_int() for _ in range(4)]
+    assert L.fmm_batch_items(None, 0, 0, *[ctypes.byref(v) for v in i]) == fmm.FMM_EINVAL
+    assert L.fmm_batch_withhold(None, 0, 0) == fmm.FMM_EINVAL
+    assert L.fmm_batch_destroy(None) == fmm.FMM_EINVAL
+    assert b"fmm_batch" in L.fmm_last_error(None)
