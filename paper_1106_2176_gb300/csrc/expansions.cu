@@ -30,6 +30,7 @@
 #include <tuple>
 
 #include "fmm_internal.cuh"
+#include "m2lx_layout.cuh"
 
 namespace fmm {
 
@@ -713,19 +714,25 @@ __global__ void __launch_bounds__(M2L_CC_T) m2l_cc_k(int p, const M2LTile *__res
 constexpr int M2LX_W = 4;
 
 // Column m of I_n^m(u), n = m .. Q-1, computed in C and written as T to
-// full complex storage: I_m^m = (2m-1)!! (x + iy)^m / r^(2m+1), then the
-// three-term recurrence in n; orders -m from I_n^-m = (-1)^m conj(I_n^m).
-template <class C, class T>
-__device__ void irregular_col(int Q, int m, C x, C y, C z, T *sI)
+// complex storage whose entry (n, m) sits at row(n) + m (full storage: row(n)
+// = n^2 + n): I_m^m = (2m-1)!! (x + iy)^m / r^(2m+1), then the three-term
+// recurrence in n; orders -m from I_n^-m = (-1)^m conj(I_n^m).
+struct FullRows {
+    __device__ int operator()(int n) const { return n * n + n; }
+};
+
+template <class C, class T, class Row = FullRows>
+__device__ void irregular_col(int Q, int m, C x, C y, C z, T *sI, Row row = Row())
 {
     const C r2 = x * x + y * y + z * z, ir2 = C(1) / r2;
     const C sg = (m & 1) ? C(-1) : C(1);
     auto put = [&](int n, C cr, C ci) {
-        sI[2 * (n * n + n + m)] = (T)cr;
-        sI[2 * (n * n + n + m) + 1] = (T)ci;
+        const int e = row(n);
+        sI[2 * (e + m)] = (T)cr;
+        sI[2 * (e + m) + 1] = (T)ci;
         if (m) {
-            sI[2 * (n * n + n - m)] = (T)(sg * cr);
-            sI[2 * (n * n + n - m) + 1] = (T)(-sg * ci);
+            sI[2 * (e - m)] = (T)(sg * cr);
+            sI[2 * (e - m) + 1] = (T)(-sg * ci);
         }
     };
     C pr = sqrt(ir2), pi = C(0);
@@ -829,13 +836,17 @@ __global__ void __launch_bounds__(32 * M2LX_W) m2lx_k(int p, int nc, const int *
     }
 }
 
-// FP32 form of the same for p = 2 .. 10, p fixed at compile time.  Eight warps
+// FP32 form of the same for p = 2 .. 10, p fixed at compile time. Eight warps
 // per target cell, each half-warp on its own pair: the cell's pair q goes to
-// half-warp q % 16 (its 16 lanes own outputs o, o + 16, ... of the triangle and
-// build columns m, m + 16 of I(u)).  A warp loads the source ids and cells of
-// 32 of its pairs at once (lane i: pair i), prefetches each half's next M~
-// while the current pair is computed, and keeps running sums as FP32 (hi, lo)
-// pairs; the 16 partial sums are added in half-warp order.
+// half-warp q % 16. Lane u of a half-warp owns a run of R consecutive orders
+// m0 .. m0+R-1 of one degree n (M2lxLayout<P>), so each entry of I(u) it loads
+// serves up to R outputs and each row of M~ it loads (16-byte broadcast loads)
+// serves R; the rows of I(u) are placed so that the 16 lanes' loads of one
+// step fall in 16 different bank pairs (m2lx_layout.py gives the argument).
+// A warp loads the source ids and cells of 32 of its pairs at once (lane i:
+// pair i), prefetches each half's next M~ while the current pair is computed,
+// and keeps running sums as FP32 (hi, lo) pairs; the 16 partial sums are added
+// in half-warp order.
 constexpr int M2LX_FW = 8;
 
 __device__ __forceinline__ void m2lx_two_sum(float &hi, float &lo, float b)
@@ -846,12 +857,42 @@ __device__ __forceinline__ void m2lx_two_sum(float &hi, float &lo, float b)
     hi = s;
 }
 
+// entry of I_l^0 in a half-warp's table: row l starts where row l-1 ends,
+// moved up to the first entry with rowptr(l) = C l (mod 16)
+template <int P>
+__host__ __device__ constexpr int m2lx_rowptr(int l)
+{
+    int nxt = 0, b = 0;
+    for (int i = 0; i <= l; i++) {
+        b = nxt;
+        while ((((b + i - M2lxLayout<P>::C * i) % 16) + 16) % 16 != 0) b++;
+        nxt = b + 2 * i + 1;
+    }
+    return b + l;
+}
+
+// entries of one half-warp's I table (the last row, the R-1 entries a run
+// reads past its end), rounded up to even so that M~ starts 16-byte aligned
+template <int P>
+__host__ __device__ constexpr int m2lx_isize()
+{
+    constexpr int Q = 2 * P - 1;
+    return (m2lx_rowptr<P>(Q - 1) + Q + M2lxLayout<P>::R - 1 + 1) & ~1;
+}
+
 template <int P>
 constexpr size_t m2lx_f_smem()
 {
-    return sizeof(float2) * 2 * M2LX_FW * (size_t)((2 * P - 1) * (2 * P - 1) + P * P) +
-           sizeof(double) * 2 * M2LX_FW * (size_t)(P * (P + 1));
+    // per half-warp: I table, then M~ rows j at j(j+1) (2j+1 entries and one
+    // spare, so each row is whole 16-byte pairs); the partial sums; the row table
+    return sizeof(float2) * 2 * M2LX_FW * (size_t)(m2lx_isize<P>() + P * (P + 1)) +
+           sizeof(double) * 2 * M2LX_FW * (size_t)(P * (P + 1)) + sizeof(int) * 2 * P;
 }
+
+struct TableRows {
+    const int *rp;
+    __device__ int operator()(int n) const { return rp[n]; }
+};
 
 // different-level M2L into target cell c by one CTA of 32 M2LX_FW threads
 template <int P>
@@ -859,17 +900,23 @@ __device__ __forceinline__ void m2lx_f_cell(int c, const int *__restrict__ ptr, 
                                             const int4 *__restrict__ xyz, const float *__restrict__ M,
                                             float *__restrict__ L, unsigned char *smem_raw)
 {
-    constexpr int PP = P * P, Q = 2 * P - 1, NT = P * (P + 1) / 2, NO = (NT + 15) / 16, NM = (PP + 15) / 16;
+    using Lay = M2lxLayout<P>;
+    constexpr int PP = P * P, Q = 2 * P - 1, NT = P * (P + 1) / 2, NM = (PP + 15) / 16, R = Lay::R;
     constexpr int NH = 2 * M2LX_FW;  // half-warps
+    constexpr int IS = m2lx_isize<P>(), HS = IS + P * (P + 1);
     const int k0 = ptr[c], npair = ptr[c + 1] - k0;
     if (npair == 0) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15;
     const int hw = 2 * warp + half;
-    float2 *sI = reinterpret_cast<float2 *>(smem_raw) + (size_t)hw * (Q * Q + PP);
-    float2 *sM = sI + Q * Q;
-    double *red = reinterpret_cast<double *>(reinterpret_cast<float2 *>(smem_raw) + (size_t)NH * (Q * Q + PP));
+    float2 *sI = reinterpret_cast<float2 *>(smem_raw) + (size_t)hw * HS;
+    float2 *sM = sI + IS;
+    double *red = reinterpret_cast<double *>(reinterpret_cast<float2 *>(smem_raw) + (size_t)NH * HS);
+    int *rp = reinterpret_cast<int *>(red + (size_t)NH * 2 * NT);
+    if ((int)threadIdx.x < Q) rp[threadIdx.x] = m2lx_rowptr<P>((int)threadIdx.x);
+    __syncthreads();
     const int4 a = xyz[c];
-    // this lane's entries of M~ in full complex storage: i = hl + 16 r = j^2 + j + k
+    // this lane's entries of M~ in full complex storage: i = hl + 16 r = j^2 + j + k,
+    // staged at j(j+1) + j + k = i + j
     int mre[NM], mim[NM], mj[NM];
     float msr[NM], msi[NM];
 #pragma unroll
@@ -886,19 +933,16 @@ __device__ __forceinline__ void m2lx_f_cell(int c, const int *__restrict__ ptr, 
         msr[r] = sg;
         msi[r] = k < 0 ? -sg : sg;
     }
-    // this lane's outputs o = hl + 16 r of the (n, m) triangle
-    int on[NO], om[NO];
+    // this lane's run of outputs: degree rn, orders rm0 .. rm0 + rlen - 1
+    const int rn = (int)((Lay::N >> (4 * hl)) & 15ull), rm0 = (int)((Lay::M0 >> (4 * hl)) & 15ull),
+              rlen = (int)((Lay::LEN >> (4 * hl)) & 15ull);
+    // step t of row j reads I entry ib[j] + t
+    int ib[P];
 #pragma unroll
-    for (int r = 0; r < NO; r++) {
-        const int o = hl + 16 * r;
-        int n = 0;
-        while ((n + 1) * (n + 2) / 2 <= o) n++;
-        on[r] = o < NT ? n : -1;
-        om[r] = o - n * (n + 1) / 2;
-    }
-    float ahr[NO], alr[NO], ahi[NO], ali[NO];
+    for (int j = 0; j < P; j++) ib[j] = rlen ? rp[j + rn] + rm0 - j : 0;
+    float ahr[R], alr[R], ahi[R], ali[R];
 #pragma unroll
-    for (int r = 0; r < NO; r++) ahr[r] = alr[r] = ahi[r] = ali[r] = 0.f;
+    for (int i = 0; i < R; i++) ahr[i] = alr[i] = ahi[i] = ali[i] = 0.f;
 
     // step t of this warp: half h takes pair q = NH t + 2 warp + h
     const int nstep = npair > 2 * warp ? (npair - 2 * warp + NH - 1) / NH : 0;
@@ -942,52 +986,65 @@ __device__ __forceinline__ void m2lx_f_cell(int c, const int *__restrict__ ptr, 
             const float uz = (float)(2LL * (a.z - bz) + (WA - WB)) * sc;
             __syncwarp();
             if (valid) {
-                for (int m = hl; m < Q; m += 16) irregular_col<float, float>(Q, m, ux, uy, uz, reinterpret_cast<float *>(sI));
+                for (int m = hl; m < Q; m += 16)
+                    irregular_col<float, float>(Q, m, ux, uy, uz, reinterpret_cast<float *>(sI), TableRows{rp});
 #pragma unroll
                 for (int r = 0; r < NM; r++)
                     if (hl + 16 * r < PP) {
                         const float f = dl < 0 ? ldexpf(1.f, dl * mj[r]) : 1.f;  // (w_B / s)^j
-                        sM[hl + 16 * r] = make_float2(pre[r] * msr[r] * f, pim[r] * msi[r] * f);
+                        sM[hl + 16 * r + mj[r]] = make_float2(pre[r] * msr[r] * f, pim[r] * msi[r] * f);
                     }
             }
             if (t + 1 < nb && NH * (t0 + t + 1) + 2 * warp + half < npair) fetch(Bn);
             __syncwarp();
-            if (!valid) continue;
-#pragma unroll 1
-            for (int r = 0; r < NO; r++) {
-                if (on[r] < 0) continue;
-                const int n = on[r], m = om[r];
-                // eight independent partial sums (term parity x four products)
-                // keep the FMA chains short
-                float a0[2] = {0.f, 0.f}, a1[2] = {0.f, 0.f}, a2[2] = {0.f, 0.f}, a3[2] = {0.f, 0.f};
+            if (!valid || rlen == 0) continue;
+            // four partial sums per output (the four real products) keep the
+            // FMA chains independent
+            float a0[R], a1[R], a2[R], a3[R];
 #pragma unroll
-                for (int j = 0; j < P; j++) {
-                    const float2 *Ij = sI + (j + n) * (j + n) + (j + n) + m;
+            for (int i = 0; i < R; i++) a0[i] = a1[i] = a2[i] = a3[i] = 0.f;
 #pragma unroll
-                    for (int k = -j; k <= j; k++) {
-                        const int t = (j * j + j + k) & 1;
-                        const float2 mv = sM[j * j + j + k];
-                        const float2 iv = Ij[k];
-                        a0[t] = fmaf(mv.x, iv.x, a0[t]);
-                        a1[t] = fmaf(mv.y, iv.y, a1[t]);
-                        a2[t] = fmaf(mv.x, iv.y, a2[t]);
-                        a3[t] = fmaf(mv.y, iv.x, a3[t]);
+            for (int j = 0; j < P; j++) {
+                float2 mv[2 * P];
+                const float4 *Mj = reinterpret_cast<const float4 *>(sM + j * (j + 1));
+#pragma unroll
+                for (int s2 = 0; s2 <= j; s2++) {
+                    const float4 v = Mj[s2];
+                    mv[2 * s2] = make_float2(v.x, v.y);
+                    mv[2 * s2 + 1] = make_float2(v.z, v.w);
+                }
+                const float2 *Ij = sI + ib[j];
+#pragma unroll
+                for (int e = 0; e < 2 * j + R; e++) {
+                    const float2 iv = Ij[e];
+#pragma unroll
+                    for (int i = 0; i < R; i++) {
+                        const int k = e - i - j;  // output m = rm0 + i takes I_{j+n}^{m+k} M_j^k
+                        if (k >= -j && k <= j) {
+                            const float2 mk = mv[k + j];
+                            a0[i] = fmaf(mk.x, iv.x, a0[i]);
+                            a1[i] = fmaf(mk.y, iv.y, a1[i]);
+                            a2[i] = fmaf(mk.x, iv.y, a2[i]);
+                            a3[i] = fmaf(mk.y, iv.x, a3[i]);
+                        }
                     }
                 }
-                const float sr = (a0[0] + a0[1]) - (a1[0] + a1[1]), si = (a2[0] + a2[1]) + (a3[0] + a3[1]);
-                float f = dl > 0 ? ldexpf(1.f, -dl * (n + 1)) : 1.f;  // (w_A / s)^(n+1)
-                if (n & 1) f = -f;
-                m2lx_two_sum(ahr[r], alr[r], f * sr);
-                m2lx_two_sum(ahi[r], ali[r], f * si);
+            }
+            float f = dl > 0 ? ldexpf(1.f, -dl * (rn + 1)) : 1.f;  // (w_A / s)^(n+1)
+            if (rn & 1) f = -f;
+#pragma unroll
+            for (int i = 0; i < R; i++) {
+                m2lx_two_sum(ahr[i], alr[i], f * (a0[i] - a1[i]));
+                m2lx_two_sum(ahi[i], ali[i], f * (a2[i] + a3[i]));
             }
         }
     }
+    const int o0 = rn * (rn + 1) / 2 + rm0;
 #pragma unroll
-    for (int r = 0; r < NO; r++)
-        if (on[r] >= 0) {
-            const int o = hl + 16 * r;
-            red[(size_t)hw * 2 * NT + 2 * o] = (double)ahr[r] + (double)alr[r];
-            red[(size_t)hw * 2 * NT + 2 * o + 1] = (double)ahi[r] + (double)ali[r];
+    for (int i = 0; i < R; i++)
+        if (i < rlen) {
+            red[(size_t)hw * 2 * NT + 2 * (o0 + i)] = (double)ahr[i] + (double)alr[i];
+            red[(size_t)hw * 2 * NT + 2 * (o0 + i) + 1] = (double)ahi[i] + (double)ali[i];
         }
     __syncthreads();
     if (warp) return;
@@ -1007,7 +1064,7 @@ __device__ __forceinline__ void m2lx_f_cell(int c, const int *__restrict__ ptr, 
 }
 
 template <int P>
-__global__ void __launch_bounds__(32 * M2LX_FW, 3) m2lx_f_k(int nc, const int *__restrict__ ptr,
+__global__ void __launch_bounds__(32 * M2LX_FW, 2) m2lx_f_k(int nc, const int *__restrict__ ptr,
                                                             const int *__restrict__ src, const int4 *__restrict__ xyz,
                                                             const float *__restrict__ M, float *__restrict__ L)
 {
@@ -1685,7 +1742,7 @@ __global__ void __launch_bounds__(32 * MV_WARPS) batch_down_k(const BatchSys *__
 }
 
 template <int P>
-__global__ void __launch_bounds__(32 * M2LX_FW, 3) batch_m2lx_k(const BatchSys *__restrict__ sys,
+__global__ void __launch_bounds__(32 * M2LX_FW, 2) batch_m2lx_k(const BatchSys *__restrict__ sys,
                                                                const int2 *__restrict__ items, int nitems)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -214,3 +214,23 @@ def test_tensor_and_cudacore_engines_agree():
     pc, gc, fc = run_fmm(x, q, 8, 0.5, 64, precision="mixed", dtype=np.float32, engine="cudacore")
     assert ft.stats()["m2l_engine"] == 1 and fc.stats()["m2l_engine"] == 2
     assert rel(pt, pc) < 1e-6 and rel(gt, gc) < 1e-6
+
+
+@pytest.mark.parametrize("P", [2, 3, 5, 7, 8, 9, 10])
+def test_mixed_irregular_m2l_matches_fp64_expansions(P):
+    # adaptive tree (Plummer sphere, small leaves): the accepted pairs whose
+    # cells sit on different levels run through the FP32 CUDA-core kernel (one
+    # run of orders per lane, each p's own shared-memory layout); the local
+    # expansions of every cell against the FP64 path's, relative to each
+    # cell's largest coefficient
+    x, q = inputs.plummer(40000, 31)
+    _, _, f64 = run_fmm(x, q, P, 0.5, 8, precision="fp64")
+    _, _, fmx = run_fmm(x, q, P, 0.5, 8, precision="mixed")
+    st = fmx.stats()
+    assert st["n_m2l_irregular"] > 1000 and st["async_error"] == 0
+    _, L64 = f64.export_expansions()
+    _, Lmx = fmx.export_expansions()
+    lev = f64.export_tree()["level"]
+    sel = lev >= 2
+    sc = np.max(np.abs(L64[sel]), axis=1, keepdims=True) + 1e-300
+    assert np.max(np.abs(Lmx[sel] - L64[sel]) / sc) < 2e-5
