@@ -614,7 +614,8 @@ def main():
     p2p_avg = phase["ms_p2p"]
     achieved = FLOP_PER_INTERACTION * inter / (p2p_avg / 1000.0) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak, "traffic": p2p_traffic(inter, N), "kernel": "p2p_k<float>",
+                "frac": achieved / fp32_peak, "traffic": p2p_traffic(inter, N),
+                "kernel": "p2p_pr_k<2>" if a.precision == "mixed" else "p2p_k<double>",
                 "peak_note": "measured: FP32 FMA-chain microbenchmark (fmm_measure_peak, best of scalar FMA and "
                              "packed f32x2 FMA, full occupancy) on this GPU before the timed region; 20 flop per "
                              "interaction",

@@ -956,14 +956,21 @@ __global__ void tiles_k(int depth, int tile, int pool_max, const unsigned *__res
     *ntiles = nt;
 }
 
+// A complete (level, octant) group (all 8^(l-1) cells present) is placed in
+// the Morton order of its sub-lattice, so that every tile of it is a block of
+// 8 x 4 x 4 cells with row = Morton index - tile base (the tensor-core M2L
+// reuses source rows along x in such tiles); other groups in arrival order.
 __global__ void oct_scatter_k(int c0, int nc, const int *__restrict__ level, const uint64_t *__restrict__ anchor,
-                              const unsigned *__restrict__ goff, unsigned *__restrict__ fill, int *__restrict__ tgt)
+                              const unsigned *__restrict__ grp, const unsigned *__restrict__ goff,
+                              unsigned *__restrict__ fill, int *__restrict__ tgt)
 {
     int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= nc) return;
     int l = level[c];
-    int o = (int)((anchor[c] >> (3 * (FMM_MAXLEVEL - l))) & 7u);
-    unsigned pos = goff[l * 8 + o] + atomicAdd(&fill[l * 8 + o], 1u);
+    const uint64_t code = anchor[c] >> (3 * (FMM_MAXLEVEL - l));
+    int o = (int)(code & 7u);
+    const bool complete = l <= 10 && grp[l * 8 + o] == (1u << (3 * (l - 1)));
+    unsigned pos = goff[l * 8 + o] + (complete ? (unsigned)(code >> 3) : atomicAdd(&fill[l * 8 + o], 1u));
     tgt[pos] = c;
 }
 
@@ -1385,7 +1392,7 @@ void tree_build(fmm_ctx *h, const void *x, const void *q, int64_t n, int dt)
         count_launch(h);
         if (nt > 0) {
             oct_scatter_k<<<nblocks(nt, TB), TB, 0, s>>>(c0, ncells, h->c_level.as<int>(), h->c_anchor.as<uint64_t>(),
-                                                         goff, fill, h->m2l_tgt.as<int>());
+                                                         grp, goff, fill, h->m2l_tgt.as<int>());
             count_launch(h);
         }
         check_launch("m2l tiles");
