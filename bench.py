@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=100_000)
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg (profiling runs)")
     ap.add_argument("--batch", type=int, default=512, help="systems in the batched-evaluation leg (0 = skip)")
+    ap.add_argument("--batch-modes", default="each,graph,engine,engine_graph",
+                    help="batched-evaluation modes to time (profiling runs take one)")
     ap.add_argument("--diff-n", type=int, default=1_000_000, help="particles in the differentiation leg (0 = skip)")
     ap.add_argument("--engines-n", type=int, default=1_000_000,
                     help="particles of the M2L engine comparison at p = 8, 10, 16 (0 = skip)")
@@ -343,12 +345,20 @@ def run_batch(a, dev):
         return sum(ts) / len(ts)
 
     reps = max(a.steps, 3)
-    k0 = sum(f.stats()["kernel_launches"] for f in b.handles)
-    t_each = timed(b.evaluate_each, reps)
-    launches_each = (sum(f.stats()["kernel_launches"] for f in b.handles) - k0) // (reps + max(a.warmup, 3))
-    t_streams = timed(b.replay_streams, reps)
-    t_engine = timed(b.evaluate, reps)
-    t_engine_graph = timed(b.replay, reps)
+    modes = set(a.batch_modes.split(","))
+    t_each = t_streams = t_engine = t_engine_graph = launches_each = None
+    if "each" in modes:
+        k0 = sum(f.stats()["kernel_launches"] for f in b.handles)
+        t_each = timed(b.evaluate_each, reps)
+        launches_each = (sum(f.stats()["kernel_launches"] for f in b.handles) - k0) // (reps + max(a.warmup, 3))
+    if "graph" in modes:
+        t_streams = timed(b.replay_streams, reps)
+    if "engine" in modes:
+        t_engine = timed(b.evaluate, reps)
+    if "engine_graph" in modes:
+        t_engine_graph = timed(b.replay, reps)
+    if t_engine is None and t_engine_graph is None:
+        b.evaluate()
     err, launches_engine = b.status()
     e_phi = e_grad = 0.0
     for (x, q), f, (phi, grad) in zip(systems, b.handles, b.out):
@@ -357,13 +367,15 @@ def run_batch(a, dev):
         pd, gd = f.direct(x, q, t)
         e_phi = max(e_phi, float(torch.linalg.norm(phi[t].double() - pd) / torch.linalg.norm(pd)))
         e_grad = max(e_grad, float(torch.linalg.norm(grad[t].double() - gd) / torch.linalg.norm(gd)))
-    best = min(t_engine, t_engine_graph)
+    best = min([t for t in (t_engine, t_engine_graph) if t is not None] or
+               [t for t in (t_streams, t_each) if t is not None])
+    ratio = lambda t: t / best if t is not None else None
     out = {"workload": "%d systems, n log-uniform in [1e3, 1e5], half uniform cube, half Plummer, q U[-1,1], FP32, "
                        "p=6, theta=0.5, mixed precision" % a.batch,
            "systems": a.batch, "particles": b.particles,
            "engine_ms": t_engine, "engine_graph_ms": t_engine_graph,
            "per_system_graph_ms": t_streams, "per_system_launches_ms": t_each,
-           "speedup_vs_per_system_launches": t_each / best, "speedup_vs_per_system_graph": t_streams / best,
+           "speedup_vs_per_system_launches": ratio(t_each), "speedup_vs_per_system_graph": ratio(t_streams),
            "particles_per_s": b.particles / (best / 1000.0), "async_error": err,
            "max_rel_l2_phi": e_phi, "max_rel_l2_grad": e_grad, "error_targets_per_system": 32,
            "ncrit_by_half_decade": {str(k / 2): v for k, v in (b.ncrit_by_bucket or {}).items()},
