@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=512, help="systems in the batched-evaluation leg (0 = skip)")
     ap.add_argument("--batch-modes", default="each,graph,engine,engine_graph",
                     help="batched-evaluation modes to time (profiling runs take one)")
+    ap.add_argument("--batch-pool-sweep", default="0,64,4096",
+                    help="M2L tile pooling thresholds (cells) timed with the batch engine besides the default 512 ('' = none)")
     ap.add_argument("--diff-n", type=int, default=1_000_000, help="particles in the differentiation leg (0 = skip)")
     ap.add_argument("--engines-n", type=int, default=1_000_000,
                     help="particles of the M2L engine comparison at p = 8, 10, 16 (0 = skip)")
@@ -360,6 +362,7 @@ def run_batch(a, dev):
     if t_engine is None and t_engine_graph is None:
         b.evaluate()
     err, launches_engine = b.status()
+    out_nc = b.ncrit_by_bucket
     e_phi = e_grad = 0.0
     for (x, q), f, (phi, grad) in zip(systems, b.handles, b.out):
         n = x.shape[0]
@@ -381,6 +384,15 @@ def run_batch(a, dev):
            "ncrit_by_half_decade": {str(k / 2): v for k, v in (b.ncrit_by_bucket or {}).items()},
            "streams": b.nstreams, "kernel_launches_engine": launches_engine,
            "kernel_launches_per_system_launches": launches_each}
+    # the M2L tile shape: levels with at most `pool` cells pool their 8
+    # octants' tiles; the engine timed with other thresholds (same leaf sizes)
+    sweep = {"512 (default)": t_engine}
+    for pool in [int(v) for v in a.batch_pool_sweep.split(",") if v.strip()]:
+        b.close()
+        b = FMMBatch(systems, p=6, theta=0.5, ncrit=out_nc, precision="mixed", streams=8, mode="persistent", m2l_pool=pool)
+        sweep[str(pool)] = timed(b.evaluate, reps)
+        assert b.status()[0] == 0
+    out["engine_ms_by_m2l_pool_cells"] = sweep
     b.close()
     return out
 

@@ -156,6 +156,17 @@ FMM_API int fmm_set_overlap(fmm_handle h, int on);
  * NULL handle or on not 0/1. */
 FMM_API int fmm_set_uniform_path(fmm_handle h, int on);
 
+/*
+ * Same-level M2L tiles (the tensor-core and dense engines): tiles hold the
+ * cells of one level and one octant, except on levels with at most max_cells
+ * cells, which are pooled over the 8 octants into tiles that walk the union
+ * of the 8 stencils (fuller tiles, longer walks; Sec. 5's grouping of work
+ * into large, contiguous pieces). max_cells = -1: the default, 4 tiles' worth
+ * (512 cells for the tensor-core engine); 0: no pooling. Takes effect at the
+ * next build. Returns FMM_EINVAL for a NULL handle or max_cells < -1.
+ */
+FMM_API int fmm_set_m2l_pool(fmm_handle h, int max_cells);
+
 /* Use the given cudaStream_t (NULL = legacy default stream) for all work. */
 FMM_API int fmm_set_stream(fmm_handle h, void *stream);
 

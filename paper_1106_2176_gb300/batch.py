@@ -93,10 +93,13 @@ def tune_buckets(systems, p, theta, precision, candidates=NCRIT_CANDIDATES, nstr
 
 
 class FMMBatch:
-    def __init__(self, systems, p=6, theta=0.5, ncrit=64, precision="mixed", streams=8, mode="persistent"):
+    def __init__(self, systems, p=6, theta=0.5, ncrit=64, precision="mixed", streams=8, mode="persistent",
+                 m2l_pool=-1):
         """systems: list of (x (n, 3), q (n,)) CUDA tensors of one dtype.
-        ncrit: a leaf size for every system, or "auto" for one per size bucket.
-        mode: "persistent" (the batch engine) or "graph" (per-system launches in one graph)."""
+        ncrit: a leaf size for every system, "auto" for one per size bucket
+        (tuned), or a {bucket: ncrit} dict from an earlier tuning.
+        mode: "persistent" (the batch engine) or "graph" (per-system launches in one graph).
+        m2l_pool: pooling threshold of the same-level M2L tiles (FMM.set_m2l_pool)."""
         if mode not in ("persistent", "graph"):
             raise ValueError("mode must be 'persistent' or 'graph'")
         self.mode = mode
@@ -104,11 +107,14 @@ class FMMBatch:
         if ncrit == "auto":
             self.ncrit_by_bucket, bucket = tune_buckets(systems, p, theta, precision, nstreams=max(1, int(streams)))
             per = [self.ncrit_by_bucket[b] for b in bucket]
+        elif isinstance(ncrit, dict):
+            self.ncrit_by_bucket = dict(ncrit)
+            per = [self.ncrit_by_bucket[size_bucket(x.shape[0])] for x, _ in systems]
         else:
             self.ncrit_by_bucket = None
             per = [int(ncrit)] * len(systems)
         for (x, q), nc in zip(systems, per):
-            f = FMM(x.shape[0], p=p, theta=theta, ncrit=nc, precision=precision, overlap=False)
+            f = FMM(x.shape[0], p=p, theta=theta, ncrit=nc, precision=precision, overlap=False, m2l_pool=m2l_pool)
             f.build(x, q)
             self.handles.append(f)
             self.out.append(f.evaluate())  # warm-up: every workspace exists from here on

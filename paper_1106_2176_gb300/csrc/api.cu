@@ -300,6 +300,14 @@ int fmm_set_uniform_path(fmm_handle h, int on)
     return FMM_OK;
 }
 
+int fmm_set_m2l_pool(fmm_handle h, int max_cells)
+{
+    if (!h) return fail(FMM_EINVAL, "fmm_set_m2l_pool: NULL handle");
+    if (max_cells < -1) return fail(FMM_EINVAL, "fmm_set_m2l_pool: max_cells must be >= -1");
+    h->m2l_pool = max_cells;
+    return FMM_OK;
+}
+
 int fmm_set_stream(fmm_handle h, void *stream)
 {
     if (!h) return fail(FMM_EINVAL, "fmm_set_stream: NULL handle");

@@ -198,6 +198,7 @@ struct fmm_ctx {
     int ntiles_max = 0;
     int p2p_cap_hint = 0;       // near-field stencil size (P2P sources of a leaf in a uniform tree)
     bool uniform_req = true;    // full octrees take the lattice-stencil lists (fmm_set_uniform_path)
+    int m2l_pool = -1;          // levels with at most this many cells pool their octants' M2L tiles (-1: 4 tiles)
     bool uniform_used = false;  // the last build did
     double ms_build = 0;
 

@@ -1388,7 +1388,8 @@ void tree_build(fmm_ctx *h, const void *x, const void *q, int64_t n, int dt)
             oct_count_k<<<nblocks(nt, TB), TB, 0, s>>>(c0, ncells, h->c_level.as<int>(), h->c_anchor.as<uint64_t>(), grp);
             count_launch(h);
         }
-        tiles_k<<<1, 1, 0, s>>>(depth, tile, 4 * tile, grp, goff, h->m2l_tiles.as<M2LTile>(), ntiles);
+        const int pool_max = h->m2l_pool >= 0 ? h->m2l_pool : 4 * tile;
+        tiles_k<<<1, 1, 0, s>>>(depth, tile, pool_max, grp, goff, h->m2l_tiles.as<M2LTile>(), ntiles);
         count_launch(h);
         if (nt > 0) {
             oct_scatter_k<<<nblocks(nt, TB), TB, 0, s>>>(c0, ncells, h->c_level.as<int>(), h->c_anchor.as<uint64_t>(),

@@ -78,6 +78,7 @@ def lib():
     L.fmm_set_precision.argtypes = [_vp, i32]
     L.fmm_set_m2l_engine.argtypes = [_vp, i32]
     L.fmm_set_overlap.argtypes = [_vp, i32]
+    L.fmm_set_m2l_pool.argtypes = [_vp, i32]
     L.fmm_set_stream.argtypes = [_vp, _vp]
     L.fmm_set_uniform_path.argtypes = [_vp, ctypes.c_int]
     L.fmm_m2l_rotation_host.argtypes = [ctypes.c_int, _vp, _vp, _vp]
@@ -128,7 +129,7 @@ class FMM:
     """Handle of one FMM configuration (N, p, theta, ncrit) on the current GPU."""
 
     def __init__(self, N, p=8, theta=0.5, ncrit=64, precision="fp64", m2l_engine="auto", overlap=True,
-                 uniform_path=True):
+                 uniform_path=True, m2l_pool=-1):
         self._h = _vp()
         _check(lib().fmm_create(int(N), int(p), float(theta), int(ncrit), ctypes.byref(self._h)))
         self.N, self.p, self.theta, self.ncrit = int(N), int(p), float(theta), int(ncrit)
@@ -136,6 +137,7 @@ class FMM:
         self.set_m2l_engine(m2l_engine)
         self.set_overlap(overlap)
         self.set_uniform_path(uniform_path)
+        self.set_m2l_pool(m2l_pool)
         self._n = 0
         self._dtype = None
         self._host = False
@@ -160,6 +162,12 @@ class FMM:
         """True: full octrees skip the traversal (lattice-stencil lists); False: always traverse."""
         _check(lib().fmm_set_uniform_path(self._h, 1 if on else 0), self._h)
         self.uniform_path = bool(on)
+
+    def set_m2l_pool(self, max_cells):
+        """Levels with at most max_cells cells pool the 8 octants' same-level M2L
+        tiles (-1: the default, 4 tiles' worth; 0: never). Next build."""
+        _check(lib().fmm_set_m2l_pool(self._h, int(max_cells)), self._h)
+        self.m2l_pool = int(max_cells)
 
     # -- the two calls of the method ------------------------------------------
     def build(self, x, q):

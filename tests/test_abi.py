@@ -85,3 +85,7 @@ def test_batch_entry_points_check_arguments(L):
     assert L.fmm_batch_withhold(None, 0, 0) == fmm.FMM_EINVAL
     assert L.fmm_batch_destroy(None) == fmm.FMM_EINVAL
     assert b"fmm_batch" in L.fmm_last_error(None)
+
+
+def test_m2l_pool_setter_checks_arguments(L):
+    assert L.fmm_set_m2l_pool(None, 512) == fmm.FMM_EINVAL

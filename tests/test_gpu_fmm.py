@@ -234,3 +234,18 @@ def test_mixed_irregular_m2l_matches_fp64_expansions(P):
     sel = lev >= 2
     sc = np.max(np.abs(L64[sel]), axis=1, keepdims=True) + 1e-300
     assert np.max(np.abs(Lmx[sel] - L64[sel]) / sc) < 2e-5
+
+
+@pytest.mark.parametrize("pool,gen", [(0, "uniform"), (4096, "uniform"), (0, "plummer"), (100000, "plummer")])
+def test_m2l_tile_pooling_keeps_the_error_bound(pool, gen):
+    # per-octant tiles on every level (pool 0) or pooled tiles on every level
+    # up to `pool` cells: the same pairs in other tiles, so each mixed run stays
+    # within its FP64 FMM's error on the same targets plus 2e-6
+    x, q = getattr(inputs, "uniform_cube" if gen == "uniform" else "plummer")(30000, 41)
+    t = inputs.sample_targets(len(q), 512, seed=41)
+    pd, gd = oracle.direct(x, q, targets=t)
+    p64, g64, f64 = run_fmm(x, q, 6, 0.5, 32, precision="fp64", m2l_pool=pool)
+    pm, gm, fm = run_fmm(x, q, 6, 0.5, 32, precision="mixed", m2l_pool=pool)
+    assert fm.stats()["async_error"] == 0
+    assert rel(p64[t], pd) < 1e-4 and rel(g64[t], gd) < 1e-4
+    assert rel(pm[t], pd) <= rel(p64[t], pd) + MIXED_SLACK and rel(gm[t], gd) <= rel(g64[t], gd) + MIXED_SLACK
