@@ -383,7 +383,10 @@ def run_batch(a, dev):
            "max_rel_l2_phi": e_phi, "max_rel_l2_grad": e_grad, "error_targets_per_system": 32,
            "ncrit_by_half_decade": {str(k / 2): v for k, v in (b.ncrit_by_bucket or {}).items()},
            "streams": b.nstreams, "kernel_launches_engine": launches_engine,
-           "kernel_launches_per_system_launches": launches_each}
+           "kernel_launches_per_system_launches": launches_each,
+           "interactions": sum(int(f.stats()["n_interactions"]) for f in b.handles),
+           "m2l_pairs": sum(int(f.stats()["n_m2l_pairs"]) for f in b.handles),
+           "m2l_pairs_across_levels": sum(int(f.stats()["n_m2l_irregular"]) for f in b.handles)}
     # the M2L tile shape: levels with at most `pool` cells pool their 8
     # octants' tiles; the engine timed with other thresholds (same leaf sizes)
     sweep = {"512 (default)": t_engine}
