@@ -75,19 +75,56 @@ def assign_streams(sizes, nstreams):
     return lane
 
 
-def tune_buckets(systems, p, theta, precision, candidates=NCRIT_CANDIDATES, nstreams=8, per_bucket=8):
-    """ncrit per size bucket (half a decade of n): the candidate that
-    evaluates up to per_bucket members of the bucket (spread over its sizes),
-    side by side on nstreams streams, in the least time.
+def _engine_ms(members, p, theta, ncrit, precision, m2l_pool, reps=5):
+    """Device time of one batch-engine evaluation of the given systems (best
+    of reps)."""
+    hs, outs = [], []
+    for x, q in members:
+        f = FMM(x.shape[0], p=p, theta=theta, ncrit=ncrit, precision=precision, overlap=False, m2l_pool=m2l_pool)
+        f.build(x, q)
+        hs.append(f)
+        outs.append(f.evaluate())
+    torch.cuda.synchronize()
+    n = len(hs)
+    b = _vp()
+    _check(lib().fmm_batch_create((_vp * n)(*[f._h for f in hs]), n, (_vp * n)(*[o[0].data_ptr() for o in outs]),
+                                  (_vp * n)(*[o[1].data_ptr() for o in outs]), ctypes.byref(b)))
+    best = float("inf")
+    try:
+        for _ in range(reps + 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            _check(lib().fmm_batch_evaluate(b, _stream_ptr()))
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+    finally:
+        lib().fmm_batch_destroy(b)
+        for f in hs:
+            f.close()
+    return best
+
+
+def tune_buckets(systems, p, theta, precision, candidates=NCRIT_CANDIDATES, nstreams=8, per_bucket=8, engine=False,
+                 m2l_pool=-1):
+    """ncrit per size bucket (half a decade of n). Per-system launches
+    (engine=False): the candidate that evaluates up to per_bucket members of
+    the bucket (spread over its sizes), side by side on nstreams streams, in
+    the least time. Batch engine (engine=True): the candidate whose engine
+    evaluation of up to 16 per_bucket members takes the least device time.
     Returns ({bucket: ncrit}, bucket of each system)."""
     bucket = [size_bucket(x.shape[0]) for x, _ in systems]
     streams = [torch.cuda.Stream() for _ in range(nstreams)]
     choice = {}
     for b in sorted(set(bucket)):
         members = sorted((i for i in range(len(systems)) if bucket[i] == b), key=lambda i: systems[i][0].shape[0])
-        k = min(per_bucket, len(members))
+        k = min(16 * per_bucket if engine else per_bucket, len(members))
         pick = [systems[members[(j * (len(members) - 1)) // max(k - 1, 1)]] for j in range(k)]
-        ms = {nc: _throughput_ms(pick, p, theta, nc, precision, streams) for nc in candidates}
+        if engine:
+            ms = {nc: _engine_ms(pick, p, theta, nc, precision, m2l_pool) for nc in candidates}
+        else:
+            ms = {nc: _throughput_ms(pick, p, theta, nc, precision, streams) for nc in candidates}
         choice[b] = min(ms, key=lambda k: (ms[k], k))
     return choice, bucket
 
@@ -105,7 +142,8 @@ class FMMBatch:
         self.mode = mode
         self.handles, self.out = [], []
         if ncrit == "auto":
-            self.ncrit_by_bucket, bucket = tune_buckets(systems, p, theta, precision, nstreams=max(1, int(streams)))
+            self.ncrit_by_bucket, bucket = tune_buckets(systems, p, theta, precision, nstreams=max(1, int(streams)),
+                                                        engine=mode == "persistent", m2l_pool=m2l_pool)
             per = [self.ncrit_by_bucket[b] for b in bucket]
         elif isinstance(ncrit, dict):
             self.ncrit_by_bucket = dict(ncrit)
