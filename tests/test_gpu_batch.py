@@ -149,3 +149,29 @@ def test_withheld_item_times_out_with_error_status(pass_, kinds):
     assert b.status()[0] == 0
     assert_same(b, ref)
     b.close()
+
+
+def test_batch_engine_tiny_and_shallow_systems():
+    # systems whose trees stop at the root (one particle, two, a handful), at
+    # level 1 or 2, next to deeper ones: work lists without M2M, L2L or M2L
+    # items, leaves padded to even counts, and the result still bitwise that
+    # of each system's own evaluation
+    torch = torch_cuda()
+    ensure_built()
+    from paper_1106_2176_gb300.batch import FMMBatch
+    rng = np.random.default_rng(23)
+    systems = []
+    for k, n in enumerate([1, 2, 7, 64, 65, 500, 3000, 1, 20000]):
+        x = inputs.uniform_cube(n, 700 + k)[0] if k % 2 == 0 else inputs.plummer(n, 700 + k)[0]
+        q = rng.uniform(-1, 1, n)
+        systems.append((torch.tensor(x.astype(np.float32), device="cuda"), torch.tensor(q.astype(np.float32), device="cuda")))
+    b = FMMBatch(systems, p=6, theta=0.5, ncrit=64, precision="mixed")
+    ref = [(x.clone(), y.clone()) for x, y in b.evaluate_each()]
+    clear(torch, b)
+    b.evaluate()
+    torch.cuda.synchronize()
+    assert b.status()[0] == 0
+    assert_same(b, ref)
+    # a single particle feels nothing
+    assert float(b.out[0][0][0]) == 0.0 and torch.all(b.out[0][1] == 0)
+    b.close()
