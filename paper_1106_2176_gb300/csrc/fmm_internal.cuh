@@ -355,6 +355,21 @@ __host__ __device__ inline uint64_t morton3(uint32_t x, uint32_t y, uint32_t z)
     return spread3(x) | (spread3(y) << 1) | (spread3(z) << 2);
 }
 
+// The same interleave for coordinates below 2^10 (levels <= 10), in 32-bit
+// arithmetic.
+__host__ __device__ inline uint32_t morton3_10(uint32_t x, uint32_t y, uint32_t z)
+{
+    auto sp = [](uint32_t v) {
+        v &= 0x3ffu;
+        v = (v | (v << 16)) & 0x030000ffu;
+        v = (v | (v << 8)) & 0x0300f00fu;
+        v = (v | (v << 4)) & 0x030c30c3u;
+        v = (v | (v << 2)) & 0x09249249u;
+        return v;
+    };
+    return sp(x) | (sp(y) << 1) | (sp(z) << 2);
+}
+
 // Cell at lattice position (x, y, z) of level l, or -1.
 __device__ inline int level_lookup(const LevelDesc &L, const int *__restrict__ map_pool,
                                    const uint64_t *__restrict__ anchor, int l, int x, int y, int z)

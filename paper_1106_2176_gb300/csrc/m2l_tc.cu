@@ -366,6 +366,7 @@ __global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
         const int nown = nunits > g ? (nunits - g + 1) / 2 : 0;  // units u = g, g + 2, ... of this group
         int *myring = ring + g * RINGU * C::M;
         const bool dense = LD.map_off >= 0;  // the level has a lattice map: lookups arrive by cp.async
+        const bool full = rl <= 10 && LD.end - LD.start == (1 << (3 * rl));  // every lattice cell present
 
         // source cell of this row for the group's unit j, looked up QU units
         // ahead into ring slot j % RINGU (cp.async of the lattice-map entry, or
@@ -387,6 +388,12 @@ __global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
             if (cell >= 0) {
                 const int x = px + v.x, y = py + v.y, z = pz + v.z, side = 1 << rl;
                 if (((v.w >> (16 + ro)) & 1) && x >= 0 && y >= 0 && z >= 0 && x < side && y < side && z < side) {
+                    // a complete level holds every lattice cell in Morton order:
+                    // the index follows from the position
+                    if (full) {
+                        myring[(j % RINGU) * C::M + row] = LD.start + (int)morton3_10((uint32_t)x, (uint32_t)y, (uint32_t)z);
+                        return;
+                    }
                     if (dense) {
                         cp_async4(slot, map_pool + LD.map_off + (long long)morton3((uint32_t)x, (uint32_t)y, (uint32_t)z));
                         return;
@@ -394,7 +401,7 @@ __global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
                     r = level_lookup(LD, map_pool, anchor, rl, x, y, z);
                 }
             }
-            if (dense) cp_async4(slot, &g_no_cell);
+            if (dense && !full) cp_async4(slot, &g_no_cell);
             else myring[(j % RINGU) * C::M + row] = r;
         };
         // copy the group's unit j into its raw stage j % RSG. The warp fills
