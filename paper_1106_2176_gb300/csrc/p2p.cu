@@ -95,7 +95,7 @@ constexpr int P2P_T = FMM_P2P_T;  // threads per block (one target leaf)
 #define FMM_P2P_TPT 2
 #endif
 #ifndef FMM_P2P_MINB
-#define FMM_P2P_MINB 7
+#define FMM_P2P_MINB 6
 #endif
 // sources per shared-memory chunk of the FP32-input path, and the number of
 // chunk buffers (2: the next chunk is copied while the current one is
