@@ -245,25 +245,36 @@ __device__ __forceinline__ void p2m_leaf_warp(int c, int lane, const int *__rest
         const double4_32a pt = rel_pt(xs, j, cen);
         p2m_accum<P, float>((float)(pt.x * iw), (float)(pt.y * iw), (float)(pt.z * iw), (float)pt.w, are, aim);
     }
+    // sum over the 32 lanes by recursive halving: the 2 NT values (padded to
+    // VP, a multiple of 32) are split in two at every step, each lane keeping
+    // the half its lane bit selects and adding its partner's copy of that
+    // half, so that lane l ends with the sums of values [l W, (l + 1) W)
+    constexpr int VP = (2 * NT + 31) / 32 * 32, W = VP / 32;
+    float v[VP];
 #pragma unroll
-    for (int k = 0; k < NT; k++) {
+    for (int i = 0; i < VP; i++) v[i] = i < NT ? are[i] : (i < 2 * NT ? aim[i - NT] : 0.f);
 #pragma unroll
-        for (int o = 16; o; o >>= 1) {
-            are[k] += __shfl_xor_sync(0xffffffffu, are[k], o);
-            aim[k] += __shfl_xor_sync(0xffffffffu, aim[k], o);
+    for (int o = 16, h = VP / 2; o; o >>= 1, h >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < h; i++) {
+            const float keep = up ? v[i + h] : v[i], send = up ? v[i] : v[i + h];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
         }
     }
     float *Mc = M + (size_t)c * (P * P);
 #pragma unroll
-    for (int n = 0; n < P; n++)
-#pragma unroll
-        for (int m = 0; m <= n; m++) {
-            const int k = tri(n, m);
-            if (lane == (k & 31)) {
-                Mc[re_idx(n, m)] = are[k];
-                if (m) Mc[im_idx(n, m)] = aim[k];
-            }
+    for (int t = 0; t < W; t++) {
+        const int i = lane * W + t;
+        if (i < 2 * NT) {
+            const int k = i < NT ? i : i - NT;
+            int n = 0;
+            while ((n + 1) * (n + 2) / 2 <= k) n++;
+            const int m = k - n * (n + 1) / 2;
+            if (i < NT) Mc[re_idx(n, m)] = v[t];
+            else if (m) Mc[im_idx(n, m)] = v[t];
         }
+    }
 }
 
 template <int P, class P4>
