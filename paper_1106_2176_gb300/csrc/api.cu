@@ -97,7 +97,7 @@ fmm_ctx::~fmm_ctx()
                            &idx2, &hist, &scan_tmp, &xs64, &xs32, &xs32lo, &c_level, &c_anchor, &c_begin, &c_end, &c_child,
                            &c_nchild, &c_parent, &c_xyz, &split_cnt, &split_off, &split_bnd, &leaves, &frontA,
                            &frontB, &p2p_pairs, &m2lx_pairs, &near_dev, &pair_keys, &pair_keys2, &pair_vals, &pair_vals2,
-                           &p2p_ptr, &p2p_src, &p2p_runs, &p2p_nrun, &pr_pad, &pr_flag, &pr_pairs, &p2p_runs_pr, &m2lx_ptr, &m2lx_src, &row_cnt, &counters, &lvl_desc, &map_pool,
+                           &p2p_ptr, &p2p_src, &p2p_runs, &p2p_nrun, &pr_pad, &pr_flag, &pr_pairs, &p2p_runs_pr, &m2lx_ptr, &m2lx_src, &row_cnt, &counters, &lvl_desc, &map_pool, &hash_pool,
                            &m2l_tgt, &m2l_tiles, &m2l_misc, &msplit, &Mexp, &Lexp, &far, &near, &out_phi, &out_grad,
                            &direct_part, &rot_tab};
     for (auto *b : bufs) b->release();

@@ -85,10 +85,20 @@ struct Box {
     int pad;
 };
 
+// open-addressed table slot: Morton index of a cell at its level plus one
+// (0: empty), and the cell
+struct HashSlot {
+    unsigned long long key;
+    int val, pad;
+};
+
 // per-level lookup from lattice position to cell index (M2L stencil)
 struct LevelDesc {
-    int start, end;      // cell index range of the level
-    long long map_off;   // offset of a dense map (8^l int32) in the map pool, or -1
+    int start, end;         // cell index range of the level
+    long long map_off;      // offset of a dense map (8^l int32) in the map pool, or -1
+    const HashSlot *hash;   // levels without a dense map: a table of at least twice their cells, or null
+    unsigned hash_mask;     // table size - 1 (a power of two)
+    int pad;
 };
 
 // M2L tile: up to TILE target cells of one level and one octant, or (octant
@@ -242,7 +252,7 @@ struct fmm_ctx {
     fmm::DevBuf pr_pad, pr_flag, pr_pairs, p2p_runs_pr;
     bool pr_ready = false;
     fmm::DevBuf counters;
-    fmm::DevBuf lvl_desc, map_pool;
+    fmm::DevBuf lvl_desc, map_pool, hash_pool;
     fmm::DevBuf m2l_tgt, m2l_tiles, m2l_misc;
     fmm::DevBuf Mexp, Lexp;
     fmm::DevBuf far, near;
@@ -370,6 +380,12 @@ __host__ __device__ inline uint32_t morton3_10(uint32_t x, uint32_t y, uint32_t 
     return sp(x) | (sp(y) << 1) | (sp(z) << 2);
 }
 
+// slot of a key in a table of hash_mask + 1 slots (multiplicative hashing)
+__host__ __device__ inline unsigned level_hash(unsigned long long key, unsigned mask)
+{
+    return (unsigned)((key * 0x9E3779B97F4A7C15ull) >> 32) & mask;
+}
+
 // Cell at lattice position (x, y, z) of level l, or -1.
 __device__ inline int level_lookup(const LevelDesc &L, const int *__restrict__ map_pool,
                                    const uint64_t *__restrict__ anchor, int l, int x, int y, int z)
@@ -378,6 +394,17 @@ __device__ inline int level_lookup(const LevelDesc &L, const int *__restrict__ m
     if (x < 0 || y < 0 || z < 0 || x >= side || y >= side || z >= side) return -1;
     const uint64_t k = morton3((uint32_t)x, (uint32_t)y, (uint32_t)z);
     if (L.map_off >= 0) return map_pool[L.map_off + (long long)k];
+    if (L.hash) {
+        // linear probing from the key's hash; the table is at most half full
+        const unsigned long long key = k + 1;
+        unsigned hs = level_hash(key, L.hash_mask);
+        for (unsigned i = 0; i <= L.hash_mask; i++, hs = (hs + 1) & L.hash_mask) {
+            const unsigned long long kk = L.hash[hs].key;
+            if (kk == key) return L.hash[hs].val;
+            if (kk == 0) return -1;
+        }
+        return -1;
+    }
     const uint64_t a = k << (3 * (FMM_MAXLEVEL - l));
     int lo = L.start, hi = L.end;
     while (lo < hi) {

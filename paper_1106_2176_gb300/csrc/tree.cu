@@ -880,6 +880,24 @@ __global__ void map_fill_k(int ls, int le, int l, const uint64_t *__restrict__ a
     map[anchor[c] >> (3 * (FMM_MAXLEVEL - l))] = c;
 }
 
+// the cells of a level without a dense map into its open-addressed table
+// (linear probing; at most half full, so every insertion finds a slot)
+__global__ void hash_fill_k(int ls, int le, int l, const uint64_t *__restrict__ anchor, HashSlot *__restrict__ tab,
+                            unsigned mask)
+{
+    int c = ls + blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= le) return;
+    const unsigned long long key = (anchor[c] >> (3 * (FMM_MAXLEVEL - l))) + 1ull;
+    unsigned hs = level_hash(key, mask);
+    for (unsigned i = 0; i <= mask; i++, hs = (hs + 1) & mask) {
+        const unsigned long long prev = atomicCAS(&tab[hs].key, 0ull, key);
+        if (prev == 0ull || prev == key) {
+            tab[hs].val = c;
+            return;
+        }
+    }
+}
+
 __global__ void oct_count_k(int c0, int nc, const int *__restrict__ level, const uint64_t *__restrict__ anchor,
                             unsigned *__restrict__ grp)
 {
@@ -1362,6 +1380,33 @@ void tree_build(fmm_ctx *h, const void *x, const void *q, int64_t n, int dt)
             map_fill_k<<<nblocks(m, TB), TB, 0, s>>>(ld[l].start, ld[l].end, l, h->c_anchor.as<uint64_t>(),
                                                      h->map_pool.as<int>() + ld[l].map_off);
             count_launch(h);
+        }
+        // deeper levels: hash tables of at least twice their cells
+        std::vector<long long> hoff(FMM_MAXLEVEL + 1, -1);
+        long long hpool = 0;
+        for (int l = FMM_DENSE_MAP_MAXLEVEL + 1; l <= depth; l++) {
+            const long long m = ld[l].end - ld[l].start;
+            ld[l].hash = nullptr;
+            ld[l].hash_mask = 0;
+            if (m == 0) continue;
+            long long t = 64;
+            while (t < 2 * m) t <<= 1;
+            hoff[l] = hpool;
+            ld[l].hash_mask = (unsigned)(t - 1);
+            hpool += t;
+        }
+        if (hpool > 0) {
+            h->hash_pool.ensure(sizeof(HashSlot) * (size_t)hpool);
+            FMM_CUDA_TRY(cudaMemsetAsync(h->hash_pool.p, 0, sizeof(HashSlot) * (size_t)hpool, s));
+            for (int l = FMM_DENSE_MAP_MAXLEVEL + 1; l <= depth; l++) {
+                if (hoff[l] < 0) continue;
+                HashSlot *tab = h->hash_pool.as<HashSlot>() + hoff[l];
+                ld[l].hash = tab;
+                const int m = ld[l].end - ld[l].start;
+                hash_fill_k<<<nblocks(m, TB), TB, 0, s>>>(ld[l].start, ld[l].end, l, h->c_anchor.as<uint64_t>(), tab,
+                                                          ld[l].hash_mask);
+                count_launch(h);
+            }
         }
         h->lvl_desc.ensure(sizeof(LevelDesc) * ld.size());
         LevelDesc *hp = reinterpret_cast<LevelDesc *>(h->hpin.as<char>() + 1024);
