@@ -249,3 +249,21 @@ def test_m2l_tile_pooling_keeps_the_error_bound(pool, gen):
     assert fm.stats()["async_error"] == 0
     assert rel(p64[t], pd) < 1e-4 and rel(g64[t], gd) < 1e-4
     assert rel(pm[t], pd) <= rel(p64[t], pd) + MIXED_SLACK and rel(gm[t], gd) <= rel(g64[t], gd) + MIXED_SLACK
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_deep_adaptive_tree_against_oracle(precision):
+    # a clustered input with small leaves reaches levels deeper than the dense
+    # lattice maps (8): the M2L sources there come from the per-level hash
+    # tables; FP64 to 1e-12 of the oracle FMM, mixed within the FP64 FMM's
+    # error plus 2e-6 against the direct sum
+    x, q = inputs.plummer(20000, 43)
+    phi, grad, f = run_fmm(x, q, 6, 0.5, 4, precision=precision)
+    assert f.stats()["depth"] >= 10 and f.stats()["async_error"] == 0
+    if precision == "fp64":
+        po, go = oracle.fmm(x, q, 6, 0.5, 4)
+        assert rel(phi, po) <= FP64_TOL and rel(grad, go) <= FP64_TOL
+    else:
+        pd, gd = oracle.direct(x, q)
+        p64, g64, _ = run_fmm(x, q, 6, 0.5, 4, precision="fp64")
+        assert rel(phi, pd) <= rel(p64, pd) + MIXED_SLACK and rel(grad, gd) <= rel(g64, gd) + MIXED_SLACK
