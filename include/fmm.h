@@ -100,7 +100,7 @@ typedef struct {
     double ms_p2m, ms_m2m, ms_m2l, ms_l2l, ms_l2p, ms_p2p, ms_combine;
     int64_t kernel_launches; /* kernels this handle launched since creation */
     int32_t uniform_path;    /* 1 if the last build took the full-octree fast path */
-    int32_t reserved;
+    int32_t lattice_levels;  /* bit l: level l's M2L sources come by TMA tile loads (fmm_set_m2l_lattice) */
 } fmm_stats;
 
 /* Sizes of the arrays fmm_export_tree writes. */
@@ -166,6 +166,21 @@ FMM_API int fmm_set_uniform_path(fmm_handle h, int on);
  * next build. Returns FMM_EINVAL for a NULL handle or max_cells < -1.
  */
 FMM_API int fmm_set_m2l_pool(fmm_handle h, int max_cells);
+
+/*
+ * Sources of the tensor-core M2L on complete levels (Sec. 2.2: every box of a
+ * level present, boxes indexed by lattice position). on = 1 (default): on a
+ * complete level with at least 8^4 cells (above the pooling threshold, at
+ * most level 9) each evaluation first copies the level's M~ into lattice
+ * order (octant bits, then z, y, x of the halved position), and the kernel
+ * brings a tile's sources for one translation as TMA tile loads of a shifted
+ * block, positions outside the level as zeros; no per-row lookups or row
+ * gathers. on = 0: per-row lookups and gathers on every level. The results
+ * are bitwise the same. Takes effect at the next build; fmm_stats
+ * .lattice_levels says which levels the last build set up (bit l: level l).
+ * Returns FMM_EINVAL for a NULL handle or on not 0/1.
+ */
+FMM_API int fmm_set_m2l_lattice(fmm_handle h, int on);
 
 /* Use the given cudaStream_t (NULL = legacy default stream) for all work. */
 FMM_API int fmm_set_stream(fmm_handle h, void *stream);

@@ -99,9 +99,10 @@ fmm_ctx::~fmm_ctx()
                            &frontB, &p2p_pairs, &m2lx_pairs, &near_dev, &pair_keys, &pair_keys2, &pair_vals, &pair_vals2,
                            &p2p_ptr, &p2p_src, &p2p_runs, &p2p_nrun, &pr_pad, &pr_flag, &pr_pairs, &p2p_runs_pr, &m2lx_ptr, &m2lx_src, &row_cnt, &counters, &lvl_desc, &map_pool, &hash_pool,
                            &m2l_tgt, &m2l_tiles, &m2l_misc, &msplit, &Mexp, &Lexp, &far, &near, &out_phi, &out_grad,
-                           &direct_part, &rot_tab};
+                           &direct_part, &rot_tab, &mlat, &lat_maps};
     for (auto *b : bufs) b->release();
     hpin.release();
+    lat_host.release();
     for (auto &t : tms)
         for (auto &e : t.ev)
             if (e) cudaEventDestroy(e);
@@ -308,6 +309,14 @@ int fmm_set_m2l_pool(fmm_handle h, int max_cells)
     return FMM_OK;
 }
 
+int fmm_set_m2l_lattice(fmm_handle h, int on)
+{
+    if (!h) return fail(FMM_EINVAL, "fmm_set_m2l_lattice: NULL handle");
+    if (on != 0 && on != 1) return fail(FMM_EINVAL, "fmm_set_m2l_lattice: on must be 0 or 1");
+    h->lattice_req = on != 0;
+    return FMM_OK;
+}
+
 int fmm_set_stream(fmm_handle h, void *stream)
 {
     if (!h) return fail(FMM_EINVAL, "fmm_set_stream: NULL handle");
@@ -493,6 +502,7 @@ int fmm_get_stats(fmm_handle h, fmm_stats *out)
     }
     out->kernel_launches = h->launches;
     out->uniform_path = h->uniform_used ? 1 : 0;
+    out->lattice_levels = (int32_t)h->lat_levels;
     phase_means(h, 1, out);
     return FMM_OK;
     API_END

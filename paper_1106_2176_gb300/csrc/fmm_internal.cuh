@@ -126,6 +126,10 @@ struct M2LJob {
     const float *mrow;
     const unsigned char *ttab;
     float *L;
+    // complete levels whose sources come by TMA tile loads from the lattice
+    // copy of M~ (bit l: level l); lat_maps holds a 128-byte tensor map per level
+    const unsigned char *lat_maps;
+    unsigned lat_levels;
     int item0;
     int count;
 };
@@ -226,6 +230,14 @@ struct fmm_ctx {
     fmm::DevBuf rot_tab;        // rotation M2L maps per vector ([A | B], FP32 or FP64)
     int rot_nv = -1, rot_kind = 0;  // vectors and precision (1 FP32, 2 FP64) of rot_tab
     fmm::DevBuf msplit;         // M~ split into TF32 (hi, lo) rows for the tensor-core M2L
+    // tensor-core M2L on complete levels: M~ of each such level in lattice
+    // order (octant bits, then z, y, x of the halved position), one TMA tensor
+    // map per level (device copy and its pinned staging)
+    bool lattice_req = true;    // fmm_set_m2l_lattice
+    unsigned lat_levels = 0;    // bit l: level l reads its sources from the lattice copy
+    long long lat_off[FMM_MAXLEVEL + 1] = {};  // float offset of level l in mlat
+    fmm::DevBuf mlat, lat_maps;
+    fmm::PinnedBuf lat_host;
 
     // workspaces
     fmm::DevBuf box;
@@ -326,6 +338,9 @@ void m2l_tensor(fmm_ctx *h, float *L, const float *M);
 // whole k-blocks where p^2 is not a multiple of 32) in one persistent launch
 void m2l_tensor_jobs(int p, int nsm, const M2LJob *jobs_dev, int njobs, int *queue, int *err, cudaStream_t s);
 M2LJob m2l_tensor_job(fmm_ctx *h, float *L, const float *M, cudaStream_t s);  // pads M if needed
+// (build) which complete levels the tensor-core M2L reads through TMA tile
+// loads: their lattice buffer and tensor maps
+void lattice_prepare(fmm_ctx *h, cudaStream_t s);
 void batch_mpad(int p, const BatchSys *sys, int nsys, cudaStream_t s);  // every system's padded M rows
 
 // p2p.cu

@@ -46,6 +46,8 @@
 #include <mutex>
 #include <tuple>
 
+#include <cuda.h>  // CUtensorMap and its encoding enums (the encoder comes from the runtime's driver entry point)
+
 #include "fmm_internal.cuh"
 #include "ptx_sm100.cuh"
 
@@ -105,13 +107,14 @@ struct TcCfg {
     static constexpr int OPV = KB * B_RAW;         // operator bytes of one vector
     static constexpr int VR = 8;
     static constexpr int RSG_V = 2;
-    static constexpr int OSV_FIT = (220 * 1024 - RING - 512 - 1024 - NG * RSG_V * A_RAW) / OPV;
+    static constexpr int BAR = 768;                // mbarriers (first 512 bytes), then the CTA's job
+    static constexpr int OSV_FIT = (220 * 1024 - RING - BAR - 1024 - NG * RSG_V * A_RAW) / OPV;
     static constexpr int OSV = OSV_FIT > 6 ? 6 : OSV_FIT;
-    static constexpr int BUDGET = 220 * 1024 - RING - 512 - 1024 - CS * B_RAW;
+    static constexpr int BUDGET = 220 * 1024 - RING - BAR - 1024 - CS * B_RAW;
     static constexpr int RSG_U = BUDGET / (NG * A_RAW) >= 3 ? 3 : BUDGET / (NG * A_RAW);
     static constexpr int RSG = VEC ? RSG_V : RSG_U;  // raw stages per group
     static constexpr int OPB = VEC ? OSV * OPV : CS * B_RAW;  // operator bytes in shared memory
-    static constexpr int SMEM = NG * RSG * A_RAW + OPB + RING + 512 + 1024;
+    static constexpr int SMEM = NG * RSG * A_RAW + OPB + RING + BAR + 1024;
     static_assert(!VEC || (OSV >= 2 && OSV <= VR), "operator ring");
     static_assert(RSG >= 2 && RSG <= 3 && CS >= 2 && CS >= KB && QU >= RSG && ACC_COLS + CS * ACOLS <= TCOLS &&
                       SMEM <= 227 * 1024,
@@ -129,6 +132,27 @@ __global__ void mpad_k(const float *__restrict__ M, int PP, int KP, int c0, int 
     if (i >= (int64_t)(nc - c0) * KP) return;
     const int c = c0 + (int)(i / KP), k = (int)(i % KP);
     out[(size_t)c * KP + k] = k < PP ? M[(size_t)c * PP + k] : 0.f;
+}
+
+// Lattice copy of a complete level's M~ for the TMA tile loads of the
+// tensor-core M2L: the row of the cell at lattice position (x, y, z) goes to
+// ((b H + z/2) H + y/2) H + x/2, b = (x & 1) | (y & 1) << 1 | (z & 1) << 2 its
+// octant bits and H = 2^(l-1), zero-padded to KP coefficients. The cells of
+// one octant then form an H^3 block in x, y, z order, so the sources of a
+// block of targets under one translation are a shifted block.
+__global__ void lattice_fill_k(const float *__restrict__ M, int PP, int KP, const int4 *__restrict__ xyz, int c0, int c1,
+                               int l, float *__restrict__ out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)(c1 - c0) * KP) return;
+    const int c = c0 + (int)(i / KP), k = (int)(i % KP);
+    const int4 a = xyz[c];
+    const int sh = FMM_MAXLEVEL - l;
+    const int64_t H = 1ll << (l - 1);
+    const int x = a.x >> sh, y = a.y >> sh, z = a.z >> sh;
+    const int b = (x & 1) | ((y & 1) << 1) | ((z & 1) << 2);
+    const int64_t r = ((b * H + (z >> 1)) * H + (y >> 1)) * H + (x >> 1);
+    out[r * KP + k] = k < PP ? M[(size_t)c * PP + k] : 0.f;
 }
 
 template <int NP, int KB, bool PERSIST>
@@ -160,11 +184,13 @@ __global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
     uint64_t *acc_empty = acc_full + AC;      // AC: one arrival per worker warp after a drain
     uint64_t *fin = acc_empty + AC;           // 1
     uint64_t *ready = fin + 1;                // VEC, VR: vector w ready (its KB units split, its operator landed)
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(ready + C::VR);
+    uint64_t *a_lat = ready + C::VR;          // NG x RSG x 4: TMA tile loads of one warp's 32 rows (lattice tiles)
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(a_lat + NG * RSG * 4);
     int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
     int *s_tile = abort_flag + 1;                 // this CTA's current tile (-1: none left)
-    M2LJob *s_job = reinterpret_cast<M2LJob *>(reinterpret_cast<unsigned char *>(bar) + 384);  // its job
-    static_assert(sizeof(uint64_t) * (6 + 6 + 4 + 8 + 2 + 2 + 1 + 8) + 16 <= 384 && 384 + sizeof(M2LJob) <= 512,
+    M2LJob *s_job = reinterpret_cast<M2LJob *>(reinterpret_cast<unsigned char *>(bar) + 512);  // its job
+    static_assert(sizeof(uint64_t) * (NG * RSG + NB + CS + NF + 2 * AC + 1 + C::VR + NG * RSG * 4) + 16 <= 512 &&
+                      512 + sizeof(M2LJob) <= C::BAR,
                   "barrier area");
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -210,6 +236,7 @@ __global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
         // per vector: one arrival per warp of the groups that split its KB
         // units, and one from the operator warp once the operator landed
         for (int s = 0; s < C::VR; s++) mbar_init(&ready[s], 4 * KB + 1);
+        for (int s = 0; s < NG * RSG * 4; s++) mbar_init(&a_lat[s], 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -367,6 +394,19 @@ __global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
         int *myring = ring + g * RINGU * C::M;
         const bool dense = LD.map_off >= 0;  // the level has a lattice map: lookups arrive by cp.async
         const bool full = rl <= 10 && LD.end - LD.start == (1 << (3 * rl));  // every lattice cell present
+        // Lattice tile (a complete level with a lattice copy of M~): the tile
+        // is an 8 x 4 x 4 block of its octant's sub-lattice with rows in x, y,
+        // z order, and for every vector the sources form the same block
+        // shifted, in the sub-lattice of the source octant. Each warp brings
+        // its 32 rows (one z slice) with one TMA tile load; positions outside
+        // the level arrive as zeros, like absent cells.
+        const bool lat = J.lat_maps != nullptr && td.octant < 8 && ((J.lat_levels >> l) & 1u);
+        const int q = warp & 3;
+        const int obx = td.octant & 1, oby = (td.octant >> 1) & 1, obz = (td.octant >> 2) & 1;
+        // tile origin in halved coordinates (from row 32 q = (0, 0, q), this warp's lane 0)
+        const int ox = (px >> 1) - (row & 7), oy = (py >> 1) - ((row >> 3) & 3), oz = (pz >> 1) - (row >> 5);
+        const void *lmap = lat ? (const void *)(J.lat_maps + 128 * l) : nullptr;
+        int lat_issued = 0, lat_done = 0;  // this warp's TMA loads issued / waited for
 
         // source cell of this row for the group's unit j, looked up QU units
         // ahead into ring slot j % RINGU (cp.async of the lattice-map entry, or
@@ -377,7 +417,7 @@ __global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
         int4 st_next = make_int4(0, 0, 0, 0);
         int st_next_j = -1;
         auto fetch = [&](int j) {
-            if (j >= nown) return;
+            if (lat || j >= nown) return;
             const int4 v = st_next_j == j ? st_next : st[e0 + (2 * j + g) / KB];
             if (j + 1 < nown) {
                 st_next = st[e0 + (2 * (j + 1) + g) / KB];
@@ -411,6 +451,29 @@ __global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
         // that looked it up
         auto load_unit = [&](int j) {
             const int u = 2 * j + g, kb = u % KB;
+            if (lat) {
+                // the stencil entry of this call is loaded one call ahead (the
+                // lookahead registers of the lookups, which lattice tiles skip)
+                if (lane == 0) {
+                    const int4 v = st_next_j == j ? st_next : st[e0 + u / KB];
+                    if (j + 1 < nown) {
+                        st_next = st[e0 + (u + 2) / KB];
+                        st_next_j = j + 1;
+                    }
+                    // source octant bits and the block's shift in halved
+                    // coordinates (arithmetic shifts: floor division by 2)
+                    const int sx = obx + v.x, sy = oby + v.y, sz = obz + v.z;
+                    const int ps = (sx & 1) | ((sy & 1) << 1) | ((sz & 1) << 2);
+                    uint64_t *b = &a_lat[(g * RSG + j % RSG) * 4 + q];
+                    // the warp's generic reads of this stage precede the async-proxy writes
+                    fence_proxy_async();
+                    mbar_arrive_tx(b, 32 * 128);
+                    tma_load_5d(smem_u32(araw + (g * RSG + j % RSG) * C::A_RAW + q * 32 * 128), lmap, kb * 32,
+                                ox + (sx >> 1), oy + (sy >> 1), oz + q + (sz >> 1), ps, b);
+                }
+                lat_issued = j + 1;
+                return;
+            }
             const int src = myring[(j % RINGU) * C::M + row];
             fetch(j + QU);
             const uint32_t ab = smem_u32(araw + (g * RSG + j % RSG) * C::A_RAW);
@@ -471,14 +534,16 @@ __global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
             // the compute stage is free once the unit that used it last (u - CS)
             // is done: its vector's commit (VEC) or its own (otherwise)
             const int wprev = max(u - CS, 0) / KB;
-            const bool ok = VEC ? mbar_wait2(u >= CS ? 3u : 1u, &a_full[g * RSG + j % RSG], (uint32_t)((j / RSG) & 1),
+            uint64_t *araw_bar = lat ? &a_lat[(g * RSG + j % RSG) * 4 + q] : &a_full[g * RSG + j % RSG];
+            const bool ok = VEC ? mbar_wait2(u >= CS ? 3u : 1u, araw_bar, (uint32_t)((j / RSG) & 1),
                                              &cmp_free[wprev % NF], (uint32_t)((wprev / NF) & 1))
-                                : mbar_wait2(u >= CS ? 3u : 1u, &a_full[g * RSG + j % RSG], (uint32_t)((j / RSG) & 1),
+                                : mbar_wait2(u >= CS ? 3u : 1u, araw_bar, (uint32_t)((j / RSG) & 1),
                                              &cmp_free[c], (uint32_t)((max(u - CS, 0) / CS) & 1));
             if (!ok) {
                 atomicExch(abort_flag, 1);
                 break;
             }
+            lat_done = j + 1;
             tc_fence_after();
             // split this row's raw FP32 k-block into TF32 (hi, lo): hi rounded to
             // nearest, lo = a - hi (exact in FP32; the MMA reads its leading 11
@@ -519,6 +584,12 @@ __global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
             }
         }
         cp_async_wait_all();
+        // tile loads still in flight when the loop stopped early land before
+        // the shared memory is reused or released (bounded waits)
+        if (lat && lane == 0)
+            for (int jj = lat_done; jj < lat_issued; jj++)
+                mbar_wait(&a_lat[(g * RSG + jj % RSG) * 4 + q], (uint32_t)((jj / RSG) & 1));
+        __syncwarp();
         if (!*(volatile int *)abort_flag) {
             while (drained < ngroups) {
                 drain(drained);
@@ -781,9 +852,78 @@ M2LJob m2l_tensor_job(fmm_ctx *h, float *L, const float *M, cudaStream_t s)
     j.mrow = mrow;
     j.ttab = h->ttab.as<unsigned char>();
     j.L = L;
+    j.lat_maps = nullptr;  // gathers on every level (the single-system launch sets the lattice levels)
+    j.lat_levels = 0;
     j.item0 = 0;
     j.count = -1;
     return j;
+}
+
+// cuTensorMapEncodeTiled, looked up once through the runtime (no link
+// against the driver library)
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_tiled()
+{
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(f);
+    });
+    return fn;
+}
+
+// The complete levels whose tiles are lattice blocks (at least 8^4 cells,
+// more than the pooling threshold, so every tile is 128 cells of one octant)
+// read their sources by TMA from a lattice copy of M~: one 5-D tensor map per
+// level over [octant bits][z/2][y/2][x/2][KP coefficients] (FP32), box
+// 32 coefficients x 8 x 4 x 1 x 1 = one warp's 32 rows, 128-byte swizzle
+// (the layout of the gathered stages). Levels beyond 9 keep the gathers.
+void lattice_prepare(fmm_ctx *h, cudaStream_t s)
+{
+    h->lat_levels = 0;
+    if (!h->lattice_req || h->precision != FMM_MIXED || h->engine_used != FMM_M2L_TENSOR || !tensor_m2l_supported(h) ||
+        m2l_tile_size(h) != TcCfg<64, 2>::M)
+        return;
+    const EncodeTiledFn enc = encode_tiled();
+    if (!enc) return;
+    const int KP = tc_shape(h->p).KB * 32;
+    const int pool_max = h->m2l_pool >= 0 ? h->m2l_pool : 4 * m2l_tile_size(h);
+    unsigned levels = 0;
+    long long total = 0;
+    for (int l = 4; l <= std::min(h->depth, 9); l++) {
+        const long long cells = (long long)h->lvl_start[(size_t)l + 1] - h->lvl_start[(size_t)l];
+        if (cells != (1ll << (3 * l)) || cells <= pool_max) continue;
+        levels |= 1u << l;
+        h->lat_off[l] = total;
+        total += cells * KP;
+    }
+    if (!levels) return;
+    h->mlat.ensure(sizeof(float) * (size_t)total);
+    const size_t mbytes = sizeof(CUtensorMap) * (FMM_MAXLEVEL + 1);
+    h->lat_maps.ensure(mbytes);
+    h->lat_host.ensure(mbytes);
+    CUtensorMap *mp = h->lat_host.as<CUtensorMap>();
+    std::memset(mp, 0, mbytes);
+    for (int l = 4; l <= 9; l++) {
+        if (!((levels >> l) & 1u)) continue;
+        const cuuint64_t H = 1ull << (l - 1), row = sizeof(float) * (cuuint64_t)KP;
+        const cuuint64_t dims[5] = {(cuuint64_t)KP, H, H, H, 8};
+        const cuuint64_t strides[4] = {row, row * H, row * H * H, row * H * H * H};
+        const cuuint32_t box[5] = {32, 8, 4, 1, 1}, estride[5] = {1, 1, 1, 1, 1};
+        const CUresult r = enc(&mp[l], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, h->mlat.as<float>() + h->lat_off[l], dims,
+                               strides, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) throw Error{FMM_ECUDA, "tensor-core M2L: encoding a lattice tensor map failed"};
+    }
+    FMM_CUDA_TRY(cudaMemcpyAsync(h->lat_maps.p, mp, mbytes, cudaMemcpyHostToDevice, s));
+    h->lat_levels = levels;
 }
 
 __global__ void batch_mpad_k(int PP, int KP, const BatchSys *__restrict__ sys)
@@ -815,7 +955,19 @@ void m2l_tensor_jobs(int p, int nsm, const M2LJob *jobs_dev, int njobs, int *que
 void m2l_tensor(fmm_ctx *h, float *L, const float *M)
 {
     cudaStream_t s = h->work;
-    const M2LJob j = m2l_tensor_job(h, L, M, s);
+    M2LJob j = m2l_tensor_job(h, L, M, s);
+    if (h->lat_levels) {
+        const int PP = h->p * h->p, KP = tc_shape(h->p).KB * 32;
+        for (int l = 0; l <= FMM_MAXLEVEL; l++) {
+            if (!((h->lat_levels >> l) & 1u)) continue;
+            const int c0 = h->lvl_start[(size_t)l], c1 = h->lvl_start[(size_t)l + 1];
+            lattice_fill_k<<<nblk((int64_t)(c1 - c0) * KP, 256), 256, 0, s>>>(M, PP, KP, h->c_xyz.as<int4>(), c0, c1, l,
+                                                                            h->mlat.as<float>() + h->lat_off[l]);
+            count_launch(h);
+        }
+        j.lat_maps = h->lat_maps.as<unsigned char>();
+        j.lat_levels = h->lat_levels;
+    }
     int *misc = reinterpret_cast<int *>(h->m2l_misc.as<unsigned>() + 24 * (FMM_MAXLEVEL + 1));
     int *err = misc + 4, *queue = misc + 6;
     FMM_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));

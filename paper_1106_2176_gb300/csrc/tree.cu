@@ -975,12 +975,15 @@ __global__ void tiles_k(int depth, int tile, int pool_max, const unsigned *__res
 }
 
 // A complete (level, octant) group (all 8^(l-1) cells present) is placed in
-// the Morton order of its sub-lattice, so that every tile of it is a block of
-// 8 x 4 x 4 cells with row = Morton index - tile base (the tensor-core M2L
-// reuses source rows along x in such tiles); other groups in arrival order.
+// the Morton order of its sub-lattice, so that every 128 consecutive entries
+// are a block of 8 x 4 x 4 cells (x taking Morton bits 0, 3, 6, y 1, 4 and z
+// 2, 5 of the halved position). With raster set (tiles of 128 rows) the
+// entries inside each such block of a group of at least 512 cells are put in
+// x, y, z order, row = x + 8 y + 32 z, the order in which the tensor-core M2L
+// loads a shifted block of sources by TMA. Other groups in arrival order.
 __global__ void oct_scatter_k(int c0, int nc, const int *__restrict__ level, const uint64_t *__restrict__ anchor,
                               const unsigned *__restrict__ grp, const unsigned *__restrict__ goff,
-                              unsigned *__restrict__ fill, int *__restrict__ tgt)
+                              unsigned *__restrict__ fill, int raster, int *__restrict__ tgt)
 {
     int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= nc) return;
@@ -988,7 +991,15 @@ __global__ void oct_scatter_k(int c0, int nc, const int *__restrict__ level, con
     const uint64_t code = anchor[c] >> (3 * (FMM_MAXLEVEL - l));
     int o = (int)(code & 7u);
     const bool complete = l <= 10 && grp[l * 8 + o] == (1u << (3 * (l - 1)));
-    unsigned pos = goff[l * 8 + o] + (complete ? (unsigned)(code >> 3) : atomicAdd(&fill[l * 8 + o], 1u));
+    unsigned hm = (unsigned)(code >> 3);
+    if (complete && raster && l >= 4) {
+        const unsigned m = hm & 127u;
+        const unsigned x = (m & 1u) | ((m >> 2) & 2u) | ((m >> 4) & 4u);
+        const unsigned y = ((m >> 1) & 1u) | ((m >> 3) & 2u);
+        const unsigned z = ((m >> 2) & 1u) | ((m >> 4) & 2u);
+        hm = (hm & ~127u) | x | (y << 3) | (z << 5);
+    }
+    unsigned pos = goff[l * 8 + o] + (complete ? hm : atomicAdd(&fill[l * 8 + o], 1u));
     tgt[pos] = c;
 }
 
@@ -1438,10 +1449,11 @@ void tree_build(fmm_ctx *h, const void *x, const void *q, int64_t n, int dt)
         count_launch(h);
         if (nt > 0) {
             oct_scatter_k<<<nblocks(nt, TB), TB, 0, s>>>(c0, ncells, h->c_level.as<int>(), h->c_anchor.as<uint64_t>(),
-                                                         grp, goff, fill, h->m2l_tgt.as<int>());
+                                                         grp, goff, fill, tile == 128 ? 1 : 0, h->m2l_tgt.as<int>());
             count_launch(h);
         }
         check_launch("m2l tiles");
+        lattice_prepare(h, s);
     }
 }
 

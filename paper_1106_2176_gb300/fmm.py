@@ -47,7 +47,7 @@ class fmm_stats(ctypes.Structure):
                 ("ms_p2m", ctypes.c_double), ("ms_m2m", ctypes.c_double), ("ms_m2l", ctypes.c_double),
                 ("ms_l2l", ctypes.c_double), ("ms_l2p", ctypes.c_double), ("ms_p2p", ctypes.c_double),
                 ("ms_combine", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
-                ("uniform_path", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("uniform_path", ctypes.c_int32), ("lattice_levels", ctypes.c_int32)]
 
 
 class fmm_tree_sizes(ctypes.Structure):
@@ -79,6 +79,7 @@ def lib():
     L.fmm_set_m2l_engine.argtypes = [_vp, i32]
     L.fmm_set_overlap.argtypes = [_vp, i32]
     L.fmm_set_m2l_pool.argtypes = [_vp, i32]
+    L.fmm_set_m2l_lattice.argtypes = [_vp, ctypes.c_int]
     L.fmm_set_stream.argtypes = [_vp, _vp]
     L.fmm_set_uniform_path.argtypes = [_vp, ctypes.c_int]
     L.fmm_m2l_rotation_host.argtypes = [ctypes.c_int, _vp, _vp, _vp]
@@ -129,7 +130,7 @@ class FMM:
     """Handle of one FMM configuration (N, p, theta, ncrit) on the current GPU."""
 
     def __init__(self, N, p=8, theta=0.5, ncrit=64, precision="fp64", m2l_engine="auto", overlap=True,
-                 uniform_path=True, m2l_pool=-1):
+                 uniform_path=True, m2l_pool=-1, m2l_lattice=True):
         self._h = _vp()
         _check(lib().fmm_create(int(N), int(p), float(theta), int(ncrit), ctypes.byref(self._h)))
         self.N, self.p, self.theta, self.ncrit = int(N), int(p), float(theta), int(ncrit)
@@ -138,6 +139,7 @@ class FMM:
         self.set_overlap(overlap)
         self.set_uniform_path(uniform_path)
         self.set_m2l_pool(m2l_pool)
+        self.set_m2l_lattice(m2l_lattice)
         self._n = 0
         self._dtype = None
         self._host = False
@@ -168,6 +170,13 @@ class FMM:
         tiles (-1: the default, 4 tiles' worth; 0: never). Next build."""
         _check(lib().fmm_set_m2l_pool(self._h, int(max_cells)), self._h)
         self.m2l_pool = int(max_cells)
+
+    def set_m2l_lattice(self, on):
+        """True: the tensor-core M2L brings the sources of complete levels
+        (8^4 cells and more) by TMA tile loads from a lattice copy of M~;
+        False: per-row lookups and gathers everywhere. Same results. Next build."""
+        _check(lib().fmm_set_m2l_lattice(self._h, 1 if on else 0), self._h)
+        self.m2l_lattice = bool(on)
 
     # -- the two calls of the method ------------------------------------------
     def build(self, x, q):

@@ -29,14 +29,15 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-def run_fmm(x, q, p, theta, ncrit, precision="fp64", dtype=np.float64, engine="auto", m2l_pool=-1):
+def run_fmm(x, q, p, theta, ncrit, precision="fp64", dtype=np.float64, engine="auto", m2l_pool=-1, m2l_lattice=True):
     """FMM through the C ABI on device tensors; returns (phi, grad, handle)."""
     torch = torch_cuda()
     ensure_built()
     from paper_1106_2176_gb300 import FMM
     xt = torch.tensor(np.asarray(x, dtype=dtype), device="cuda")
     qt = torch.tensor(np.asarray(q, dtype=dtype), device="cuda")
-    f = FMM(len(q), p=p, theta=theta, ncrit=ncrit, precision=precision, m2l_engine=engine, m2l_pool=m2l_pool)
+    f = FMM(len(q), p=p, theta=theta, ncrit=ncrit, precision=precision, m2l_engine=engine, m2l_pool=m2l_pool,
+            m2l_lattice=m2l_lattice)
     f.build(xt, qt)
     phi, grad = f.evaluate()
     torch.cuda.synchronize()

@@ -89,3 +89,18 @@ def test_batch_entry_points_check_arguments(L):
 
 def test_m2l_pool_setter_checks_arguments(L):
     assert L.fmm_set_m2l_pool(None, 512) == fmm.FMM_EINVAL
+
+
+def test_m2l_lattice_setter_checks_arguments(L):
+    assert L.fmm_set_m2l_lattice(None, 1) == fmm.FMM_EINVAL
+    assert b"fmm_set_m2l_lattice" in L.fmm_last_error(None)
+
+
+def test_stats_layout_matches_the_header():
+    # the ctypes mirror of fmm_stats lists the header's fields in order
+    import re
+    hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "fmm.h")).read()
+    body = hdr[hdr.index("typedef struct {\n    int64_t n;  "):]
+    body = body[:body.index("} fmm_stats;")]
+    names = re.findall(r"\b(\w+)(?:\[\d+\])?\s*[;,]", re.sub(r"/\*.*?\*/", "", body, flags=re.S))
+    assert names == [f[0] for f in fmm.fmm_stats._fields_]
