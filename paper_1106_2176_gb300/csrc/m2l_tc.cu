@@ -400,7 +400,8 @@ __global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
         // shifted, in the sub-lattice of the source octant. Each warp brings
         // its 32 rows (one z slice) with one TMA tile load; positions outside
         // the level arrive as zeros, like absent cells.
-        const bool lat = J.lat_maps != nullptr && td.octant < 8 && ((J.lat_levels >> l) & 1u);
+        // (persistent launches serve the batch engine, which gathers everywhere)
+        const bool lat = !PERSIST && J.lat_maps != nullptr && td.octant < 8 && ((J.lat_levels >> l) & 1u);
         const int q = warp & 3;
         const int obx = td.octant & 1, oby = (td.octant >> 1) & 1, obz = (td.octant >> 2) & 1;
         // tile origin in halved coordinates (from row 32 q = (0, 0, q), this warp's lane 0)
