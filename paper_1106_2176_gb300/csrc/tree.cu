@@ -155,19 +155,59 @@ __global__ void box_init_k(Box *b)
     b->nonfinite = 0;
 }
 
+// FP32 -> FP64 without flushing subnormal inputs (the library is built with
+// flush-to-zero for its FP32 arithmetic; the box and the keys use every
+// input value exactly)
+__device__ __forceinline__ double f32_to_f64_exact(float v)
+{
+    double d;
+    asm("cvt.f64.f32 %0, %1;" : "=d"(d) : "f"(v));
+    return d;
+}
+__device__ __forceinline__ double to_f64_exact(float v) { return f32_to_f64_exact(v); }
+__device__ __forceinline__ double to_f64_exact(double v) { return v; }
+
 template <class T>
 __global__ void bbox_k(const T *__restrict__ x, int64_t n, Box *b)
 {
+    // FP32 input: each thread's extremes as order-preserving integer
+    // encodings of the float bits (exact, subnormals included, and off
+    // GB300's slow FP64 pipe), converted to FP64 once; FP64 input in FP64
     double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     int bad = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if constexpr (sizeof(T) == 4) {
+        // (no finite value encodes to 0xffffffff or to 0: the initial values mark "none seen")
+        unsigned elo[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, ehi[3] = {0u, 0u, 0u};
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
 #pragma unroll
-        for (int k = 0; k < 3; k++) {
-            double v = (double)x[3 * i + k];
-            if (!isfinite(v)) bad = 1;
-            else {
-                lo[k] = fmin(lo[k], v);
-                hi[k] = fmax(hi[k], v);
+            for (int k = 0; k < 3; k++) {
+                const unsigned u = __float_as_uint((float)x[3 * i + k]);
+                if ((u & 0x7f800000u) == 0x7f800000u) bad = 1;
+                else {
+                    const unsigned e = (u >> 31) ? ~u : (u | 0x80000000u);
+                    elo[k] = min(elo[k], e);
+                    ehi[k] = max(ehi[k], e);
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 3; k++)
+            if (elo[k] != 0xffffffffu) {
+                const unsigned a = (elo[k] >> 31) ? (elo[k] & 0x7fffffffu) : ~elo[k];
+                const unsigned c = (ehi[k] >> 31) ? (ehi[k] & 0x7fffffffu) : ~ehi[k];
+                lo[k] = f32_to_f64_exact(__uint_as_float(a));
+                hi[k] = f32_to_f64_exact(__uint_as_float(c));
+            }
+    } else {
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                const double v = (double)x[3 * i + k];
+                if (!isfinite(v)) bad = 1;
+                else {
+                    lo[k] = fmin(lo[k], v);
+                    hi[k] = fmax(hi[k], v);
+                }
             }
         }
     }
@@ -219,11 +259,12 @@ __global__ void keys_k(const T *__restrict__ x, int64_t n, const Box *__restrict
     uint32_t ic[3];
 #pragma unroll
     for (int k = 0; k < 3; k++) {
-        double v = (double)x[3 * i + k];
-        double f = floor(__dmul_rn(__dsub_rn(v, b->origin[k]), b->s));
-        f = f < 0.0 ? 0.0 : f;
-        f = f > 2097151.0 ? 2097151.0 : f;
-        ic[k] = (uint32_t)f;
+        const double v = to_f64_exact(x[3 * i + k]);
+        // floor to an integer in one conversion (saturating), clamped as an
+        // integer: the same value as floor, clamp and cast in FP64, with half
+        // the FP64 instructions
+        const int f = __double2int_rd(__dmul_rn(__dsub_rn(v, b->origin[k]), b->s));
+        ic[k] = (uint32_t)min(max(f, 0), 2097151);
     }
     keys[i] = morton3(ic[0], ic[1], ic[2]);
     idx[i] = (int)i;
@@ -407,8 +448,9 @@ __global__ void gather_k(const T *__restrict__ x, const T *__restrict__ q, const
     if (i >= n) return;
     int j = idx[i];
     inv[j] = (int)i;
-    double a = (double)x[3 * (int64_t)j], b = (double)x[3 * (int64_t)j + 1], c = (double)x[3 * (int64_t)j + 2];
-    double d = (double)q[j];
+    const double a = to_f64_exact(x[3 * (int64_t)j]), b = to_f64_exact(x[3 * (int64_t)j + 1]),
+                 c = to_f64_exact(x[3 * (int64_t)j + 2]);
+    const double d = to_f64_exact(q[j]);
     if (xs64) xs64[i] = make_double4_32a(a, b, c, d);
     if (xs32) {
         const float ha = (float)a, hb = (float)b, hc = (float)c;

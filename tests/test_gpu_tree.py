@@ -76,6 +76,21 @@ def test_float32_input_bit_exact():
     compare(x, q, 64, 0.5, dtype=np.float32)
 
 
+def test_float32_subnormal_and_signed_zero_coordinates_bit_exact():
+    # FP32 inputs whose coordinates are subnormal (below 2^-126), with +0 and
+    # -0 among them: the box and the keys take every value exactly, as the
+    # oracle does in FP64, although the library's FP32 arithmetic flushes
+    # subnormals to zero
+    rng = np.random.default_rng(12)
+    m = rng.integers(-(2 ** 22), 2 ** 22, size=(3000, 3)).astype(np.float64)
+    x = (m * 2.0 ** -149).astype(np.float32)
+    x[:5] = 0.0
+    x[5:10] = -0.0
+    assert np.all(np.abs(x[x != 0]) < np.float32(2.0 ** -126))
+    q = np.ones(3000, np.float32)
+    compare(x, q, 16, 0.5, dtype=np.float32)
+
+
 def test_ragged_sizes_span_several_sort_tiles():
     # 4096 keys per radix tile: sizes around tile edges
     for n in (4095, 4096, 4097, 12289):
