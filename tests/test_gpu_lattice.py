@@ -58,6 +58,19 @@ def test_lattice_loads_give_the_gathered_results_bitwise(P, gen, n, ncrit, level
     f0.close()
 
 
+def test_lattice_loads_with_float64_inputs():
+    # FP64 positions and charges on the mixed path (FP32 expansions): the
+    # lattice loads again give the gathered results bit for bit
+    x, q = inputs.uniform_cube(200000, 75)
+    p1, g1, f1 = run_fmm(x, q, 8, 0.5, 64, precision="mixed", dtype=np.float64, m2l_lattice=True)
+    p0, g0, f0 = run_fmm(x, q, 8, 0.5, 64, precision="mixed", dtype=np.float64, m2l_lattice=False)
+    assert f1.stats()["lattice_levels"] == 1 << 4 and f0.stats()["lattice_levels"] == 0
+    assert f1.stats()["async_error"] == 0
+    assert np.array_equal(p1, p0) and np.array_equal(g1, g0)
+    f1.close()
+    f0.close()
+
+
 def test_lattice_path_within_the_error_bound():
     # N = 2e5 uniform, p = 8: level 4 by TMA; against the oracle's direct sum
     # on sampled targets, within the FP64 FMM's own error plus 2e-6
