@@ -306,8 +306,13 @@ __global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
                     const int u = u0 + kk, c = u % CS, kb = u % KB;
                     const uint32_t ahi = tmem + (uint32_t)(C::ACC_COLS + c * C::ACOLS), alo = ahi + 32;
                     const uint32_t bb = VEC ? smem_u32(bops + (vi % NB) * C::OPV + kb * C::B_RAW) : smem_u32(bops + c * C::B_RAW);
+                    // k-steps of 8 coefficients holding any of the p^2 real ones: the
+                    // rest of a padded k-block is zero in A and in the operator and
+                    // would add exactly zero (p = 6: 5 of 8 k-steps; p = 8: all)
+                    const int ks = min(4, (PP - kb * 32 + 7) >> 3);
 #pragma unroll
                     for (int k = 0; k < 4; k++) {
+                        if (k >= ks) break;
                         // A_hi [T_hi ; T_lo] -> main | correction, then A_lo T_hi -> correction
                         mma_tf32_ta(dmain, ahi + 8 * k, sdesc(bb + 32 * k), id_full, (first && kb == 0 && k == 0) ? 0u : 1u);
                         mma_tf32_ta(dcorr, alo + 8 * k, sdesc(bb + 32 * k), id_half, 1u);
@@ -551,8 +556,12 @@ __global__ void __launch_bounds__(TcCfg<NP, KB>::NT, 1)
             // bits, an error below 2^-21 of a); both go to the A stage in TMEM
             const unsigned char *rs = araw + (g * RSG + j % RSG) * C::A_RAW + row * 128;
             const uint32_t ta = tmem + tlane + (uint32_t)(C::ACC_COLS + c * C::ACOLS);
+            // the second half of a k-block that holds only padding is never read
+            // by the MMAs (they skip its k-steps)
+            const int nh = (u % KB) * 32 + 16 < PP ? 2 : 1;
 #pragma unroll
             for (int h = 0; h < 2; h++) {
+                if (h >= nh) break;
                 float hi[16], lo[16];
 #pragma unroll
                 for (int q = 0; q < 4; q++) {
