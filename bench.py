@@ -623,7 +623,14 @@ def main():
         f.build(xt, qt)
         uni["build_ms_traversal"] = min(bt)
 
-    # end to end through the C ABI with pinned host buffers
+    # the device-buffer handle and inputs are done with: the end-to-end leg
+    # through the C ABI with pinned host buffers runs with the device to itself
+    f.close()
+    del xt, qt, phi, grad, x64, q64
+    if a.targets > 0:
+        del pd, gd, tgt
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
     e2e = None
     if not a.no_e2e:
         e2e = run_e2e(a, x, q, N, ncrit, world, dist, dev)
@@ -680,11 +687,7 @@ def main():
                                                                              "m2l_engine")},
                "roofline": roofline, "phase_rooflines": phases_roof, "cpu_baseline": cpu, "e2e": e2e,
                "gpu_launches": launches, "clocks": ck, "uniform_path": uni}
-    f.close()
     if rank == 0:
-        if world == 1 and (a.batch > 0 or a.diff_n > 0 or a.engines_n > 0):
-            del xt, qt, phi, grad
-            torch.cuda.empty_cache()
         if world == 1 and a.batch > 0:
             out["batch"] = run_batch(a, dev)
         if world == 1 and a.diff_n > 0:
